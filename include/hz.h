@@ -1,0 +1,174 @@
+/*
+ * hz.h -- C ABI of the GB300 two-level ORAS-FGMRES Helmholtz solver.
+ *
+ * Method: Dolean, Jolivet, Tournier, Operto, "Iterative frequency-domain
+ * seismic wave solvers based on multi-level domain-decomposition
+ * preconditioners" (EAGE 2020, arXiv 2004.06309).
+ *   Eq. (1)  (Delta + k^2(x)) u = b, k = omega / c(x), c complex; first-order
+ *            absorbing faces on the sides and bottom, Dirichlet on top.
+ *   Eq. (2)  A u = b from P1/P2 Lagrange elements on tetrahedra.
+ *   Eq. (3)  M^{-1} = M_1^{-1}(I - A Q) + Q, Q = Z E^{-1} Z^T, E = Z^T A Z.
+ *   Eq. (4)  M_1^{-1} = sum_i R_i^T D_i A_i^{-1} R_i (one-level ORAS).
+ *   GMRES with relative-residual stopping rule ||A x - b|| / ||b|| <= tol
+ *   (experiments section; tol = 1e-6 there).
+ *
+ * Conventions
+ *   - Complex values are interleaved (re, im) pairs of double: complex128.
+ *   - Vectors indexed by global dofs: vertex dofs are the mesh vertices in
+ *     input order, then (P2) one dof per mesh edge, edges sorted by
+ *     (smaller vertex id, larger vertex id).
+ *   - Sign convention (time dependence e^{-i omega t}): the absorbing
+ *     condition is d_n u - i k u = 0 and A = K - omega^2 M' - i omega B'
+ *     with M' = int c^-2 phi phi, B' = int_{ABC} c^-1 phi phi; a point source
+ *     at x_s has right-hand side -phi_a(x_s).  Dirichlet dofs are identity
+ *     rows/columns of A and carry zero right-hand side.
+ *   - Every call returns a status and never aborts.  A context is not
+ *     thread-safe; all device work is ordered on options.stream.
+ *   - The library owns every device buffer it allocates (cudaMalloc); the
+ *     caller keeps ownership of everything it passes in.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hz_ctx hz_ctx;
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad option) */
+  HZ_ERR_STATE = 2,         /* call out of order (e.g. solve before factor)          */
+  HZ_ERR_OOM = 3,           /* device allocation failed or over options.hbm_budget   */
+  HZ_ERR_CUDA = 4,          /* a CUDA runtime call failed                             */
+  HZ_ERR_ZERO_PIVOT = 5,    /* |d_j| below 1e-13 max|A_i| in an LDL^T factor          */
+  HZ_ERR_BREAKDOWN = 6,     /* non-finite value met in the Krylov iteration           */
+  HZ_ERR_NOT_CONVERGED = 7, /* iteration limit reached; x holds the last iterate      */
+  HZ_ERR_TIMEOUT = 8        /* a bounded device wait ran out                          */
+} hz_status;
+
+enum { HZ_TAG_DIRICHLET = 0, HZ_TAG_ABC = 1 };
+enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+
+/* Mesh (Eq. 1-2).  All arrays are host pointers, read during hz_setup_mesh only. */
+typedef struct {
+  int64_t nv;               /* vertices                                              */
+  int64_t ne;               /* tetrahedra                                            */
+  int64_t nf;               /* tagged boundary faces                                 */
+  const double* xyz;        /* nv x 3, row-major (km)                                */
+  const int32_t* tets;      /* ne x 4 vertex ids                                     */
+  const int32_t* faces;     /* nf x 3 vertex ids: every boundary face of the mesh    */
+  const int8_t* face_tag;   /* nf: HZ_TAG_DIRICHLET (top) or HZ_TAG_ABC              */
+  const double* c_re;       /* ne: wave speed per element, real part (km/s)          */
+  const double* c_im;       /* ne: imaginary part (attenuation)                      */
+  int32_t order;            /* 1 or 2                                                */
+  /* Nested coarse mesh for the two-level method (Eq. 3); ignored if levels == 1.
+     The fine mesh must be one uniform refinement of it: every fine tet lies inside
+     coarse tet fine_parent[e]. */
+  int64_t coarse_nv, coarse_ne, coarse_nf;
+  const double* coarse_xyz;
+  const int32_t* coarse_tets;
+  const int32_t* coarse_faces;
+  const int8_t* coarse_face_tag;
+  const int32_t* fine_parent;  /* ne */
+} hz_mesh_desc;
+
+typedef struct {
+  int32_t nsub;             /* N_d subdomains (Eq. 4)                                */
+  int32_t overlap;          /* delta: element layers grown through shared vertices   */
+  int32_t levels;           /* 1 (Eq. 4) or 2 (Eq. 3)                                */
+  int32_t restart;          /* m of FGMRES(m)                                        */
+  int32_t precision;        /* HZ_FP64, or HZ_MIXED: subdomain factors/solves c64    */
+  int32_t max_iter;         /* total inner-iteration limit per right-hand side       */
+  int32_t leaf_size;        /* nested-dissection leaf size (0: default 64)           */
+  int32_t max_snode;        /* widest supernode (0: default 96; capped at 112 for
+                               HZ_FP64 and 128 for HZ_MIXED)                      */
+  uint64_t hbm_budget;      /* bytes; 0 = unlimited                                  */
+  const int32_t* elem_part; /* ne part ids in [0, nsub) (host); NULL = built-in RCB  */
+  uintptr_t stream;         /* cudaStream_t; 0 = legacy default stream               */
+} hz_options;
+
+typedef struct {
+  int32_t iterations;       /* total inner iterations over all restarts              */
+  int32_t status;           /* HZ_OK or HZ_ERR_NOT_CONVERGED / HZ_ERR_BREAKDOWN      */
+  double rel_residual;      /* true ||b - A x|| / ||b|| at return                     */
+} hz_rhs_info;
+
+typedef struct {
+  int64_t n;                /* fine dofs                                             */
+  int64_t nnz;              /* nonzeros of A                                          */
+  int64_t n_coarse;         /* coarse dofs (0 if one level)                          */
+  int64_t nnz_coarse;       /* nonzeros of E                                          */
+  int64_t sum_ni;           /* total dofs over overlapping subdomains                */
+  int64_t nnz_local;        /* nonzeros of all A_i (full, both triangles)            */
+  int64_t nnz_factor;       /* stored panel entries of all local factors             */
+  int64_t nnz_factor_coarse;/* stored panel entries of the coarse factor             */
+  int64_t nsupernodes;      /* local supernodes over all subdomains                  */
+  int32_t nlevels;          /* local assembly-tree levels                            */
+  int32_t nlevels_coarse;
+  int64_t front_bytes;      /* transient device bytes of the frontal workspace       */
+  int64_t device_bytes;     /* device bytes held by the context after hz_factor      */
+  double factor_flops;      /* real flops of the numeric local factorisation         */
+  double setup_seconds;     /* host wall time of hz_setup_mesh                        */
+  double factor_seconds;    /* wall time of the last hz_factor                        */
+  double min_pivot;         /* min |d_j| over all local factors (last hz_factor)     */
+} hz_stats;
+
+/* Build everything that does not depend on frequency: dofs, the sparsity of A,
+   frequency-free matrices K, M', B' (Eq. 2), the overlapping decomposition with
+   its partition of unity and local absorbing interfaces (Eq. 4), nested
+   dissection orderings and symbolic supernodal factorisations of every A_i and
+   of E, and the interpolation Z (Eq. 3).  Copies what it needs; returns a context
+   in *out.  Errors: HZ_ERR_ARG (bad mesh/options), HZ_ERR_OOM, HZ_ERR_CUDA. */
+hz_status hz_setup_mesh(const hz_mesh_desc* mesh, const hz_options* opt, hz_ctx** out);
+
+/* Per frequency (omega = 2 pi freq_hz): assemble A(omega) and every A_i(omega)
+   on the device, factor all A_i = L_i D_i L_i^T (complex symmetric, no pivoting,
+   batched by assembly-tree level) and, with two levels, E = Z^T A Z in FP64.
+   Replaces any previous factorisation.  HZ_ERR_ZERO_PIVOT if a pivot is tiny. */
+hz_status hz_factor(hz_ctx* ctx, double freq_hz);
+
+/* Solve A x = b for nrhs right-hand sides with right-preconditioned FGMRES(m)
+   (CGS2, complex Givens), x0 = 0, until ||b - A x|| / ||b|| <= tol.
+   rhs, x: complex128, n x nrhs column-major; host pointers if on_device == 0
+   (copied in and out on the context's stream inside this call), device pointers
+   otherwise.  info: nrhs entries (may be NULL).  Returns HZ_ERR_STATE before
+   hz_factor; HZ_ERR_NOT_CONVERGED if any column hit max_iter. */
+hz_status hz_solve(hz_ctx* ctx, const void* rhs, int32_t nrhs, double tol, void* x,
+                   int32_t on_device, hz_rhs_info* info);
+
+/* Point-source right-hand sides: column j = -phi(x_j) (zero on Dirichlet dofs).
+   xyz: host nsrc x 3.  rhs_out: complex128 n x nsrc, host or device per on_device.
+   HZ_ERR_ARG if a point lies outside the mesh. */
+hz_status hz_point_sources(hz_ctx* ctx, const double* xyz, int32_t nsrc, void* rhs_out,
+                           int32_t on_device);
+
+/* y = A x (device complex128 vectors of length n) -- the operator of Eq. (2). */
+hz_status hz_apply_A(hz_ctx* ctx, const void* x_dev, void* y_dev);
+
+/* z = M^{-1} v (device complex128, length n) -- Eq. (3) with two levels, Eq. (4)
+   with one.  HZ_ERR_STATE before hz_factor. */
+hz_status hz_apply_M(hz_ctx* ctx, const void* v_dev, void* z_dev);
+
+/* Host-only planning: runs the frequency-independent analysis of hz_setup_mesh
+   (dofs, decomposition, orderings, symbolic factorisations) without touching
+   the device, and fills *out with sizes, factor flops and the device bytes a
+   context would hold after hz_factor (the transient frontal workspace is
+   front_bytes on top).  Lets a caller admit work against an HBM budget. */
+hz_status hz_plan(const hz_mesh_desc* mesh, const hz_options* opt, hz_stats* out);
+
+/* Sizes and timings of a context (see hz_stats). */
+hz_status hz_get_stats(const hz_ctx* ctx, hz_stats* out);
+int64_t hz_ndofs(const hz_ctx* ctx);
+const char* hz_status_string(hz_status s);
+/* Message of the last error on this context ("" if none). */
+const char* hz_last_error(const hz_ctx* ctx);
+void hz_free(hz_ctx* ctx); /* NULL-safe; releases every device buffer of the context */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H */

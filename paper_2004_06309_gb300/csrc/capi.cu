@@ -1,0 +1,793 @@
+// C ABI of the hz library: context management, per-frequency factorisation and
+// the right-preconditioned FGMRES(m) driver.  See include/hz.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hz.h"
+#include "dev.h"
+#include "host.h"
+
+using hz::cplx;
+
+struct hz_ctx {
+  std::string err;
+  hz_options opt{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  int order = 1, levels = 1, restart = 30, precision = 0, max_iter = 1000;
+  hz::Mesh mesh;       // kept for point location
+  hz::Dofs dofs;       // kept for point sources
+  int64_t n = 0, nnz = 0, nH = 0, nnzH = 0;
+  // global operator
+  int64_t* d_rp = nullptr;
+  int32_t* d_ci = nullptr;
+  double* d_K = nullptr;
+  double2* d_M = nullptr;
+  double2* d_B = nullptr;
+  double2* d_A = nullptr;
+  // coarse interpolation
+  int64_t *d_Zrp = nullptr, *d_Ztrp = nullptr;
+  int32_t *d_Zci = nullptr, *d_Ztci = nullptr;
+  double *d_Zv = nullptr, *d_Ztv = nullptr;
+  hz::FactorDev loc, crs;
+  double loc_max[3] = {0, 0, 0}, crs_max[3] = {0, 0, 0};
+  // Krylov workspace
+  double2 *V = nullptr, *Zs = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *y = nullptr, *t = nullptr;
+  double2 *rH = nullptr, *yH = nullptr;
+  double2 *partial = nullptr, *h1 = nullptr, *h2 = nullptr, *nrm = nullptr;
+  double2 *H = nullptr, *sn = nullptr, *g = nullptr, *ysol = nullptr;
+  double *cs = nullptr, *scal = nullptr;   // scal: est, invh, invbeta, beta
+  int* brk = nullptr;
+  hz::DevStatus* status = nullptr;
+  double* h_pin = nullptr;                 // pinned: est, invh, invbeta, beta, brk, norm
+  bool factored = false;
+  hz_stats stats{};
+  std::vector<void*> allocs;
+  std::vector<size_t> sizes;
+  int64_t bytes = 0;
+};
+
+namespace {
+
+hz_status fail(hz_ctx* c, hz_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, HZ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <typename T>
+hz_status dalloc(hz_ctx* c, T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) return HZ_OK;
+  const size_t bytes = size_t(count) * sizeof(T);
+  if (c->opt.hbm_budget && uint64_t(c->bytes) + bytes > c->opt.hbm_budget)
+    return fail(c, HZ_ERR_OOM, "allocation exceeds hbm_budget");
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  c->sizes.push_back(bytes);
+  c->bytes += int64_t(bytes);
+  return HZ_OK;
+}
+
+void dfree(hz_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) {
+    const size_t i = size_t(it - c->allocs.begin());
+    c->bytes -= int64_t(c->sizes[i]);
+    c->allocs.erase(it);
+    c->sizes.erase(c->sizes.begin() + i);
+  }
+  cudaFree(p);
+}
+
+template <typename T>
+hz_status upload(hz_ctx* c, T** dst, const std::vector<T>& v) {
+  hz_status s = dalloc(c, dst, int64_t(v.size()));
+  if (s != HZ_OK) return s;
+  if (!v.empty()) CU(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
+  return HZ_OK;
+}
+
+#define TRY(expr)                     \
+  do {                                \
+    hz_status s_ = (expr);            \
+    if (s_ != HZ_OK) return s_;       \
+  } while (0)
+
+std::vector<double2> to_d2(const std::vector<cplx>& v) {
+  std::vector<double2> o(v.size());
+  for (size_t i = 0; i < v.size(); i++) o[i] = make_double2(v[i].real(), v[i].imag());
+  return o;
+}
+
+// Device copy of a symbolic set with its task lists.
+hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
+                        double maxabs[3]) {
+  F = hz::FactorDev();
+  F.precision = precision;
+  F.nmat = S.nmat;
+  F.nsn = int(S.sn_k.size());
+  F.nlev = S.nlev;
+  F.ntot = S.voff.back();
+  F.panel_elems = S.panel_elems;
+  F.u_elems = S.u_elems;
+  F.front_elems = S.front_elems;
+  F.nentries = int64_t(S.epos.size());
+  F.nglob = nglob;
+  const int ns = F.nsn;
+  std::vector<hz::SnDev> sn(ns);
+  for (int s = 0; s < ns; s++) {
+    sn[s].k = S.sn_k[s];
+    sn[s].m = S.sn_m[s];
+    sn[s].first = S.sn_first[s];
+    sn[s].parent = S.sn_parent[s];
+    sn[s].rowoff = S.sn_rowoff[s];
+    sn[s].paneloff = S.sn_paneloff[s];
+    sn[s].uoff = S.sn_uoff[s];
+    sn[s].frontoff = S.sn_frontoff[s];
+    F.maxk = std::max(F.maxk, S.sn_k[s]);
+    F.maxm = std::max(F.maxm, S.sn_m[s]);
+  }
+  const size_t vs = precision == 0 ? 16 : 8;
+  if (size_t(F.maxm) * vs > 227 * 1024)
+    return fail(c, HZ_ERR_ARG, "a supernode front is too large for the backward-solve staging; use more subdomains");
+  TRY(upload(c, &F.sn, sn));
+  TRY(upload(c, &F.rowlist, S.rowlist));
+  TRY(upload(c, &F.cptr, S.cptr));
+  TRY(upload(c, &F.cidx, S.cidx));
+  TRY(upload(c, &F.rel, S.rel));
+  TRY(upload(c, &F.reloff, S.sn_reloff));
+  TRY(upload(c, &F.gidx, S.gidx));
+  TRY(upload(c, &F.epos, S.epos));
+  TRY(upload(c, &F.ek, S.ek));
+  TRY(upload(c, &F.em, to_d2(S.em)));
+  TRY(upload(c, &F.eb, to_d2(S.eb)));
+  for (size_t e = 0; e < S.ek.size(); e++) {
+    maxabs[0] = std::max(maxabs[0], std::fabs(S.ek[e]));
+    maxabs[1] = std::max(maxabs[1], std::abs(S.em[e]));
+    maxabs[2] = std::max(maxabs[2], std::abs(S.eb[e]));
+  }
+  // gather-form prolongation (entries with zero weight are skipped)
+  {
+    std::vector<int64_t> pptr(nglob + 1, 0);
+    for (int64_t q = 0; q < F.ntot; q++)
+      if (S.weight[q] != 0.0) pptr[S.gidx[q] + 1]++;
+    for (int64_t g = 0; g < nglob; g++) pptr[g + 1] += pptr[g];
+    std::vector<int32_t> pidx(pptr[nglob]);
+    std::vector<double> pw(pptr[nglob]);
+    std::vector<int64_t> fill(pptr.begin(), pptr.end() - 1);
+    for (int64_t q = 0; q < F.ntot; q++)
+      if (S.weight[q] != 0.0) {
+        const int64_t p = fill[S.gidx[q]]++;
+        pidx[p] = int32_t(q);
+        pw[p] = S.weight[q];
+      }
+    TRY(upload(c, &F.pptr, pptr));
+    TRY(upload(c, &F.pidx, pidx));
+    TRY(upload(c, &F.pw, pw));
+  }
+  // task lists
+  const int nlev = S.nlev;
+  std::vector<int2> fwd, bwd, wg, ea;
+  std::vector<int4> cbt;
+  std::vector<int64_t> scr_off(ns, 0);
+  std::vector<std::vector<int32_t>> children(ns);
+  for (int s = 0; s < ns; s++)
+    if (S.sn_parent[s] >= 0) children[S.sn_parent[s]].push_back(s);
+  int max_slot = 1;
+  for (int s = 0; s < ns; s++) max_slot = std::max(max_slot, int(children[s].size()));
+  F.max_slot = max_slot;
+  std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), wg_ptr(nlev + 1),
+      cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1);
+  int64_t scratch = 0;
+  for (int l = 0; l < nlev; l++) {
+    lev_ptr[l] = S.lev_ptr[l];
+    fwd_ptr[l] = int64_t(fwd.size());
+    bwd_ptr[l] = int64_t(bwd.size());
+    wg_ptr[l] = int64_t(wg.size());
+    cb_ptr[l] = int64_t(cbt.size());
+    int64_t lev_scr = 0;
+    for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+      const int s = S.lev_sn[q];
+      const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
+      for (int rb = 0; rb * 64 < m; rb++) fwd.push_back(make_int2(s, rb));
+      for (int cb = 0; cb * 32 < k; cb++) bwd.push_back(make_int2(s, cb));
+      for (int rb = 0; rb * 32 < r; rb++) wg.push_back(make_int2(s, rb));
+      const int T = (r + 31) / 32;
+      for (int ti = 0; ti < T; ti++)
+        for (int tj = 0; tj <= ti; tj++) cbt.push_back(make_int4(s, ti, tj, 0));
+      scr_off[s] = lev_scr;
+      lev_scr += int64_t(r) * k;
+    }
+    scratch = std::max(scratch, lev_scr);
+    for (int q = 0; q < max_slot; q++) {
+      ea_ptr[int64_t(l) * max_slot + q] = int64_t(ea.size());
+      for (int32_t z = S.lev_ptr[l]; z < S.lev_ptr[l + 1]; z++) {
+        const int p = S.lev_sn[z];
+        if (q < int(children[p].size())) {
+          const int ch = children[p][q];
+          const int r = S.sn_m[ch] - S.sn_k[ch];
+          for (int cb = 0; cb * 8 < r; cb++) ea.push_back(make_int2(ch, cb));
+        }
+      }
+    }
+  }
+  lev_ptr[nlev] = S.lev_ptr[nlev];
+  fwd_ptr[nlev] = int64_t(fwd.size());
+  bwd_ptr[nlev] = int64_t(bwd.size());
+  wg_ptr[nlev] = int64_t(wg.size());
+  cb_ptr[nlev] = int64_t(cbt.size());
+  ea_ptr[int64_t(nlev) * max_slot] = int64_t(ea.size());
+  F.scratch_elems = scratch;
+  TRY(upload(c, &F.fwd_tasks, fwd));
+  TRY(upload(c, &F.bwd_tasks, bwd));
+  TRY(upload(c, &F.wg_tasks, wg));
+  TRY(upload(c, &F.cb_tasks, cbt));
+  TRY(upload(c, &F.ea_tasks, ea));
+  TRY(upload(c, &F.scr_off, scr_off));
+  TRY(upload(c, &F.lev_sn, S.lev_sn));
+  auto hcopy = [](const std::vector<int64_t>& v) {
+    int64_t* p = new int64_t[v.size()];
+    std::copy(v.begin(), v.end(), p);
+    return p;
+  };
+  F.h_lev_ptr = hcopy(lev_ptr);
+  F.h_fwd_ptr = hcopy(fwd_ptr);
+  F.h_bwd_ptr = hcopy(bwd_ptr);
+  F.h_wg_ptr = hcopy(wg_ptr);
+  F.h_cb_ptr = hcopy(cb_ptr);
+  F.h_ea_ptr = hcopy(ea_ptr);
+  // numeric storage and solve workspaces
+  void *pan = nullptr, *tl = nullptr, *zl = nullptr, *xl = nullptr, *uw = nullptr;
+  TRY(dalloc(c, (char**)&pan, F.panel_elems * int64_t(vs)));
+  TRY(dalloc(c, (char**)&tl, F.ntot * int64_t(vs)));
+  TRY(dalloc(c, (char**)&zl, F.ntot * int64_t(vs)));
+  TRY(dalloc(c, (char**)&xl, F.ntot * int64_t(vs)));
+  TRY(dalloc(c, (char**)&uw, std::max<int64_t>(F.u_elems, 1) * int64_t(vs)));
+  F.panels = pan;
+  F.t_loc = tl;
+  F.z_loc = zl;
+  F.x_loc = xl;
+  F.u_ws = uw;
+  return HZ_OK;
+}
+
+void free_host_ptrs(hz::FactorDev& F) {
+  delete[] F.h_lev_ptr;
+  delete[] F.h_fwd_ptr;
+  delete[] F.h_bwd_ptr;
+  delete[] F.h_wg_ptr;
+  delete[] F.h_cb_ptr;
+  delete[] F.h_ea_ptr;
+  F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = nullptr;
+}
+
+hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[3], double& min_pivot) {
+  if (F.nsn == 0) return HZ_OK;
+  const size_t vs = F.precision == 0 ? 16 : 8;
+  char *fronts = nullptr, *scratch = nullptr;
+  TRY(dalloc(c, &fronts, F.front_elems * int64_t(vs)));
+  hz_status s = dalloc(c, &scratch, std::max<int64_t>(F.scratch_elems, 1) * int64_t(vs));
+  if (s != HZ_OK) {
+    dfree(c, fronts);
+    return s;
+  }
+  hz::DevStatus init{0u, 0u, 0.0};
+  const double big = 1e300;
+  std::memcpy(&init.min_pivot, &big, sizeof(double));
+  CU(cudaMemcpyAsync(c->status, &init, sizeof(init), cudaMemcpyHostToDevice, c->st));
+  CU(cudaMemsetAsync(fronts, 0, size_t(F.front_elems) * vs, c->st));
+  hz::launch_front_fill(F, w, fronts, c->st);
+  const double tiny = 1e-13 * (maxabs[0] + w * w * maxabs[1] + w * maxabs[2]);
+  for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, fronts, scratch, c->status, tiny, c->st);
+  hz::launch_panel_copy(F, fronts, c->st);
+  CU(cudaGetLastError());
+  hz::DevStatus out{};
+  CU(cudaMemcpyAsync(&out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  dfree(c, fronts);
+  dfree(c, scratch);
+  min_pivot = std::min(min_pivot, out.min_pivot);
+  if (out.zero_pivot) return fail(c, HZ_ERR_ZERO_PIVOT, "tiny pivot in a local LDL^T factor");
+  return HZ_OK;
+}
+
+// z = M^{-1} v  (Eq. 3 with two levels, Eq. 4 with one)
+void apply_prec(hz_ctx* c, const double2* v, double2* z) {
+  cudaStream_t st = c->st;
+  if (c->levels == 2) {
+    hz::launch_spmv_real(c->nH, c->d_Ztrp, c->d_Ztci, c->d_Ztv, v, c->rH, st);   // r_H = Z^T v
+    hz::launch_gather(c->crs, c->rH, st);
+    hz::launch_solve(c->crs, st);                                                // E^{-1}
+    hz::launch_prolong(c->crs, nullptr, c->yH, st);
+    hz::launch_spmv_real(c->n, c->d_Zrp, c->d_Zci, c->d_Zv, c->yH, c->y, st);     // y = Z y_H
+    hz::launch_spmv(c->n, c->d_rp, c->d_ci, c->d_A, c->y, v, c->t, st);          // t = v - A y
+    hz::launch_gather(c->loc, c->t, st);                                         // R_i t
+    hz::launch_solve(c->loc, st);                                                // A_i^{-1}
+    hz::launch_prolong(c->loc, c->y, z, st);                                     // y + sum R_i^T D_i x_i
+  } else {
+    hz::launch_gather(c->loc, v, st);
+    hz::launch_solve(c->loc, st);
+    hz::launch_prolong(c->loc, nullptr, z, st);
+  }
+}
+
+hz_status read_scalars(hz_ctx* c) {
+  CU(cudaMemcpyAsync(c->h_pin, c->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CU(cudaMemcpyAsync(c->h_pin + 4, c->brk, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  return HZ_OK;
+}
+
+hz_status norm2(hz_ctx* c, const double2* v, double& out) {
+  const int nb = hz::cgs_blocks();
+  hz::launch_cgs(c->n, 0, c->V, c->n, nullptr, const_cast<double2*>(v), 0, c->partial, c->st);
+  hz::launch_reduce(c->partial, nb, 0, c->nrm, c->st);
+  CU(cudaMemcpyAsync(c->h_pin + 5, &c->nrm[64].x, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  out = std::sqrt(c->h_pin[5]);
+  return HZ_OK;
+}
+
+// One right-hand side: FGMRES(m), CGS2, complex Givens (x0 = 0).
+hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
+  const int64_t n = c->n;
+  const int m = c->restart;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  double bnorm = 0;
+  TRY(norm2(c, c->b, bnorm));
+  CU(cudaMemsetAsync(c->x, 0, size_t(n) * 16, st));
+  info->iterations = 0;
+  info->status = HZ_OK;
+  info->rel_residual = 0.0;
+  if (bnorm == 0.0) return HZ_OK;
+  if (!std::isfinite(bnorm)) {
+    info->status = HZ_ERR_BREAKDOWN;
+    return HZ_OK;
+  }
+  double* d_est = c->scal;
+  double* d_invh = c->scal + 1;
+  double* d_invbeta = c->scal + 2;
+  double* d_beta = c->scal + 3;
+  // r = b
+  hz::launch_axpby_copy(n, c->b, c->w, st);
+  hz::launch_cgs(n, 0, c->V, n, nullptr, c->w, 0, c->partial, st);
+  hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+  int its = 0;
+  for (;;) {
+    hz::launch_init_cycle(c->nrm, c->g, m, d_invbeta, d_beta, st);
+    hz::launch_scale(n, c->w, d_invbeta, c->V, st);
+    int k = 0;
+    bool stop_nonfinite = false;
+    for (int j = 0; j < m; j++) {
+      double2* vj = c->V + int64_t(j) * n;
+      double2* zj = c->Zs + int64_t(j) * n;
+      apply_prec(c, vj, zj);
+      hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, zj, nullptr, c->w, st);
+      hz::launch_cgs(n, j + 1, c->V, n, nullptr, c->w, j + 1, c->partial, st);   // h1, |w|
+      hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
+      hz::launch_cgs(n, j + 1, c->V, n, c->h1, c->w, j + 1, c->partial, st);     // w -= V h1; h2
+      hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
+      hz::launch_cgs(n, j + 1, c->V, n, c->h2, c->w, 0, c->partial, st);         // w -= V h2; |w|
+      hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+      hz::launch_givens(j, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, bnorm, d_est, c->brk, d_invh, st);
+      TRY(read_scalars(c));
+      its++;
+      k = j + 1;
+      const double est = c->h_pin[0];
+      int brk = 0;
+      std::memcpy(&brk, c->h_pin + 4, sizeof(int));
+      if (!std::isfinite(est)) { stop_nonfinite = true; break; }
+      if (brk || est <= tol || its >= c->max_iter) break;
+      hz::launch_scale(n, c->w, d_invh, c->V + int64_t(j + 1) * n, st);
+    }
+    if (stop_nonfinite) {
+      info->iterations = its;
+      info->status = HZ_ERR_BREAKDOWN;
+      info->rel_residual = NAN;
+      return HZ_OK;
+    }
+    hz::launch_update_x(n, k, c->H, m + 1, c->g, c->ysol, c->Zs, n, c->x, st);
+    hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, c->x, c->b, c->w, st);        // r = b - A x
+    double rn = 0;
+    TRY(norm2(c, c->w, rn));
+    const double rel = rn / bnorm;
+    info->iterations = its;
+    info->rel_residual = rel;
+    if (!std::isfinite(rel)) {
+      info->status = HZ_ERR_BREAKDOWN;
+      return HZ_OK;
+    }
+    if (rel <= tol) return HZ_OK;
+    if (its >= c->max_iter) {
+      info->status = HZ_ERR_NOT_CONVERGED;
+      return HZ_OK;
+    }
+    // nrm still holds |r|^2 from norm2 for the next cycle
+  }
+}
+
+hz_status check_ctx(hz_ctx* c) {
+  if (!c) return HZ_ERR_ARG;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return fail(c, HZ_ERR_CUDA, cudaGetErrorString(e));
+  return HZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hz_status_string(hz_status s) {
+  switch (s) {
+    case HZ_OK: return "ok";
+    case HZ_ERR_ARG: return "invalid argument";
+    case HZ_ERR_STATE: return "call out of order";
+    case HZ_ERR_OOM: return "out of device memory";
+    case HZ_ERR_CUDA: return "CUDA error";
+    case HZ_ERR_ZERO_PIVOT: return "zero pivot";
+    case HZ_ERR_BREAKDOWN: return "breakdown";
+    case HZ_ERR_NOT_CONVERGED: return "not converged";
+    case HZ_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+const char* hz_last_error(const hz_ctx* c) { return c ? c->err.c_str() : ""; }
+
+int64_t hz_ndofs(const hz_ctx* c) { return c ? c->n : -1; }
+
+hz_status hz_get_stats(const hz_ctx* c, hz_stats* out) {
+  if (!c || !out) return HZ_ERR_ARG;
+  *out = c->stats;
+  out->device_bytes = c->bytes;
+  return HZ_OK;
+}
+
+void hz_free(hz_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->sizes.clear();
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  free_host_ptrs(c->loc);
+  free_host_ptrs(c->crs);
+  delete c;
+}
+
+}  // extern "C"
+
+// Host analysis shared by hz_setup_mesh and hz_plan.
+static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op, hz::HostProblem& P) {
+  if (!md || !op) return fail(c, HZ_ERR_ARG, "null mesh or options");
+  if (md->order != 1 && md->order != 2) return fail(c, HZ_ERR_ARG, "order must be 1 or 2");
+  if (md->nv <= 0 || md->ne <= 0 || !md->xyz || !md->tets || !md->c_re || !md->c_im)
+    return fail(c, HZ_ERR_ARG, "empty or incomplete mesh");
+  if (md->nf > 0 && (!md->faces || !md->face_tag)) return fail(c, HZ_ERR_ARG, "faces without tags");
+  if (op->nsub < 1 || op->overlap < 0 || (op->levels != 1 && op->levels != 2))
+    return fail(c, HZ_ERR_ARG, "bad nsub / overlap / levels");
+  if (op->restart < 1 || op->restart > 63) return fail(c, HZ_ERR_ARG, "restart must be in [1, 63]");
+  if (op->precision != HZ_FP64 && op->precision != HZ_MIXED) return fail(c, HZ_ERR_ARG, "bad precision");
+  const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
+  for (int64_t q = 0; q < ne * 4; q++)
+    if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
+  for (int64_t q = 0; q < nf * 3; q++)
+    if (md->faces[q] < 0 || md->faces[q] >= nv) return fail(c, HZ_ERR_ARG, "face vertex id out of range");
+  P.mesh.nv = nv;
+  P.mesh.ne = ne;
+  P.mesh.xyz.assign(md->xyz, md->xyz + 3 * nv);
+  P.mesh.tets.assign(md->tets, md->tets + 4 * ne);
+  P.mesh.faces.assign(md->faces, md->faces + 3 * nf);
+  P.mesh.tag.assign(md->face_tag, md->face_tag + nf);
+  P.mesh.c.resize(ne);
+  for (int64_t e = 0; e < ne; e++) {
+    P.mesh.c[e] = cplx(md->c_re[e], md->c_im[e]);
+    if (P.mesh.c[e] == cplx(0.0, 0.0)) return fail(c, HZ_ERR_ARG, "zero wave speed");
+  }
+  std::vector<int32_t> part;
+  if (op->elem_part) {
+    part.assign(op->elem_part, op->elem_part + ne);
+    for (int64_t e = 0; e < ne; e++)
+      if (part[e] < 0 || part[e] >= op->nsub) return fail(c, HZ_ERR_ARG, "elem_part out of range");
+  } else {
+    hz::rcb_partition(P.mesh, op->nsub, part);
+  }
+  if (op->levels == 2) {
+    if (!md->coarse_xyz || !md->coarse_tets || !md->fine_parent || md->coarse_nv <= 0 || md->coarse_ne <= 0)
+      return fail(c, HZ_ERR_ARG, "two levels need the nested coarse mesh");
+    P.cmesh.nv = md->coarse_nv;
+    P.cmesh.ne = md->coarse_ne;
+    P.cmesh.xyz.assign(md->coarse_xyz, md->coarse_xyz + 3 * md->coarse_nv);
+    P.cmesh.tets.assign(md->coarse_tets, md->coarse_tets + 4 * md->coarse_ne);
+    P.cmesh.faces.assign(md->coarse_faces, md->coarse_faces + 3 * md->coarse_nf);
+    P.cmesh.tag.assign(md->coarse_face_tag, md->coarse_face_tag + md->coarse_nf);
+    P.parent.assign(md->fine_parent, md->fine_parent + ne);
+    for (int64_t e = 0; e < ne; e++)
+      if (P.parent[e] < 0 || P.parent[e] >= md->coarse_ne) return fail(c, HZ_ERR_ARG, "fine_parent out of range");
+  }
+  hz::build_dofs(P.mesh, md->order, P.dofs);
+  hz::assemble_global(P.mesh, P.dofs, P.A);
+  hz::build_subdomains(P.mesh, P.dofs, part, op->nsub, op->overlap, P.subs);
+  const int prec_k = op->precision == HZ_FP64 ? 112 : 128;
+  int leaf = op->leaf_size > 0 ? op->leaf_size : 64;
+  int maxsn = op->max_snode > 0 ? op->max_snode : 96;
+  maxsn = std::min(maxsn, prec_k);
+  leaf = std::max(leaf, 1);
+  {
+    std::vector<hz::MatrixInput> mats(op->nsub);
+    std::vector<std::vector<double>> coords(op->nsub);
+    for (int i = 0; i < op->nsub; i++) {
+      const hz::Subdomain& S = P.subs[i];
+      coords[i].resize(S.dofs.size() * 3);
+      for (size_t k = 0; k < S.dofs.size(); k++)
+        for (int a = 0; a < 3; a++) coords[i][3 * k + a] = P.dofs.coord[3 * S.dofs[k] + a];
+      mats[i].A = &S.A;
+      mats[i].coord = coords[i].data();
+      mats[i].gidx = S.dofs.data();
+      mats[i].weight = S.D.data();
+    }
+    hz::symbolic_batch(mats, leaf, maxsn, P.local);
+  }
+  if (op->levels == 2) {
+    hz::build_coarse(P);
+    std::vector<double> coords(P.nH * 3);
+    std::vector<int64_t> gid(P.nH);
+    std::vector<double> one(P.nH, 1.0);
+    for (int64_t k = 0; k < P.cdofs.n; k++)
+      if (P.cfree[k] >= 0)
+        for (int a = 0; a < 3; a++) coords[3 * P.cfree[k] + a] = P.cdofs.coord[3 * k + a];
+    for (int64_t k = 0; k < P.nH; k++) gid[k] = k;
+    hz::MatrixInput mi{&P.E, coords.data(), gid.data(), one.data()};
+    hz::symbolic_batch({mi}, leaf, std::min(maxsn, 112), P.coarse);
+  }
+  return HZ_OK;
+}
+
+static void fill_stats(hz_ctx* c, const hz::HostProblem& P) {
+  hz_stats& s = c->stats;
+  s.n = P.dofs.n;
+  s.nnz = P.A.pat.nnz();
+  s.n_coarse = P.nH;
+  s.nnz_coarse = P.E.pat.nnz();
+  s.sum_ni = P.local.voff.empty() ? 0 : P.local.voff.back();
+  int64_t nl = 0;
+  for (const auto& S : P.subs) nl += S.A.pat.nnz();
+  s.nnz_local = nl;
+  s.nnz_factor = P.local.panel_elems;
+  s.nnz_factor_coarse = P.coarse.panel_elems;
+  s.nsupernodes = int64_t(P.local.sn_k.size());
+  s.nlevels = P.local.nlev;
+  s.nlevels_coarse = P.coarse.nlev;
+  const int64_t vs = c->opt.precision == HZ_FP64 ? 16 : 8;
+  s.front_bytes = std::max(P.local.front_elems * vs, P.coarse.front_elems * 16);
+  s.factor_flops = P.local.flops;
+}
+
+extern "C" hz_status hz_plan(const hz_mesh_desc* md, const hz_options* op, hz_stats* out) {
+  if (!out) return HZ_ERR_ARG;
+  hz_ctx tmp;
+  if (op) tmp.opt = *op;
+  auto t0 = std::chrono::steady_clock::now();
+  hz::HostProblem P;
+  hz_status s = analyse(&tmp, md, op, P);
+  if (s != HZ_OK) {
+    std::fprintf(stderr, "hz_plan: %s\n", tmp.err.c_str());
+    return s;
+  }
+  fill_stats(&tmp, P);
+  tmp.stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // device bytes a context would hold after hz_factor (excluding transient fronts)
+  const int64_t vs = op->precision == HZ_FP64 ? 16 : 8;
+  int64_t b = 0;
+  b += P.A.pat.nnz() * (4 + 8 + 16 + 16 + 16) + (P.dofs.n + 1) * 8;
+  b += P.local.panel_elems * vs + (3 * P.local.voff.back() + P.local.u_elems) * vs;
+  b += P.coarse.panel_elems * 16;
+  b += int64_t(2 * op->restart + 8) * P.dofs.n * 16;
+  tmp.stats.device_bytes = b;
+  *out = tmp.stats;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op, hz_ctx** outp) {
+  if (!outp) return HZ_ERR_ARG;
+  *outp = nullptr;
+  hz_ctx* c = new hz_ctx();
+  if (op) c->opt = *op;
+  auto t0 = std::chrono::steady_clock::now();
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      std::fprintf(stderr, "hz_setup_mesh: no CUDA device: %s\n", cudaGetErrorString(e));
+      delete c;
+      return HZ_ERR_CUDA;
+    }
+    c->device = dev;
+  }
+  hz::HostProblem P;
+  hz_status s = analyse(c, md, op, P);
+  if (s != HZ_OK) {
+    std::fprintf(stderr, "hz_setup_mesh: %s\n", c->err.c_str());
+    delete c;
+    return s;
+  }
+  c->st = reinterpret_cast<cudaStream_t>(op->stream);
+  c->order = md->order;
+  c->levels = op->levels;
+  c->restart = op->restart;
+  c->precision = op->precision;
+  c->max_iter = op->max_iter > 0 ? op->max_iter : 1000;
+  c->n = P.dofs.n;
+  c->nnz = P.A.pat.nnz();
+  c->nH = P.nH;
+  c->nnzH = P.E.pat.nnz();
+  fill_stats(c, P);
+  auto bail = [&](hz_status st) {
+    std::fprintf(stderr, "hz_setup_mesh: %s\n", c->err.c_str());
+    hz_free(c);
+    return st;
+  };
+#define SETUP_TRY(expr)                      \
+  do {                                       \
+    hz_status s_ = (expr);                   \
+    if (s_ != HZ_OK) return bail(s_);        \
+  } while (0)
+  SETUP_TRY(upload(c, &c->d_rp, P.A.pat.ptr));
+  SETUP_TRY(upload(c, &c->d_ci, P.A.pat.col));
+  SETUP_TRY(upload(c, &c->d_K, P.A.K));
+  SETUP_TRY(upload(c, &c->d_M, to_d2(P.A.M)));
+  SETUP_TRY(upload(c, &c->d_B, to_d2(P.A.B)));
+  SETUP_TRY(dalloc(c, &c->d_A, c->nnz));
+  SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max));
+  if (c->levels == 2) {
+    SETUP_TRY(upload(c, &c->d_Zrp, P.Z.ptr));
+    SETUP_TRY(upload(c, &c->d_Zci, P.Z.col));
+    SETUP_TRY(upload(c, &c->d_Zv, P.Zv));
+    SETUP_TRY(upload(c, &c->d_Ztrp, P.Zt.ptr));
+    SETUP_TRY(upload(c, &c->d_Ztci, P.Zt.col));
+    SETUP_TRY(upload(c, &c->d_Ztv, P.Ztv));
+    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max));
+    SETUP_TRY(dalloc(c, &c->rH, c->nH));
+    SETUP_TRY(dalloc(c, &c->yH, c->nH));
+  }
+  const int64_t n = c->n;
+  const int m = c->restart;
+  SETUP_TRY(dalloc(c, &c->V, n * (m + 1)));
+  SETUP_TRY(dalloc(c, &c->Zs, n * m));
+  SETUP_TRY(dalloc(c, &c->w, n));
+  SETUP_TRY(dalloc(c, &c->b, n));
+  SETUP_TRY(dalloc(c, &c->x, n));
+  SETUP_TRY(dalloc(c, &c->y, n));
+  SETUP_TRY(dalloc(c, &c->t, n));
+  SETUP_TRY(dalloc(c, &c->partial, int64_t(hz::cgs_blocks()) * 65));
+  SETUP_TRY(dalloc(c, &c->h1, 65));
+  SETUP_TRY(dalloc(c, &c->h2, 65));
+  SETUP_TRY(dalloc(c, &c->nrm, 65));
+  SETUP_TRY(dalloc(c, &c->H, int64_t(m + 1) * m));
+  SETUP_TRY(dalloc(c, &c->sn, m));
+  SETUP_TRY(dalloc(c, &c->g, m + 1));
+  SETUP_TRY(dalloc(c, &c->ysol, m));
+  SETUP_TRY(dalloc(c, &c->cs, m));
+  SETUP_TRY(dalloc(c, &c->scal, 4));
+  SETUP_TRY(dalloc(c, &c->brk, 1));
+  SETUP_TRY(dalloc(c, &c->status, 1));
+  if (cudaMallocHost((void**)&c->h_pin, 8 * sizeof(double)) != cudaSuccess) {
+    c->err = "cudaMallocHost failed";
+    return bail(HZ_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) {
+    c->err = "stream sync after upload failed";
+    return bail(HZ_ERR_CUDA);
+  }
+  c->mesh = std::move(P.mesh);
+  c->dofs = std::move(P.dofs);
+  c->stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *outp = c;
+  return HZ_OK;
+#undef SETUP_TRY
+}
+
+extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
+  TRY(check_ctx(c));
+  if (!(freq_hz > 0.0) || !std::isfinite(freq_hz)) return fail(c, HZ_ERR_ARG, "frequency must be positive");
+  auto t0 = std::chrono::steady_clock::now();
+  c->factored = false;
+  const double w = 2.0 * M_PI * freq_hz;
+  hz::launch_fill_values(c->nnz, c->d_K, c->d_M, c->d_B, w, c->d_A, c->st);
+  double minp = 1e300;
+  TRY(factor_one(c, c->loc, w, c->loc_max, minp));
+  if (c->levels == 2) TRY(factor_one(c, c->crs, w, c->crs_max, minp));
+  CU(cudaStreamSynchronize(c->st));
+  c->stats.min_pivot = minp;
+  c->stats.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->factored = true;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_apply_A(hz_ctx* c, const void* x, void* y) {
+  TRY(check_ctx(c));
+  if (!x || !y) return fail(c, HZ_ERR_ARG, "null vector");
+  if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run first (A depends on the frequency)");
+  hz::launch_spmv(c->n, c->d_rp, c->d_ci, c->d_A, (const double2*)x, nullptr, (double2*)y, c->st);
+  CU(cudaGetLastError());
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_apply_M(hz_ctx* c, const void* v, void* z) {
+  TRY(check_ctx(c));
+  if (!v || !z) return fail(c, HZ_ERR_ARG, "null vector");
+  if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run first");
+  apply_prec(c, (const double2*)v, (double2*)z);
+  CU(cudaGetLastError());
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double tol, void* x, int32_t on_device,
+                              hz_rhs_info* info) {
+  TRY(check_ctx(c));
+  if (!rhs || !x || nrhs < 0 || !(tol > 0.0)) return fail(c, HZ_ERR_ARG, "bad solve arguments");
+  if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run before hz_solve");
+  const int64_t n = c->n;
+  hz_status worst = HZ_OK;
+  for (int32_t j = 0; j < nrhs; j++) {
+    const double2* bj = (const double2*)rhs + int64_t(j) * n;
+    double2* xj = (double2*)x + int64_t(j) * n;
+    CU(cudaMemcpyAsync(c->b, bj, size_t(n) * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->st));
+    hz_rhs_info inf{};
+    TRY(fgmres_one(c, tol, &inf));
+    CU(cudaMemcpyAsync(xj, c->x, size_t(n) * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->st));
+    if (info) info[j] = inf;
+    if (inf.status != HZ_OK && worst == HZ_OK) worst = hz_status(inf.status);
+  }
+  CU(cudaStreamSynchronize(c->st));
+  return worst;
+}
+
+extern "C" hz_status hz_point_sources(hz_ctx* c, const double* xyz, int32_t nsrc, void* rhs_out, int32_t on_device) {
+  if (!c || !xyz || !rhs_out || nsrc < 0) return fail(c, HZ_ERR_ARG, "bad point-source arguments");
+  const int64_t n = c->n;
+  std::vector<double2> B(size_t(n) * nsrc, make_double2(0.0, 0.0));
+  const int nb = c->dofs.nb;
+  for (int j = 0; j < nsrc; j++) {
+    int64_t e = -1;
+    double lam[4], phi[10];
+    if (!hz::locate_point(c->mesh, xyz + 3 * j, e, lam)) return fail(c, HZ_ERR_ARG, "source outside the mesh");
+    hz::eval_basis(c->order, lam, phi);
+    for (int a = 0; a < nb; a++) {
+      const int64_t g = c->dofs.elem[int64_t(nb) * e + a];
+      if (!c->dofs.is_dir[g]) B[size_t(j) * n + g].x -= phi[a];
+    }
+  }
+  if (on_device) {
+    TRY(check_ctx(c));
+    CU(cudaMemcpyAsync(rhs_out, B.data(), B.size() * 16, cudaMemcpyHostToDevice, c->st));
+    CU(cudaStreamSynchronize(c->st));
+  } else {
+    std::memcpy(rhs_out, B.data(), B.size() * 16);
+  }
+  return HZ_OK;
+}

@@ -1,0 +1,101 @@
+// Device-side data structures and kernel launchers of the hz library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hz {
+
+// One supernode of a batched multifrontal factorisation (48 bytes).
+struct SnDev {
+  int32_t k, m, first, parent;   // pivots, front order, first vector index, parent (-1 root)
+  int64_t rowoff;                // into rowlist / cptr slots
+  int64_t paneloff;              // panel (m x k, column-major, ld m) in the factor store
+  int64_t uoff;                  // update vector (m - k) in the solve workspace
+  int64_t frontoff;              // front (m x m, column-major) in the frontal workspace
+};
+
+// Device view of a batched symbolic factorisation plus its numeric factor.
+struct FactorDev {
+  int nmat = 0, nsn = 0, nlev = 0;
+  int32_t maxk = 0, maxm = 0;
+  int64_t ntot = 0, nrows = 0, panel_elems = 0, u_elems = 0, front_elems = 0, nentries = 0;
+  SnDev* sn = nullptr;
+  int32_t* rowlist = nullptr;
+  int64_t* cptr = nullptr;
+  int64_t* cidx = nullptr;
+  int32_t* rel = nullptr;
+  int64_t* reloff = nullptr;
+  int32_t* gidx = nullptr;       // ntot: global index of each local vector entry
+  // gather-form prolongation: per global dof, its local entries and weights
+  int64_t nglob = 0;
+  int64_t* pptr = nullptr;
+  int32_t* pidx = nullptr;
+  double* pw = nullptr;
+  // frequency-free entry values and their front positions
+  int64_t* epos = nullptr;
+  double* ek = nullptr;
+  double2* em = nullptr;
+  double2* eb = nullptr;
+  // task arrays (device) and per-level host offsets
+  int2* fwd_tasks = nullptr;     // (sn, row block)
+  int2* bwd_tasks = nullptr;     // (sn, col block)
+  int2* ea_tasks = nullptr;      // (child sn, col block)
+  int2* wg_tasks = nullptr;      // (sn, row block of the off-diagonal part)
+  int4* cb_tasks = nullptr;      // (sn, row tile, col tile, scratch-relative offset unused)
+  int64_t* scr_off = nullptr;    // per supernode: offset of its W block in the level scratch
+  int32_t* lev_sn = nullptr;
+  int64_t* h_lev_ptr = nullptr;       // nlev + 1 (host)
+  int64_t* h_fwd_ptr = nullptr;       // nlev + 1
+  int64_t* h_bwd_ptr = nullptr;
+  int64_t* h_wg_ptr = nullptr;
+  int64_t* h_cb_ptr = nullptr;
+  int64_t* h_ea_ptr = nullptr;        // nlev * maxslot + 1, grouped (level, slot)
+  int32_t max_slot = 0;
+  int64_t scratch_elems = 0;          // max over levels of sum (m-k) k
+  // numeric
+  int precision = 0;                  // 0: complex128, 1: complex64
+  void* panels = nullptr;             // factor store
+  // solve workspaces (typed by precision)
+  void* t_loc = nullptr;
+  void* z_loc = nullptr;
+  void* x_loc = nullptr;
+  void* u_ws = nullptr;
+};
+
+// Status word written by device code (pivot health).
+struct DevStatus {
+  unsigned int zero_pivot;
+  unsigned int nonfinite;
+  double min_pivot;   // stored as the bit pattern of a non-negative double (atomicMin on u64)
+};
+
+// ---- launchers (kernels.cu) -------------------------------------------------
+void launch_fill_values(int64_t nnz, const double* K, const double2* M, const double2* B, double w,
+                        double2* out, cudaStream_t st);
+void launch_front_fill(const FactorDev& F, double w, void* fronts, cudaStream_t st);
+void launch_factor_level(const FactorDev& F, int lev, void* fronts, void* scratch, DevStatus* status,
+                         double tiny, cudaStream_t st);
+void launch_panel_copy(const FactorDev& F, const void* fronts, cudaStream_t st);
+
+void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st);
+void launch_solve(const FactorDev& F, cudaStream_t st);
+void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st);
+
+void launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
+                 const double2* sub, double2* y, cudaStream_t st);
+void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, const double2* x,
+                      double2* y, cudaStream_t st);
+int cgs_blocks();
+void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const double2* h, double2* w,
+                int ndot, double2* partial, cudaStream_t st);
+void launch_reduce(const double2* partial, int nblk, int ncols, double2* out, cudaStream_t st);
+void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
+                   const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown,
+                   double* invh, cudaStream_t st);
+void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta, cudaStream_t st);
+void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st);
+void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y,
+                     const double2* Zs, int64_t ldz, double2* x, cudaStream_t st);
+void launch_axpby_copy(int64_t n, const double2* a, double2* out, cudaStream_t st);
+
+}  // namespace hz

@@ -1,0 +1,777 @@
+// CUDA kernels of the hz library (sm_103a).
+//
+//   * value assembly A(omega) = K - omega^2 M' - i omega B'        (Eq. 2)
+//   * batched multifrontal complex-symmetric LDL^T of all A_i and E (the local
+//     "direct solver" of the method, factorised once per frequency)
+//   * batched supernodal forward / diagonal / backward solves       (Eq. 3-4)
+//   * restriction R_i (gather) and PU-weighted prolongation R_i^T D_i
+//   * complex CSR SpMV, real-by-complex CSR SpMV (Z, Z^T)
+//   * fused CGS2 passes, deterministic reductions, Givens update    (GMRES)
+//
+// Complex numbers are interleaved (re, im) pairs: double2 (complex128) or
+// float2 (complex64).  All reductions are fixed-order (no atomics on values),
+// so reruns are bitwise identical.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "dev.h"
+
+namespace hz {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename V> struct RealOf;
+template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<double2> { using T = double; };
+
+template <typename V>
+__device__ __forceinline__ V mk(typename RealOf<V>::T x, typename RealOf<V>::T y) {
+  V v;
+  v.x = x;
+  v.y = y;
+  return v;
+}
+template <typename V> __device__ __forceinline__ V czero() { return mk<V>(0, 0); }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cneg(V a) { return mk<V>(-a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk<V>(xfma(a.x, b.x, -a.y * b.y), xfma(a.x, b.y, a.y * b.x));
+}
+// c + a b
+template <typename V> __device__ __forceinline__ V cmad(V a, V b, V c) {
+  c.x = xfma(a.x, b.x, c.x);
+  c.x = xfma(-a.y, b.y, c.x);
+  c.y = xfma(a.x, b.y, c.y);
+  c.y = xfma(a.y, b.x, c.y);
+  return c;
+}
+// c - a b
+template <typename V> __device__ __forceinline__ V cmsub(V a, V b, V c) {
+  c.x = xfma(-a.x, b.x, c.x);
+  c.x = xfma(a.y, b.y, c.x);
+  c.y = xfma(-a.x, b.y, c.y);
+  c.y = xfma(-a.y, b.x, c.y);
+  return c;
+}
+// c + conj(a) b
+template <typename V> __device__ __forceinline__ V cmadc(V a, V b, V c) {
+  c.x = xfma(a.x, b.x, c.x);
+  c.x = xfma(a.y, b.y, c.x);
+  c.y = xfma(a.x, b.y, c.y);
+  c.y = xfma(-a.y, b.x, c.y);
+  return c;
+}
+template <typename V> __device__ __forceinline__ V cinv(V a) {
+  const typename RealOf<V>::T d = a.x * a.x + a.y * a.y;
+  return mk<V>(a.x / d, -a.y / d);
+}
+template <typename V> __device__ __forceinline__ V from2(double2 a);
+template <> __device__ __forceinline__ double2 from2<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from2<float2>(double2 a) { return make_float2(float(a.x), float(a.y)); }
+__device__ __forceinline__ double2 to2(double2 a) { return a; }
+__device__ __forceinline__ double2 to2(float2 a) { return make_double2(a.x, a.y); }
+
+template <typename V> __device__ __forceinline__ V shfl_xor(V v, int m, int w = 32) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m, w);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m, w);
+  return v;
+}
+template <typename V> __device__ __forceinline__ V warp_sum(V v) {
+  for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_xor(v, o));
+  return v;
+}
+
+static inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 16) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return unsigned(g);
+}
+
+// ---------------------------------------------------------------------------
+// value assembly, Eq. (2): A = K - w^2 M' - i w B'
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 helmholtz_value(double k, double2 m, double2 b, double w) {
+  // K - w^2 (m.x + i m.y) - i w (b.x + i b.y)
+  return make_double2(k - w * w * m.x + w * b.y, -w * w * m.y - w * b.x);
+}
+
+__global__ void k_fill_values(int64_t nnz, const double* K, const double2* M, const double2* B, double w,
+                              double2* out) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x)
+    out[e] = helmholtz_value(K[e], M[e], B[e], w);
+}
+
+void launch_fill_values(int64_t nnz, const double* K, const double2* M, const double2* B, double w,
+                        double2* out, cudaStream_t st) {
+  if (nnz == 0) return;
+  k_fill_values<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, K, M, B, w, out);
+}
+
+template <typename V>
+__global__ void k_front_fill(int64_t ne, const int64_t* epos, const double* K, const double2* M,
+                             const double2* B, double w, V* fronts) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < ne; e += int64_t(gridDim.x) * blockDim.x)
+    fronts[epos[e]] = from2<V>(helmholtz_value(K[e], M[e], B[e], w));
+}
+
+// ---------------------------------------------------------------------------
+// multifrontal factorisation, one assembly-tree level at a time
+// ---------------------------------------------------------------------------
+
+// Extend-add: parent front += child's contribution block (lower triangle).
+// One warp per contribution column; a launch holds at most one child per parent.
+template <typename V>
+__global__ void __launch_bounds__(256) k_extend_add(const int2* tasks, const SnDev* sn, const int32_t* rel,
+                                                    const int64_t* reloff, V* fronts) {
+  const int2 t = tasks[blockIdx.x];
+  const SnDev C = sn[t.x];
+  const int r = C.m - C.k;
+  const int b = t.y * 8 + (threadIdx.x >> 5);
+  if (b >= r) return;
+  const SnDev P = sn[C.parent];
+  const int32_t* rl = rel + reloff[t.x];
+  const V* Fc = fronts + C.frontoff;
+  V* Fp = fronts + P.frontoff;
+  const int64_t pc = int64_t(rl[b]) * P.m;
+  const int64_t cc = int64_t(C.k + b) * C.m + C.k;
+  for (int a = b + (threadIdx.x & 31); a < r; a += 32) {
+    const int64_t q = pc + rl[a];
+    Fp[q] = cadd(Fp[q], Fc[cc + a]);
+  }
+}
+
+__device__ __forceinline__ void record_pivot(DevStatus* st, double mag, double tiny) {
+  unsigned long long bits = __double_as_longlong(mag);
+  atomicMin(reinterpret_cast<unsigned long long*>(&st->min_pivot), bits);
+  if (!(mag >= tiny)) atomicOr(&st->zero_pivot, 1u);
+}
+
+// Pivot block: F11 = L D L^T in shared memory, then T = L^{-1} (unit lower) in
+// place; the front keeps T below the diagonal and D^{-1} on it.
+template <typename V>
+__global__ void __launch_bounds__(256) k_diag(const int32_t* lev_sn, const SnDev* sn, V* fronts,
+                                              DevStatus* status, double tiny) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* A = reinterpret_cast<V*>(smem_raw);
+  const SnDev S = sn[lev_sn[blockIdx.x]];
+  const int k = S.k, m = S.m, ld = k + 1;
+  V* dinv = A + ld * k;
+  V* row = dinv + k;
+  V* F = fronts + S.frontoff;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    A[i + j * ld] = (i >= j) ? F[i + int64_t(j) * m] : czero<V>();
+  }
+  __syncthreads();
+  for (int j = 0; j < k; j++) {
+    const V d = A[j + j * ld];
+    const V di = cinv(d);
+    if (tid == 0) {
+      dinv[j] = di;
+      record_pivot(status, sqrt(double(d.x) * double(d.x) + double(d.y) * double(d.y)), tiny);
+    }
+    for (int c = j + 1 + wid; c < k; c += 8) {
+      const V lc = cmul(A[c + j * ld], di);
+      for (int i = c + lane; i < k; i += 32) A[i + c * ld] = cmsub(A[i + j * ld], lc, A[i + c * ld]);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < k; i += blockDim.x) A[i + j * ld] = cmul(A[i + j * ld], di);
+    __syncthreads();
+  }
+  // T = L^{-1}, row by row: T[i][j] = -(L[i][j] + sum_{j<l<i} L[i][l] T[l][j])
+  for (int i = 1; i < k; i++) {
+    for (int l = tid; l < i; l += blockDim.x) row[l] = A[i + l * ld];
+    __syncthreads();
+    for (int j = tid; j < i; j += blockDim.x) {
+      V acc = row[j];
+      for (int l = j + 1; l < i; l++) acc = cmad(row[l], A[l + j * ld], acc);
+      A[i + j * ld] = cneg(acc);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    if (i > j) F[i + int64_t(j) * m] = A[i + j * ld];
+    else if (i == j) F[i + int64_t(j) * m] = dinv[j];
+  }
+}
+
+// Off-diagonal block, 32 rows per task:
+//   W = F21 T^T  (= L21 D), saved to the level scratch for the Schur update,
+//   G = W D^{-1} T  (= F21 F11^{-1} = L21 L11^{-1}), written over F21.
+template <typename V>
+__global__ void __launch_bounds__(256) k_wg(const int2* tasks, const SnDev* sn, const int64_t* scr_off,
+                                            V* fronts, V* scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, r = m - k;
+  V* Fs = reinterpret_cast<V*>(smem_raw);  // 32 x k, ld 32
+  V* Ws = Fs + 32 * k;
+  V* di = Ws + 32 * k;
+  V* F = fronts + S.frontoff;
+  const int R0 = t.y * 32;                 // first row within the off-diagonal part
+  const int nr = min(32, r - R0);
+  const int tid = threadIdx.x, rr = tid & 31, g = tid >> 5;
+  for (int e = tid; e < 32 * k; e += blockDim.x) {
+    const int i = e & 31, j = e >> 5;
+    Fs[e] = (i < nr) ? F[(k + R0 + i) + int64_t(j) * m] : czero<V>();
+  }
+  for (int j = tid; j < k; j += blockDim.x) di[j] = F[j + int64_t(j) * m];
+  __syncthreads();
+  for (int j = g; j < k; j += 8) {
+    V acc = Fs[rr + 32 * j];
+    for (int i = 0; i < j; i++) acc = cmad(Fs[rr + 32 * i], F[j + int64_t(i) * m], acc);
+    Ws[rr + 32 * j] = acc;
+  }
+  __syncthreads();
+  V* W = scratch + scr_off[t.x];
+  for (int e = tid; e < 32 * k; e += blockDim.x) {
+    const int i = e & 31, j = e >> 5;
+    if (i < nr) W[(R0 + i) + int64_t(j) * r] = Ws[e];
+    Fs[e] = cmul(Ws[e], di[j]);             // L21
+  }
+  __syncthreads();
+  for (int j = g; j < k; j += 8) {
+    V acc = Fs[rr + 32 * j];
+    for (int i = j + 1; i < k; i++) acc = cmad(Fs[rr + 32 * i], F[i + int64_t(j) * m], acc);
+    if (rr < nr) F[(k + R0 + rr) + int64_t(j) * m] = acc;
+  }
+}
+
+// Schur update of the contribution block, one 32x32 lower tile per task:
+//   F22[a][b] -= sum_i W[a][i] D^{-1}_i W[b][i].
+template <typename V>
+__global__ void __launch_bounds__(256) k_cb(const int4* tasks, const SnDev* sn, const int64_t* scr_off,
+                                            V* fronts, const V* scratch) {
+  __shared__ V As[16][33];
+  __shared__ V Bs[16][33];
+  const int4 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, r = m - k;
+  const V* W = scratch + scr_off[t.x];
+  V* F = fronts + S.frontoff;
+  const int a0 = t.y * 32, b0 = t.z * 32;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  V acc[2][2];
+  for (int p = 0; p < 2; p++)
+    for (int q = 0; q < 2; q++) acc[p][q] = czero<V>();
+  for (int i0 = 0; i0 < k; i0 += 16) {
+    for (int e = tid; e < 512; e += 256) {
+      const int rr = e & 31, ii = e >> 5;
+      const int i = i0 + ii;
+      V av = czero<V>(), bv = czero<V>();
+      if (i < k) {
+        if (a0 + rr < r) av = W[(a0 + rr) + int64_t(i) * r];
+        if (b0 + rr < r) bv = cmul(W[(b0 + rr) + int64_t(i) * r], F[i + int64_t(i) * m]);
+      }
+      As[ii][rr] = av;
+      Bs[ii][rr] = bv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < 16; ii++) {
+      const V x0 = As[ii][ty * 2], x1 = As[ii][ty * 2 + 1];
+      const V y0 = Bs[ii][tx * 2], y1 = Bs[ii][tx * 2 + 1];
+      acc[0][0] = cmad(x0, y0, acc[0][0]);
+      acc[0][1] = cmad(x0, y1, acc[0][1]);
+      acc[1][0] = cmad(x1, y0, acc[1][0]);
+      acc[1][1] = cmad(x1, y1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < 2; p++)
+    for (int q = 0; q < 2; q++) {
+      const int a = a0 + ty * 2 + p, b = b0 + tx * 2 + q;
+      if (a < r && b < r && a >= b) {
+        const int64_t pos = (k + a) + int64_t(k + b) * m;
+        F[pos] = csub(F[pos], acc[p][q]);
+      }
+    }
+}
+
+template <typename V>
+__global__ void k_panel_copy(const SnDev* sn, const V* fronts, V* panels) {
+  const SnDev S = sn[blockIdx.x];
+  const int64_t cnt = int64_t(S.m) * S.k;
+  const V* src = fronts + S.frontoff;
+  V* dst = panels + S.paneloff;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) dst[e] = src[e];
+}
+
+static size_t diag_smem(int kmax, size_t vs) { return (size_t(kmax + 1) * kmax + 2 * kmax) * vs; }
+static size_t wg_smem(int kmax, size_t vs) { return (size_t(64) * kmax + kmax) * vs; }
+
+template <typename V>
+static void factor_level_t(const FactorDev& F, int lev, V* fronts, V* scratch, DevStatus* status, double tiny,
+                           cudaStream_t st) {
+  // extend-add, one child slot per launch so that no parent entry is written twice
+  for (int q = 0; q < F.max_slot; q++) {
+    const int64_t b = F.h_ea_ptr[int64_t(lev) * F.max_slot + q], e = F.h_ea_ptr[int64_t(lev) * F.max_slot + q + 1];
+    if (e > b) k_extend_add<V><<<unsigned(e - b), 256, 0, st>>>(F.ea_tasks + b, F.sn, F.rel, F.reloff, fronts);
+  }
+  const int64_t nb = F.h_lev_ptr[lev + 1] - F.h_lev_ptr[lev];
+  if (nb == 0) return;
+  const size_t ds = diag_smem(F.maxk, sizeof(V));
+  k_diag<V><<<unsigned(nb), 256, ds, st>>>(F.lev_sn + F.h_lev_ptr[lev], F.sn, fronts, status, tiny);
+  const int64_t wb = F.h_wg_ptr[lev], we = F.h_wg_ptr[lev + 1];
+  if (we > wb)
+    k_wg<V><<<unsigned(we - wb), 256, wg_smem(F.maxk, sizeof(V)), st>>>(F.wg_tasks + wb, F.sn, F.scr_off, fronts,
+                                                                       scratch);
+  const int64_t cbb = F.h_cb_ptr[lev], cbe = F.h_cb_ptr[lev + 1];
+  if (cbe > cbb) k_cb<V><<<unsigned(cbe - cbb), 256, 0, st>>>(F.cb_tasks + cbb, F.sn, F.scr_off, fronts, scratch);
+}
+
+void launch_front_fill(const FactorDev& F, double w, void* fronts, cudaStream_t st) {
+  const int64_t ne = F.nentries;
+  if (ne == 0) return;
+  if (F.precision == 0)
+    k_front_fill<double2><<<grid_for(ne, 256), 256, 0, st>>>(ne, F.epos, F.ek, F.em, F.eb, w, (double2*)fronts);
+  else
+    k_front_fill<float2><<<grid_for(ne, 256), 256, 0, st>>>(ne, F.epos, F.ek, F.em, F.eb, w, (float2*)fronts);
+}
+
+static bool g_attr_done[2] = {false, false};
+static void set_attrs(int prec, int kmax) {
+  if (g_attr_done[prec]) return;
+  const int lim = 227 * 1024;
+  if (prec == 0) {
+    cudaFuncSetAttribute(k_diag<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_wg<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  } else {
+    cudaFuncSetAttribute(k_diag<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_wg<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  }
+  g_attr_done[prec] = true;
+  (void)kmax;
+}
+
+void launch_factor_level(const FactorDev& F, int lev, void* fronts, void* scratch, DevStatus* status,
+                         double tiny, cudaStream_t st) {
+  set_attrs(F.precision, F.maxk);
+  if (F.precision == 0)
+    factor_level_t<double2>(F, lev, (double2*)fronts, (double2*)scratch, status, tiny, st);
+  else
+    factor_level_t<float2>(F, lev, (float2*)fronts, (float2*)scratch, status, tiny, st);
+}
+
+void launch_panel_copy(const FactorDev& F, const void* fronts, cudaStream_t st) {
+  if (F.nsn == 0) return;
+  if (F.precision == 0)
+    k_panel_copy<double2><<<F.nsn, 256, 0, st>>>(F.sn, (const double2*)fronts, (double2*)F.panels);
+  else
+    k_panel_copy<float2><<<F.nsn, 256, 0, st>>>(F.sn, (const float2*)fronts, (float2*)F.panels);
+}
+
+// ---------------------------------------------------------------------------
+// batched supernodal solves  (A_i^{-1}: forward with D^{-1}, then backward)
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, V* dst) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < ntot; q += int64_t(gridDim.x) * blockDim.x)
+    dst[q] = from2<V>(src[gidx[q]]);
+}
+
+// Forward, 64 rows of one supernode per task:
+//   b1 = t[pivots] + children's updates;  rows < k:  z = D^{-1} (T b1);
+//   rows >= k:  u = (children's updates) - G b1.
+constexpr int kFwdRows = 64;
+constexpr int kMaxK = 128;
+template <typename V>
+__global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+                                             const int64_t* cidx, const V* panels, const V* tin, V* zout,
+                                             V* u) {
+  __shared__ V b1[kMaxK];
+  __shared__ V part[4][kFwdRows];
+  const int2 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, tid = threadIdx.x;
+  const int64_t* cp = cptr + S.rowoff;
+  for (int j = tid; j < k; j += blockDim.x) {
+    V acc = tin[S.first + j];
+    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+    b1[j] = acc;
+  }
+  __syncthreads();
+  const int rr = tid & (kFwdRows - 1), cg = tid / kFwdRows;
+  const int r = t.y * kFwdRows + rr;
+  const V* P = panels + S.paneloff;
+  V acc = czero<V>();
+  if (r < m) {
+    const int jmax = min(r, k);
+    for (int j = cg; j < jmax; j += 4) acc = cmad(P[r + int64_t(j) * m], b1[j], acc);
+  }
+  part[cg][rr] = acc;
+  __syncthreads();
+  if (cg == 0 && r < m) {
+    const V tot = cadd(cadd(part[0][rr], part[1][rr]), cadd(part[2][rr], part[3][rr]));
+    if (r < k) {
+      zout[S.first + r] = cmul(P[r + int64_t(r) * m], cadd(b1[r], tot));
+    } else {
+      V b2 = czero<V>();
+      for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+      u[S.uoff + (r - k)] = csub(b2, tot);
+    }
+  }
+}
+
+// Backward, 32 pivot columns of one supernode per task:
+//   x[j] = z[j] + sum_{j<r<k} T[r][j] z[r] - sum_{r>=k} G[r][j] x[row r].
+template <typename V>
+__global__ void __launch_bounds__(256) k_bwd(const int2* tasks, const SnDev* sn, const int32_t* rowlist,
+                                             const V* panels, const V* zin, V* x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* vec = reinterpret_cast<V*>(smem_raw);
+  const int2 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int32_t* rl = rowlist + S.rowoff;
+  for (int r = tid; r < m; r += blockDim.x) vec[r] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
+  __syncthreads();
+  const V* P = panels + S.paneloff;
+  for (int q = 0; q < 4; q++) {
+    const int j = t.y * 32 + wid + 8 * q;
+    if (j >= k) break;
+    V acc = (lane == 0) ? vec[j] : czero<V>();
+    const V* col = P + int64_t(j) * m;
+    for (int r = j + 1 + lane; r < m; r += 32) acc = cmad(col[r], vec[r], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x[S.first + j] = acc;
+  }
+}
+
+template <typename V>
+__global__ void k_prolong(int64_t n, const int64_t* pptr, const int32_t* pidx, const double* pw, const V* xl,
+                          const double2* y, double2* z) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n; g += int64_t(gridDim.x) * blockDim.x) {
+    double2 acc = y ? y[g] : make_double2(0.0, 0.0);
+    for (int64_t q = pptr[g]; q < pptr[g + 1]; q++) {
+      const double2 v = to2(xl[pidx[q]]);
+      acc.x = xfma(pw[q], v.x, acc.x);
+      acc.y = xfma(pw[q], v.y, acc.y);
+    }
+    z[g] = acc;
+  }
+}
+
+template <typename V>
+static void solve_t(const FactorDev& F, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bwd<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  const V* P = (const V*)F.panels;
+  V* t = (V*)F.t_loc;
+  V* z = (V*)F.z_loc;
+  V* x = (V*)F.x_loc;
+  V* u = (V*)F.u_ws;
+  for (int l = 0; l < F.nlev; l++) {
+    const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
+    if (e > b) k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+  }
+  const size_t sm = size_t(F.maxm) * sizeof(V);
+  for (int l = F.nlev - 1; l >= 0; l--) {
+    const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
+    if (e > b) k_bwd<V><<<unsigned(e - b), 256, sm, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x);
+  }
+}
+
+void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st) {
+  if (F.ntot == 0) return;
+  if (F.precision == 0)
+    k_gather<double2><<<grid_for(F.ntot, 256), 256, 0, st>>>(F.ntot, F.gidx, src, (double2*)F.t_loc);
+  else
+    k_gather<float2><<<grid_for(F.ntot, 256), 256, 0, st>>>(F.ntot, F.gidx, src, (float2*)F.t_loc);
+}
+
+void launch_solve(const FactorDev& F, cudaStream_t st) {
+  if (F.precision == 0) solve_t<double2>(F, st);
+  else solve_t<float2>(F, st);
+}
+
+void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st) {
+  if (F.nglob == 0) return;
+  if (F.precision == 0)
+    k_prolong<double2><<<grid_for(F.nglob, 256), 256, 0, st>>>(F.nglob, F.pptr, F.pidx, F.pw,
+                                                               (const double2*)F.x_loc, y, z);
+  else
+    k_prolong<float2><<<grid_for(F.nglob, 256), 256, 0, st>>>(F.nglob, F.pptr, F.pidx, F.pw,
+                                                              (const float2*)F.x_loc, y, z);
+}
+
+// ---------------------------------------------------------------------------
+// sparse matrix-vector products
+// ---------------------------------------------------------------------------
+template <int TPR>
+__global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val,
+                                              const double2* x, const double2* sub, double2* y) {
+  const int lane = threadIdx.x % TPR;
+  const int64_t groups = (int64_t(gridDim.x) * blockDim.x) / TPR;
+  const int64_t g0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / TPR;
+  const int64_t wbase0 = (blockIdx.x * int64_t(blockDim.x) + (threadIdx.x & ~31)) / TPR;
+  for (int64_t off = 0; wbase0 + off < n; off += groups) {
+    const int64_t row = g0 + off;
+    double2 acc = make_double2(0.0, 0.0);
+    if (row < n) {
+      const int64_t e = rp[row + 1];
+      for (int64_t q = rp[row] + lane; q < e; q += TPR) acc = cmad(val[q], x[ci[q]], acc);
+    }
+    for (int o = TPR / 2; o > 0; o >>= 1) acc = cadd(acc, shfl_xor(acc, o, TPR));
+    if (row < n && lane == 0) y[row] = sub ? csub(sub[row], acc) : acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci,
+                                                   const double* val, const double2* x, double2* y) {
+  constexpr int TPR = 4;
+  const int lane = threadIdx.x % TPR;
+  const int64_t groups = (int64_t(gridDim.x) * blockDim.x) / TPR;
+  const int64_t g0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / TPR;
+  const int64_t wbase0 = (blockIdx.x * int64_t(blockDim.x) + (threadIdx.x & ~31)) / TPR;
+  for (int64_t off = 0; wbase0 + off < n; off += groups) {
+    const int64_t row = g0 + off;
+    double2 acc = make_double2(0.0, 0.0);
+    if (row < n) {
+      const int64_t e = rp[row + 1];
+      for (int64_t q = rp[row] + lane; q < e; q += TPR) {
+        const double2 v = x[ci[q]];
+        acc.x = xfma(val[q], v.x, acc.x);
+        acc.y = xfma(val[q], v.y, acc.y);
+      }
+    }
+    for (int o = TPR / 2; o > 0; o >>= 1) acc = cadd(acc, shfl_xor(acc, o, TPR));
+    if (row < n && lane == 0) y[row] = acc;
+  }
+}
+
+void launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
+                 const double2* sub, double2* y, cudaStream_t st) {
+  if (n == 0) return;
+  k_spmv<8><<<grid_for(n * 8, 256, 152 * 32), 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+}
+
+void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, const double2* x,
+                      double2* y, cudaStream_t st) {
+  if (n == 0) return;
+  k_spmv_real<<<grid_for(n * 4, 256, 152 * 32), 256, 0, st>>>(n, rp, ci, val, x, y);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES: fused CGS passes and small dense updates
+// ---------------------------------------------------------------------------
+constexpr int kCgsRows = 32;
+constexpr int kMaxCols = 64;
+constexpr int kPartStride = kMaxCols + 1;
+int cgs_blocks() { return 152 * 4; }
+
+// One pass over V (n x ncols, column-major, ld ldv) and w:
+//   if h: w <- w - V h (in place);  partial[b][j] = sum conj(V[:,j]) w  (j < ndot);
+//   partial[b][64] = sum |w|^2.
+__global__ void __launch_bounds__(256) k_cgs(int64_t n, int ncols, const double2* V, int64_t ldv,
+                                             const double2* h, double2* w, int ndot, double2* partial,
+                                             int64_t chunk) {
+  __shared__ double2 Vt[kCgsRows * kMaxCols];
+  __shared__ double2 hs[kMaxCols];
+  __shared__ double2 red[8][kCgsRows];
+  __shared__ double2 ws[kCgsRows];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t row0 = blockIdx.x * chunk;
+  const int64_t row1 = min(n, row0 + chunk);
+  const int nld = h ? ncols : ndot;
+  if (h)
+    for (int j = tid; j < ncols; j += blockDim.x) hs[j] = h[j];
+  double2 acc[8];
+  for (int q = 0; q < 8; q++) acc[q] = make_double2(0.0, 0.0);
+  double nrm = 0.0;
+  for (int64_t base = row0; base < row1; base += kCgsRows) {
+    const int nr = int(min(int64_t(kCgsRows), row1 - base));
+    for (int e = tid; e < kCgsRows * nld; e += blockDim.x) {
+      const int r = e % kCgsRows, j = e / kCgsRows;
+      Vt[e] = (r < nr) ? V[base + r + int64_t(j) * ldv] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (h) {
+      double2 p = make_double2(0.0, 0.0);
+      for (int j = wid; j < ncols; j += 8) p = cmad(Vt[lane + kCgsRows * j], hs[j], p);
+      red[wid][lane] = p;
+      __syncthreads();
+      if (wid == 0) {
+        double2 s = red[0][lane];
+        for (int q = 1; q < 8; q++) s = cadd(s, red[q][lane]);
+        double2 wv = make_double2(0.0, 0.0);
+        if (lane < nr) {
+          wv = csub(w[base + lane], s);
+          w[base + lane] = wv;
+        }
+        ws[lane] = wv;
+      }
+    } else if (wid == 0) {
+      ws[lane] = (lane < nr) ? w[base + lane] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const double2 wl = ws[lane];
+    for (int q = 0; q < 8; q++) {
+      const int j = wid + 8 * q;
+      if (j < ndot) acc[q] = cmadc(Vt[lane + kCgsRows * j], wl, acc[q]);
+    }
+    if (wid == 0) nrm = xfma(wl.x, wl.x, xfma(wl.y, wl.y, nrm));
+    __syncthreads();
+  }
+  double2* out = partial + int64_t(blockIdx.x) * kPartStride;
+  for (int q = 0; q < 8; q++) {
+    const int j = wid + 8 * q;
+    const double2 v = warp_sum(acc[q]);
+    if (lane == 0 && j < kMaxCols) out[j] = (j < ndot) ? v : make_double2(0.0, 0.0);
+  }
+  if (wid == 0) {
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (lane == 0) out[kMaxCols] = make_double2(nrm, 0.0);
+  }
+}
+
+void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const double2* h, double2* w, int ndot,
+                double2* partial, cudaStream_t st) {
+  const int nb = cgs_blocks();
+  int64_t chunk = (n + nb - 1) / nb;
+  chunk = (chunk + kCgsRows - 1) / kCgsRows * kCgsRows;
+  k_cgs<<<nb, 256, 0, st>>>(n, ncols, V, ldv, h, w, ndot, partial, chunk);
+}
+
+__global__ void k_reduce(const double2* partial, int nblk, double2* out) {
+  const int j = threadIdx.x;
+  if (j > kMaxCols) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < nblk; b++) s = cadd(s, partial[int64_t(b) * kPartStride + j]);
+  out[j] = s;
+}
+
+void launch_reduce(const double2* partial, int nblk, int ncols, double2* out, cudaStream_t st) {
+  (void)ncols;
+  k_reduce<<<1, 96, 0, st>>>(partial, nblk, out);
+}
+
+// Complex Givens rotation zeroing b: rho = sqrt(|a|^2+|b|^2), c = |a|/rho,
+// s = (a/|a|) conj(b)/rho; a = 0 gives c = 0, s = 1.
+__device__ void givens_cs(double2 a, double2 b, double& c, double2& s) {
+  const double aa = sqrt(a.x * a.x + a.y * a.y);
+  if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+    return;
+  }
+  const double bb = sqrt(b.x * b.x + b.y * b.y);
+  const double rho = sqrt(aa * aa + bb * bb);
+  c = aa / rho;
+  const double2 u = make_double2(a.x / aa, a.y / aa);
+  const double2 bc = make_double2(b.x / rho, -b.y / rho);
+  s = cmul(u, bc);
+}
+
+__global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
+                         const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown,
+                         double* invh) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2* col = H + int64_t(j) * (m + 1);
+  for (int i = 0; i <= j; i++) col[i] = cadd(h1[i], h2[i]);
+  const double w0 = sqrt(h1[kMaxCols].x);
+  const double hn = sqrt(nrm[kMaxCols].x);
+  col[j + 1] = make_double2(hn, 0.0);
+  for (int i = 0; i < j; i++) {
+    const double2 a = col[i], b = col[i + 1];
+    const double2 sc = make_double2(sn[i].x, -sn[i].y);
+    col[i] = cadd(make_double2(cs[i] * a.x, cs[i] * a.y), cmul(sn[i], b));
+    col[i + 1] = csub(make_double2(cs[i] * b.x, cs[i] * b.y), cmul(sc, a));
+  }
+  double c;
+  double2 s;
+  givens_cs(col[j], col[j + 1], c, s);
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = cadd(make_double2(c * col[j].x, c * col[j].y), cmul(s, col[j + 1]));
+  col[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = g[j];
+  const double2 sc = make_double2(-s.x, s.y);   // -conj(s)
+  g[j + 1] = cmul(sc, gj);
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  *est = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / bnorm;
+  *breakdown = (hn <= 1e-14 * w0) ? 1 : 0;
+  *invh = 1.0 / hn;
+}
+
+void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
+                   const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown, double* invh,
+                   cudaStream_t st) {
+  k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, h1, h2, nrm, bnorm, est, breakdown, invh);
+}
+
+__global__ void k_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta) {
+  const double b = sqrt(nrm2[kMaxCols].x);
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = make_double2(i == 0 ? b : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    *beta = b;
+    *invbeta = 1.0 / b;
+  }
+}
+
+void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta, cudaStream_t st) {
+  k_init_cycle<<<1, 64, 0, st>>>(nrm2, g, m, invbeta, beta);
+}
+
+__global__ void k_scale(int64_t n, const double2* w, const double* s, double2* out) {
+  const double a = *s;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = make_double2(w[i].x * a, w[i].y * a);
+}
+
+void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st) {
+  k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, w, s, out);
+}
+
+// y = R^{-1} g (upper triangular k x k of the rotated Hessenberg matrix)
+__global__ void k_backsub(int k, const double2* H, int ldh, const double2* g, double2* y) {
+  if (threadIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; i--) {
+    double2 s = g[i];
+    for (int l = i + 1; l < k; l++) s = cmsub(H[i + int64_t(l) * ldh], y[l], s);
+    const double2 d = H[i + int64_t(i) * ldh];
+    y[i] = cmul(s, cinv(d));
+  }
+}
+
+__global__ void k_gemv_add(int64_t n, int k, const double2* y, const double2* Zs, int64_t ldz, double2* x) {
+  __shared__ double2 ys[kMaxCols];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    double2 acc = x[r];
+    for (int j = 0; j < k; j++) acc = cmad(Zs[r + int64_t(j) * ldz], ys[j], acc);
+    x[r] = acc;
+  }
+}
+
+void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y, const double2* Zs,
+                     int64_t ldz, double2* x, cudaStream_t st) {
+  k_backsub<<<1, 32, 0, st>>>(k, H, ldh, g, y);
+  k_gemv_add<<<grid_for(n, 256), 256, 0, st>>>(n, k, y, Zs, ldz, x);
+}
+
+__global__ void k_copy(int64_t n, const double2* a, double2* out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = a[i];
+}
+
+void launch_axpby_copy(int64_t n, const double2* a, double2* out, cudaStream_t st) {
+  k_copy<<<grid_for(n, 256), 256, 0, st>>>(n, a, out);
+}
+
+}  // namespace hz

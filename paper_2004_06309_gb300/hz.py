@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the hz C ABI (``include/hz.h``).
+
+Argument marshalling only: every step of setup, factorisation and solve runs in
+``libhz.so``.  Importing this module loads the library and raises if it is
+missing -- there is no fallback path.  PyTorch is used only for device memory
+and streams (CUDA tensors are passed by ``data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhz.so")
+
+HZ_OK = 0
+HZ_ERR_ARG = 1
+HZ_ERR_STATE = 2
+HZ_ERR_OOM = 3
+HZ_ERR_CUDA = 4
+HZ_ERR_ZERO_PIVOT = 5
+HZ_ERR_BREAKDOWN = 6
+HZ_ERR_NOT_CONVERGED = 7
+HZ_ERR_TIMEOUT = 8
+HZ_FP64 = 0
+HZ_MIXED = 1
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [
+        ("nv", C.c_int64), ("ne", C.c_int64), ("nf", C.c_int64),
+        ("xyz", C.c_void_p), ("tets", C.c_void_p), ("faces", C.c_void_p),
+        ("face_tag", C.c_void_p), ("c_re", C.c_void_p), ("c_im", C.c_void_p),
+        ("order", C.c_int32),
+        ("coarse_nv", C.c_int64), ("coarse_ne", C.c_int64), ("coarse_nf", C.c_int64),
+        ("coarse_xyz", C.c_void_p), ("coarse_tets", C.c_void_p), ("coarse_faces", C.c_void_p),
+        ("coarse_face_tag", C.c_void_p), ("fine_parent", C.c_void_p),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("nsub", C.c_int32), ("overlap", C.c_int32), ("levels", C.c_int32),
+        ("restart", C.c_int32), ("precision", C.c_int32), ("max_iter", C.c_int32),
+        ("leaf_size", C.c_int32), ("max_snode", C.c_int32),
+        ("hbm_budget", C.c_uint64), ("elem_part", C.c_void_p), ("stream", C.c_void_p),
+    ]
+
+
+class RhsInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_residual", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("nnz", C.c_int64), ("n_coarse", C.c_int64), ("nnz_coarse", C.c_int64),
+        ("sum_ni", C.c_int64), ("nnz_local", C.c_int64), ("nnz_factor", C.c_int64),
+        ("nnz_factor_coarse", C.c_int64), ("nsupernodes", C.c_int64), ("nlevels", C.c_int32),
+        ("nlevels_coarse", C.c_int32), ("front_bytes", C.c_int64), ("device_bytes", C.c_int64),
+        ("factor_flops", C.c_double), ("setup_seconds", C.c_double), ("factor_seconds", C.c_double),
+        ("min_pivot", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every exported symbol and its signature: (restype, argtypes).
+SIGNATURES = {
+    "hz_setup_mesh": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+    "hz_factor": (C.c_int, [C.c_void_p, C.c_double]),
+    "hz_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
+                           C.POINTER(RhsInfo)]),
+    "hz_point_sources": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "hz_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hz_apply_M": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hz_plan": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(Options), C.POINTER(Stats)]),
+    "hz_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "hz_ndofs": (C.c_int64, [C.c_void_p]),
+    "hz_status_string": (C.c_char_p, [C.c_int]),
+    "hz_last_error": (C.c_char_p, [C.c_void_p]),
+    "hz_free": (None, [C.c_void_p]),
+}
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhz.so not built ({path}); run paper_2004_06309_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+class HzError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class _MeshArrays:
+    """Owns contiguous copies of the mesh arrays for the duration of a call."""
+
+    def __init__(self, mesh, c, order, coarse=None, fine_parent=None):
+        self.xyz = _c(mesh.xyz, np.float64)
+        self.tets = _c(mesh.tets, np.int32)
+        self.faces = _c(mesh.faces, np.int32)
+        self.tag = _c(mesh.face_tag, np.int8)
+        c = np.asarray(c, np.complex128)
+        self.cre = _c(c.real, np.float64)
+        self.cim = _c(c.imag, np.float64)
+        d = MeshDesc()
+        d.nv, d.ne, d.nf = len(self.xyz), len(self.tets), len(self.faces)
+        d.xyz, d.tets, d.faces, d.face_tag = _ptr(self.xyz), _ptr(self.tets), _ptr(self.faces), _ptr(self.tag)
+        d.c_re, d.c_im = _ptr(self.cre), _ptr(self.cim)
+        d.order = int(order)
+        if coarse is not None:
+            self.cxyz = _c(coarse.xyz, np.float64)
+            self.ctets = _c(coarse.tets, np.int32)
+            self.cfaces = _c(coarse.faces, np.int32)
+            self.ctag = _c(coarse.face_tag, np.int8)
+            self.parent = _c(fine_parent, np.int32)
+            d.coarse_nv, d.coarse_ne, d.coarse_nf = len(self.cxyz), len(self.ctets), len(self.cfaces)
+            d.coarse_xyz, d.coarse_tets = _ptr(self.cxyz), _ptr(self.ctets)
+            d.coarse_faces, d.coarse_face_tag = _ptr(self.cfaces), _ptr(self.ctag)
+            d.fine_parent = _ptr(self.parent)
+        self.desc = d
+
+
+def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=2000, leaf_size=0,
+                 max_snode=0, hbm_budget=0, elem_part=None, stream=0):
+    o = Options()
+    o.nsub, o.overlap, o.levels, o.restart = int(nsub), int(overlap), int(levels), int(restart)
+    o.precision, o.max_iter = int(precision), int(max_iter)
+    o.leaf_size, o.max_snode = int(leaf_size), int(max_snode)
+    o.hbm_budget = int(hbm_budget)
+    part = None if elem_part is None else _c(elem_part, np.int32)
+    o.elem_part = _ptr(part)
+    o.stream = int(stream) if stream else None
+    return o, part
+
+
+def _problem_args(p):
+    coarse = p.coarse if p.levels == 2 else None
+    parent = p.fine_parent if p.levels == 2 else None
+    return _MeshArrays(p.mesh, p.c, p.order, coarse, parent)
+
+
+def plan(problem, precision=HZ_FP64, use_partition=True, **kw):
+    """Host-only analysis of ``problem``: sizes and device bytes (no GPU needed)."""
+    ma = _problem_args(problem)
+    o, part = make_options(problem.nsub, problem.overlap, problem.levels, problem.restart, precision,
+                           elem_part=problem.elem_part if use_partition else None, **kw)
+    st = Stats()
+    s = lib().hz_plan(C.byref(ma.desc), C.byref(o), C.byref(st))
+    if s != HZ_OK:
+        raise HzError(s, "hz_plan failed: " + lib().hz_status_string(s).decode())
+    return st.as_dict()
+
+
+class Solver:
+    """One context: mesh + decomposition + factors + Krylov workspace on the GPU."""
+
+    def __init__(self, problem, precision=HZ_FP64, stream=None, use_partition=True, **kw):
+        import torch  # device memory and streams only
+        self.torch = torch
+        self.problem = problem
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ma = _problem_args(problem)
+        o, part = make_options(problem.nsub, problem.overlap, problem.levels, problem.restart,
+                               precision, elem_part=problem.elem_part if use_partition else None,
+                               stream=self.stream.cuda_stream, **kw)
+        h = C.c_void_p()
+        s = lib().hz_setup_mesh(C.byref(ma.desc), C.byref(o), C.byref(h))
+        if s != HZ_OK:
+            raise HzError(s, "hz_setup_mesh failed: " + lib().hz_status_string(s).decode())
+        self.h = h
+        self.n = int(lib().hz_ndofs(h))
+
+    def _check(self, s, what):
+        if s not in (HZ_OK,):
+            msg = lib().hz_last_error(self.h).decode()
+            raise HzError(s, f"{what}: {lib().hz_status_string(s).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hz_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factor(self, freq=None):
+        freq = self.problem.freq if freq is None else freq
+        self._check(lib().hz_factor(self.h, float(freq)), "hz_factor")
+
+    def stats(self):
+        st = Stats()
+        self._check(lib().hz_get_stats(self.h, C.byref(st)), "hz_get_stats")
+        return st.as_dict()
+
+    def point_sources(self, pts=None, device=False):
+        pts = self.problem.sources if pts is None else pts
+        pts = _c(np.atleast_2d(pts), np.float64)
+        if device:
+            out = self.torch.empty((len(pts), self.n), dtype=self.torch.complex128, device="cuda")
+            self._check(lib().hz_point_sources(self.h, _ptr(pts), len(pts), C.c_void_p(out.data_ptr()), 1),
+                        "hz_point_sources")
+            return out.T
+        out = np.zeros((len(pts), self.n), np.complex128)
+        self._check(lib().hz_point_sources(self.h, _ptr(pts), len(pts), _ptr(out), 0), "hz_point_sources")
+        return out.T
+
+    def solve(self, B, tol=None, check=True):
+        """B: (n,) or (n, nrhs) numpy (host path) or CUDA tensor (device path).
+        Returns (X, list of (iterations, status, rel_residual))."""
+        tol = self.problem.tol if tol is None else tol
+        torch = self.torch
+        one = B.ndim == 1
+        if isinstance(B, np.ndarray):
+            Bc = np.asfortranarray(B.reshape(self.n, -1).astype(np.complex128))
+            nrhs = Bc.shape[1]
+            X = np.zeros((self.n, nrhs), np.complex128, order="F")
+            info = (RhsInfo * nrhs)()
+            s = lib().hz_solve(self.h, _ptr(Bc), nrhs, float(tol), _ptr(X), 0, info)
+        else:
+            Bt = B.reshape(self.n, -1).to(torch.complex128).T.contiguous()   # (nrhs, n) = column-major
+            nrhs = Bt.shape[0]
+            Xt = torch.empty_like(Bt)
+            info = (RhsInfo * nrhs)()
+            s = lib().hz_solve(self.h, C.c_void_p(Bt.data_ptr()), nrhs, float(tol),
+                               C.c_void_p(Xt.data_ptr()), 1, info)
+            X = Xt.T
+        if check and s not in (HZ_OK, HZ_ERR_NOT_CONVERGED):
+            self._check(s, "hz_solve")
+        inf = [(info[j].iterations, info[j].status, info[j].rel_residual) for j in range(nrhs)]
+        if one:
+            X = X[:, 0]
+        return X, inf
+
+    def apply_A(self, x):
+        y = self.torch.empty_like(x)
+        self._check(lib().hz_apply_A(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())), "hz_apply_A")
+        return y
+
+    def apply_M(self, v):
+        z = self.torch.empty_like(v)
+        self._check(lib().hz_apply_M(self.h, C.c_void_p(v.data_ptr()), C.c_void_p(z.data_ptr())), "hz_apply_M")
+        return z

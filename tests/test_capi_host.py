@@ -1,0 +1,80 @@
+"""CPU-only checks of the C ABI: the library builds, loads, exports every symbol
+declared in include/hz.h, and its host-side analysis (hz_plan) agrees with the
+oracle's dof counts and decomposition sizes.  No device call is made."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dd, fem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hzmod():
+    from paper_2004_06309_gb300 import build, hz
+    build.build()
+    return hz
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hz.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hz_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(hzmod):
+    lib = hzmod.load()
+    names = declared_symbols()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in hzmod.SIGNATURES, name
+
+
+def test_status_strings(hzmod):
+    lib = hzmod.lib()
+    assert lib.hz_status_string(0) == b"ok"
+    assert lib.hz_status_string(5) == b"zero pivot"
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.tiny_problem(),
+    lambda: synth.unit_cube_problem(n=6, order=2, nsub=4, overlap=2),
+    lambda: synth.small_overthrust(levels=2, cells=(3, 3, 2), freq=0.8, nsub=4),
+])
+def test_plan_matches_oracle_sizes(hzmod, make):
+    p = make()
+    st = hzmod.plan(p)
+    A, dm, dd_ = fem.global_system(p)
+    assert st["n"] == dm.n
+    subs = dd.grow_subdomains(p.mesh, p.elem_part, p.nsub, p.overlap, dm)
+    assert st["sum_ni"] == sum(len(s.dofs) for s in subs)
+    # nnz of A counts the element pattern (explicit zeros kept on Dirichlet couplings)
+    assert st["nnz"] >= A.nnz
+    assert st["nnz_factor"] > 0 and st["nsupernodes"] > 0
+    if p.levels == 2:
+        from oracle import coarse
+        Z, cdm, keep = coarse.interpolation(p, dm)
+        assert st["n_coarse"] == Z.shape[1]
+
+
+def test_plan_rejects_bad_options(hzmod):
+    bad = synth.tiny_problem()
+    bad.restart = 0
+    with pytest.raises(hzmod.HzError):
+        hzmod.plan(bad)
+    p2 = synth.tiny_problem()
+    p2.levels = 2          # no coarse mesh given
+    with pytest.raises(hzmod.HzError):
+        hzmod.plan(p2)
+
+
+def test_plan_builtin_partition(hzmod):
+    p = synth.tiny_problem()
+    a = hzmod.plan(p, use_partition=True)
+    b = hzmod.plan(p, use_partition=False)   # the library's own coordinate bisection
+    assert a["sum_ni"] == b["sum_ni"]

@@ -1,0 +1,150 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (FP64 path): the operator A is the same sum of element terms on both
+sides, so A x agrees to 1e-13 relative; M^{-1} differs only by the rounding of
+two different direct solvers (supernodal LDL^T without pivoting on the GPU,
+SuperLU on the CPU), 1e-10 relative; full solves at tol 1e-6 follow the same
+Krylov path, so the solutions agree to <= 1e-9 relative L2 and the iteration
+counts within +-1.  Mixed path: the true residual ||b - A x|| / ||b|| computed
+with the oracle's FP64 operator is <= tol.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle.solver import OracleSolver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hzmod():
+    from paper_2004_06309_gb300 import build, hz
+    build.build()
+    return hz
+
+
+def _rand(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+def _cases():
+    return {
+        "tiny": synth.tiny_problem,
+        "cube_p2_ragged": lambda: synth.unit_cube_problem(n=10, order=2, nsub=6, overlap=2, freq=1.5),
+        "ovt_2lvl": lambda: synth.small_overthrust(levels=2, cells=(5, 5, 3), freq=0.6, nsub=16),
+    }
+
+
+@pytest.fixture(scope="module", params=list(_cases().keys()))
+def pair(request, hzmod):
+    p = _cases()[request.param]()
+    S = OracleSolver(p)
+    S.factor()
+    G = hzmod.Solver(p)
+    G.factor()
+    yield p, S, G
+    G.close()
+
+
+def test_apply_A_matches_oracle(pair):
+    import torch
+    p, S, G = pair
+    x = _rand(S.n, 1)
+    y = G.apply_A(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = S.apply_A(x)
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_apply_M_matches_oracle(pair):
+    import torch
+    p, S, G = pair
+    v = _rand(S.n, 2)
+    z = G.apply_M(torch.from_numpy(v).cuda()).cpu().numpy()
+    ref = S.apply_M(v)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= 1e-10, err
+
+
+def test_solve_matches_oracle(pair):
+    p, S, G = pair
+    b = S.rhs()[:, 0]
+    xo, ito, relo, ok = S.solve(b)
+    assert ok
+    xg, info = G.solve(b)
+    itg, st, relg = info[0]
+    assert st == 0 and relg <= p.tol
+    assert abs(itg - ito) <= 1, (itg, ito)
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert err <= 1e-9, err
+    # true residual with the oracle's operator
+    assert np.linalg.norm(b - S.A @ xg) / np.linalg.norm(b) <= p.tol
+
+
+def test_device_path_and_multiple_rhs(pair):
+    import torch
+    p, S, G = pair
+    B = S.rhs(np.array([[0.3, 0.4, 0.5], [0.6, 0.35, 0.25]]) * (p.mesh.xyz.max(axis=0)))
+    X, info = G.solve(torch.from_numpy(B).cuda())
+    X = X.cpu().numpy()
+    for j in range(2):
+        assert info[j][1] == 0
+        assert np.linalg.norm(B[:, j] - S.A @ X[:, j]) / np.linalg.norm(B[:, j]) <= p.tol
+
+
+def test_point_sources_match_oracle(pair):
+    p, S, G = pair
+    pts = np.array([[0.31, 0.47, 0.52]]) * p.mesh.xyz.max(axis=0)
+    bg = G.point_sources(pts)
+    bo = S.rhs(pts)
+    assert np.abs(bg - bo).max() <= 1e-13
+
+
+def test_rerun_is_bitwise_identical(pair):
+    p, S, G = pair
+    b = S.rhs()[:, 0]
+    x1, i1 = G.solve(b)
+    x2, i2 = G.solve(b)
+    assert np.array_equal(x1, x2) and i1 == i2
+
+
+def test_mixed_precision_reaches_tolerance(hzmod):
+    p = synth.small_overthrust(levels=2, cells=(5, 5, 3), freq=0.6, nsub=16)
+    S = OracleSolver(p)
+    S.factor()
+    b = S.rhs()[:, 0]
+    xo, ito, _, _ = S.solve(b)
+    G = hzmod.Solver(p, precision=hzmod.HZ_MIXED)
+    G.factor()
+    xg, info = G.solve(b)
+    assert info[0][1] == 0
+    assert np.linalg.norm(b - S.A @ xg) / np.linalg.norm(b) <= p.tol
+    assert abs(info[0][0] - ito) <= max(2, ito // 5)
+    G.close()
+
+
+def test_edge_cases(hzmod):
+    p = synth.tiny_problem()
+    G = hzmod.Solver(p)
+    b = np.zeros(G.n, np.complex128)
+    with pytest.raises(hzmod.HzError) as e:
+        G.solve(b)
+    assert e.value.status == hzmod.HZ_ERR_STATE
+    G.factor()
+    x, info = G.solve(b)                       # zero right-hand side
+    assert np.all(x == 0) and info[0][0] == 0
+    bad = np.full(G.n, np.nan + 0j)
+    x, info = G.solve(bad, check=False)
+    assert info[0][1] == hzmod.HZ_ERR_BREAKDOWN
+    G.close()
+
+
+def test_one_subdomain_is_one_iteration(hzmod):
+    p = synth.unit_cube_problem(n=6, nsub=1, overlap=0)
+    G = hzmod.Solver(p)
+    G.factor()
+    S = OracleSolver(p)
+    x, info = G.solve(S.rhs()[:, 0])
+    assert info[0][0] == 1 and info[0][2] < 1e-10
+    G.close()
