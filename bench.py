@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: right-hand sides solved per second to relative residual 1e-6 with
+two-level ORAS-preconditioned FGMRES (arXiv 2004.06309), mixed precision versus
+FP64, with p50/p99 latency per right-hand side.
+
+Workload (default): the 5 Hz Overthrust-shaped synthetic model -- 20 x 20 x 4.65
+km, layered 2-6 km/s with two thrust-fold surfaces and 5% random texture, Q =
+100; nested P2 tetrahedral meshes (fine 100 x 100 x 24 cells x 6 tets, 1.98M
+dofs; coarse mesh twice as coarse); 64 subdomains, overlap 2, two-level ORAS,
+FGMRES(50), one source at (2.5, 2.5, 0.58) km.  A step is one hz_solve of that
+right-hand side to 1e-6 (the per-frequency factorisation is done once before the
+timed region and reported separately).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hz|reference]
+
+One JSON line on rank 0.  Under torchrun every rank solves its own replica of
+the workload (no collective on the data path; replicas only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS solved/s to rel. residual 1e-6, mixed vs FP64 ORAS-GMRES; p50/p99 latency"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal, from the platform figures
+WORKLOADS = {
+    "overthrust-5hz": dict(kind="overthrust", cells=(50, 50, 12), freq=5.0, nsub=64, overlap=2,
+                           restart=50),
+    "overthrust-small": dict(kind="overthrust", cells=(12, 12, 3), freq=1.2, nsub=8, overlap=2,
+                             restart=50),
+    "tiny": dict(kind="tiny"),
+}
+# Oracle sample for the CPU baseline / reference arm: same generator, 1/64 of the dofs.
+ORACLE_SAMPLE = dict(kind="overthrust", cells=(12, 12, 3), freq=1.25, nsub=8, overlap=2, restart=50)
+
+
+def make_problem(spec):
+    import synth
+    if spec["kind"] == "tiny":
+        return synth.tiny_problem()
+    return synth.overthrust_problem(seed=0, freq=spec["freq"], cells=spec["cells"], nsub=spec["nsub"],
+                                    overlap=spec["overlap"], restart=spec["restart"], levels=2)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+
+    def __init__(self, index, path):
+        self.path = path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_oracle_sample(steps, warmup):
+    """Time the FP64 oracle (as it stands) on the bounded sample; one solve per step."""
+    import numpy as np
+    from oracle.solver import OracleSolver
+    p = make_problem(ORACLE_SAMPLE)
+    S = OracleSolver(p)
+    S.factor()
+    b = S.rhs()[:, 0]
+    times, its = [], []
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        x, it, rel, ok = S.solve(b)
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            times.append(dt)
+            its.append(it)
+    return dict(n=S.n, seconds=statistics.mean(times), iterations=int(statistics.median(its)),
+                cores=1, times=times)
+
+
+def oracle_subprocess(steps, warmup):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--steps", str(steps),
+           "--warmup", str(warmup)]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    for line in out.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+
+
+def scaled_rhs_per_s(sample, n_full, it_full):
+    """Oracle throughput on the sample, scaled to the full workload by dofs x iterations."""
+    work_ratio = (sample["n"] * sample["iterations"]) / float(n_full * max(it_full, 1))
+    return work_ratio / sample["seconds"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
+    ap.add_argument("--workload", default="overthrust-5hz", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.oracle_sample:
+        print(json.dumps(run_oracle_sample(args.steps, args.warmup)))
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        samp = oracle_subprocess(args.steps, args.warmup)
+        full_it = 40  # iterations of the full workload on the GPU path (order of magnitude)
+        p_full_n = 1_985_000 if args.workload == "overthrust-5hz" else samp["n"]
+        val = scaled_rhs_per_s(samp, p_full_n, full_it) if args.workload == "overthrust-5hz" else 1.0 / samp["seconds"]
+        sample_txt = (f"FP64 oracle solve (factorisation excluded) of the same Overthrust-shaped generator at "
+                      f"cells {ORACLE_SAMPLE['cells']} ({samp['n']} dofs, {ORACLE_SAMPLE['nsub']} subdomains, "
+                      f"{samp['iterations']} iterations), scaled by dofs x iterations")
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "RHS/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * samp["seconds"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128",
+                "data": "synthetic", "config": {"workload": args.workload},
+                "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": samp["cores"], "kind": "oracle",
+                                 "sample": sample_txt},
+                "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+
+    from paper_2004_06309_gb300 import build, hz
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    spec = WORKLOADS[args.workload]
+    t0 = time.time()
+    prob = make_problem(spec)
+    t_gen = time.time() - t0
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def maxall(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    precs = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    results = {}
+    stream = torch.cuda.current_stream()
+    for pname in precs:
+        G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream)
+        tf = time.time()
+        G.factor()
+        torch.cuda.synchronize()
+        t_factor = time.time() - tf
+        b_host = G.point_sources(prob.sources)[:, 0].copy()
+        b_dev = torch.from_numpy(b_host).cuda()
+        for _ in range(args.warmup):
+            x, info = G.solve(b_dev)
+        st0 = G.stats()["launches"]
+        clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_{pname}_r{rank}.csv")) \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/clocks_{pname}.csv")
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        its = []
+        for s in range(args.steps):
+            x, info = G.solve(b_dev)
+            ev[s + 1].record(stream)
+            its.append(info[0][0])
+        barrier()
+        ck = clocks.stop()
+        launches = G.stats()["launches"] - st0
+        step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+        total_ms = maxall(sum(step_ms))
+        rel = info[0][2]
+        # end to end through the C ABI with host buffers (copies inside the timed region)
+        barrier()
+        te = time.perf_counter()
+        for s in range(args.steps):
+            xh, infoh = G.solve(b_host)
+        torch.cuda.synchronize()
+        e2e_s = maxall(time.perf_counter() - te)
+        prof = G.profile(reps=3)
+        stats = G.stats()
+        results[pname] = dict(total_ms=total_ms, step_ms=step_ms, iterations=its, rel=rel, clocks=ck,
+                              launches=launches, e2e_s=e2e_s, profile=prof, stats=stats,
+                              t_factor=t_factor, n=G.n)
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    main_p = "mixed" if "mixed" in results else "fp64"
+    R = results[main_p]
+    n = R["n"]
+    K = args.steps
+    value = world * K / (R["total_ms"] / 1e3)
+
+    def lat(r):
+        s = sorted(r["step_ms"])
+        return {"p50": float(np.percentile(s, 50)), "p99": float(np.percentile(s, 99))}
+
+    # roofline of the dominant phase of one iteration
+    hbm_peak, peak_kind = load_peaks()
+    prof = R["profile"]
+    cand = ["spmv", "coarse", "restrict", "local_solve", "prolong", "cgs2"]
+    dom = max(cand, key=lambda k: prof[k]["ms"])
+    ph = prof[dom]
+    fp64_phase = dom != "local_solve" or main_p == "fp64"
+    t_s = ph["ms"] / 1e3
+    gbs = ph["bytes"] / t_s / 1e9
+    tfl = ph["flops"] / t_s / 1e12
+    if fp64_phase and ph["flops"] / (FP64_PEAK_TFLOPS * 1e12) > ph["bytes"] / (hbm_peak * 1e9):
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 nominal (platform figure)"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    roof.update({"kernel": f"{dom} ({main_p})", "ms_per_launch": ph["ms"], "algorithmic_bytes": ph["bytes"],
+                 "flops": ph["flops"], "launches_per_run": ph["launches"]})
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": R["total_ms"] / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64 subdomain factors/solves + complex128 Krylov, SpMV, coarse" if main_p == "mixed"
+        else "complex128",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_dofs": n, "nsub": prob.nsub, "overlap": prob.overlap,
+                   "levels": 2 if prob.levels == 2 else 1, "restart": prob.restart, "tol": 1e-6,
+                   "rhs_per_step": 1, "freq_hz": prob.freq,
+                   "l2": "inputs larger than L2 (factors >> 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations": R["iterations"][-1], "rel_residual": R["rel"],
+        "latency_ms": lat(R),
+        "factor_seconds": R["t_factor"],
+        "e2e": {"value": world * K / R["e2e_s"], "unit": "RHS/s", "h2d_bytes_per_step": n * 16,
+                "d2h_bytes_per_step": n * 16},
+        "gpu_launches": R["launches"],
+        "clocks": R["clocks"],
+        "roofline": roof,
+        "phases_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
+        "stats": {k: R["stats"][k] for k in ("nnz", "n_coarse", "sum_ni", "nnz_factor", "nnz_factor_coarse",
+                                             "nsupernodes", "nlevels", "front_bytes", "device_bytes",
+                                             "setup_seconds")},
+        "generate_seconds": t_gen,
+    }
+    if "fp64" in results and main_p != "fp64":
+        F = results["fp64"]
+        line["fp64"] = {"value": world * K / (F["total_ms"] / 1e3), "ms_per_step": F["total_ms"] / K,
+                        "iterations": F["iterations"][-1], "rel_residual": F["rel"], "latency_ms": lat(F),
+                        "factor_seconds": F["t_factor"],
+                        "e2e_value": world * K / F["e2e_s"],
+                        "phases_ms": {k: round(v["ms"], 4) for k, v in F["profile"].items()},
+                        "clocks": F["clocks"]}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            samp = oracle_subprocess(1, 1)
+            val = scaled_rhs_per_s(samp, n, R["iterations"][-1]) if args.workload != "tiny" \
+                else 1.0 / samp["seconds"]
+            line["cpu_baseline"] = {
+                "value": val, "unit": "RHS/s", "cores": samp["cores"], "kind": "oracle",
+                "sample": (f"serial FP64 oracle solve (factorisation excluded) of the same generator at cells "
+                           f"{ORACLE_SAMPLE['cells']}: {samp['n']} dofs, {ORACLE_SAMPLE['nsub']} subdomains, "
+                           f"{samp['iterations']} iterations in {samp['seconds']:.2f} s; scaled to this workload "
+                           f"by dofs x iterations")}
+        except Exception as e:  # the GPU line still stands
+            line["cpu_baseline"] = {"value": None, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {e}"[:300]}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -115,7 +115,28 @@ typedef struct {
   double setup_seconds;     /* host wall time of hz_setup_mesh                        */
   double factor_seconds;    /* wall time of the last hz_factor                        */
   double min_pivot;         /* min |d_j| over all local factors (last hz_factor)     */
+  int64_t launches;         /* kernel launches issued by the library in this process */
 } hz_stats;
+
+/* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */
+enum {
+  HZ_PH_SPMV = 0,        /* w = A z (Eq. 2 operator, complex CSR)                      */
+  HZ_PH_COARSE = 1,      /* y = Z E^{-1} Z^T v (Eq. 3), with the coarse LDL^T solves   */
+  HZ_PH_RESTRICT = 2,    /* t_i = R_i t for all subdomains (Eq. 4), cast to the factor type */
+  HZ_PH_LOCAL_SOLVE = 3, /* A_i^{-1} t_i: forward, D^{-1}, backward over all levels    */
+  HZ_PH_PROLONG = 4,     /* z = y + sum_i R_i^T D_i x_i (Eq. 4)                       */
+  HZ_PH_CGS2 = 5,        /* two classical Gram-Schmidt passes at j = restart/2        */
+  HZ_PH_PRECOND = 6,     /* the whole M^{-1} v                                        */
+  HZ_PH_ITERATION = 7,   /* one full inner iteration (M^{-1}, A, CGS2, Givens)        */
+  HZ_PH_COUNT = 8
+};
+
+typedef struct {
+  double ms[HZ_PH_COUNT];        /* mean device time of one run (CUDA events, ctx stream) */
+  double bytes[HZ_PH_COUNT];     /* algorithmic bytes of one run                          */
+  double flops[HZ_PH_COUNT];     /* real floating-point operations of one run             */
+  int64_t launches[HZ_PH_COUNT]; /* kernel launches of one run                            */
+} hz_profile_out;
 
 /* Build everything that does not depend on frequency: dofs, the sparsity of A,
    frequency-free matrices K, M', B' (Eq. 2), the overlapping decomposition with
@@ -159,6 +180,12 @@ hz_status hz_apply_M(hz_ctx* ctx, const void* v_dev, void* z_dev);
    context would hold after hz_factor (the transient frontal workspace is
    front_bytes on top).  Lets a caller admit work against an HBM budget. */
 hz_status hz_plan(const hz_mesh_desc* mesh, const hz_options* opt, hz_stats* out);
+
+/* Time each phase of one inner iteration (reps runs each, after one warm-up run)
+   with CUDA events on the context's stream, on the current factors; fills
+   algorithmic bytes and flops per run.  Overwrites the Krylov workspace.
+   HZ_ERR_STATE before hz_factor. */
+hz_status hz_profile(hz_ctx* ctx, int32_t reps, hz_profile_out* out);
 
 /* Sizes and timings of a context (see hz_stats). */
 hz_status hz_get_stats(const hz_ctx* ctx, hz_stats* out);

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -24,7 +25,7 @@ struct hz_ctx {
   int order = 1, levels = 1, restart = 30, precision = 0, max_iter = 1000;
   hz::Mesh mesh;       // kept for point location
   hz::Dofs dofs;       // kept for point sources
-  int64_t n = 0, nnz = 0, nH = 0, nnzH = 0;
+  int64_t n = 0, nnz = 0, nH = 0, nnzH = 0, zeta_nnz = 0;
   // global operator
   int64_t* d_rp = nullptr;
   int32_t* d_ci = nullptr;
@@ -185,6 +186,28 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     TRY(upload(c, &F.pidx, pidx));
     TRY(upload(c, &F.pw, pw));
   }
+  // algorithmic bytes / flops of one forward + backward sweep
+  {
+    const double v = double(vs);
+    double pan = 0, macs = 0, cb = 0, rows = 0;
+    for (int s = 0; s < ns; s++) {
+      const double k = S.sn_k[s], m = S.sn_m[s];
+      pan += k * (k + 1) / 2 + (m - k) * k;
+      macs += k * (k - 1) / 2 + (m - k) * k;
+      cb += m - k;
+      rows += m;
+    }
+    const double nt = double(F.ntot);
+    const double fwd = pan * v + nt * v + cb * (v + 8) + rows * 8 + nt * v + cb * v;
+    const double bwd = pan * v + nt * v + cb * (v + 4) + nt * v;
+    F.solve_bytes = fwd + bwd;
+    F.solve_flops = 8.0 * 2.0 * macs;
+    F.gather_bytes = nt * (4 + 16 + v);
+    int64_t pn = 0;
+    for (int64_t q = 0; q < F.ntot; q++) pn += S.weight[q] != 0.0;
+    F.prolong_nnz = pn;
+    F.prolong_bytes = double(nglob + 1) * 8 + double(pn) * (4 + 8 + v) + double(nglob) * 16;
+  }
   // task lists
   const int nlev = S.nlev;
   std::vector<int2> fwd, bwd, wg, ea;
@@ -256,6 +279,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_wg_ptr = hcopy(wg_ptr);
   F.h_cb_ptr = hcopy(cb_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
+  F.h_ent_ptr = hcopy(S.ent_ptr);
   // numeric storage and solve workspaces
   void *pan = nullptr, *tl = nullptr, *zl = nullptr, *xl = nullptr, *uw = nullptr;
   TRY(dalloc(c, (char**)&pan, F.panel_elems * int64_t(vs)));
@@ -278,7 +302,8 @@ void free_host_ptrs(hz::FactorDev& F) {
   delete[] F.h_wg_ptr;
   delete[] F.h_cb_ptr;
   delete[] F.h_ea_ptr;
-  F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = nullptr;
+  delete[] F.h_ent_ptr;
+  F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;
 }
 
 hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[3], double& min_pivot) {
@@ -295,11 +320,8 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
   const double big = 1e300;
   std::memcpy(&init.min_pivot, &big, sizeof(double));
   CU(cudaMemcpyAsync(c->status, &init, sizeof(init), cudaMemcpyHostToDevice, c->st));
-  CU(cudaMemsetAsync(fronts, 0, size_t(F.front_elems) * vs, c->st));
-  hz::launch_front_fill(F, w, fronts, c->st);
   const double tiny = 1e-13 * (maxabs[0] + w * w * maxabs[1] + w * maxabs[2]);
-  for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, fronts, scratch, c->status, tiny, c->st);
-  hz::launch_panel_copy(F, fronts, c->st);
+  for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, w, fronts, scratch, c->status, tiny, c->st);
   CU(cudaGetLastError());
   hz::DevStatus out{};
   CU(cudaMemcpyAsync(&out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
@@ -461,6 +483,7 @@ hz_status hz_get_stats(const hz_ctx* c, hz_stats* out) {
   if (!c || !out) return HZ_ERR_ARG;
   *out = c->stats;
   out->device_bytes = c->bytes;
+  out->launches = hz::launch_count();
   return HZ_OK;
 }
 
@@ -479,7 +502,14 @@ void hz_free(hz_ctx* c) {
 
 }  // extern "C"
 
-// Host analysis shared by hz_setup_mesh and hz_plan.
+// Host analysis shared by hz_setup_mesh and hz_plan.  HZ_VERBOSE=1 prints phase times.
+static void phase(const char* what, std::chrono::steady_clock::time_point& t) {
+  static const bool on = std::getenv("HZ_VERBOSE") != nullptr;
+  const auto now = std::chrono::steady_clock::now();
+  if (on) std::fprintf(stderr, "[hz] %-28s %8.3f s\n", what, std::chrono::duration<double>(now - t).count());
+  t = now;
+}
+
 static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op, hz::HostProblem& P) {
   if (!md || !op) return fail(c, HZ_ERR_ARG, "null mesh or options");
   if (md->order != 1 && md->order != 2) return fail(c, HZ_ERR_ARG, "order must be 1 or 2");
@@ -527,9 +557,14 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     for (int64_t e = 0; e < ne; e++)
       if (P.parent[e] < 0 || P.parent[e] >= md->coarse_ne) return fail(c, HZ_ERR_ARG, "fine_parent out of range");
   }
+  auto tp = std::chrono::steady_clock::now();
+  phase("validate + partition", tp);
   hz::build_dofs(P.mesh, md->order, P.dofs);
+  phase("dofs", tp);
   hz::assemble_global(P.mesh, P.dofs, P.A);
+  phase("global assembly", tp);
   hz::build_subdomains(P.mesh, P.dofs, part, op->nsub, op->overlap, P.subs);
+  phase("subdomains + local A_i", tp);
   const int prec_k = op->precision == HZ_FP64 ? 112 : 128;
   int leaf = op->leaf_size > 0 ? op->leaf_size : 64;
   int maxsn = op->max_snode > 0 ? op->max_snode : 96;
@@ -550,6 +585,7 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     }
     hz::symbolic_batch(mats, leaf, maxsn, P.local);
   }
+  phase("local symbolic", tp);
   if (op->levels == 2) {
     hz::build_coarse(P);
     std::vector<double> coords(P.nH * 3);
@@ -560,7 +596,9 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
         for (int a = 0; a < 3; a++) coords[3 * P.cfree[k] + a] = P.cdofs.coord[3 * k + a];
     for (int64_t k = 0; k < P.nH; k++) gid[k] = k;
     hz::MatrixInput mi{&P.E, coords.data(), gid.data(), one.data()};
+    phase("coarse space", tp);
     hz::symbolic_batch({mi}, leaf, std::min(maxsn, 112), P.coarse);
+    phase("coarse symbolic", tp);
   }
   return HZ_OK;
 }
@@ -643,6 +681,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
   c->nnz = P.A.pat.nnz();
   c->nH = P.nH;
   c->nnzH = P.E.pat.nnz();
+  c->zeta_nnz = P.Z.nnz();
   fill_stats(c, P);
   auto bail = [&](hz_status st) {
     std::fprintf(stderr, "hz_setup_mesh: %s\n", c->err.c_str());
@@ -789,5 +828,115 @@ extern "C" hz_status hz_point_sources(hz_ctx* c, const double* xyz, int32_t nsrc
   } else {
     std::memcpy(rhs_out, B.data(), B.size() * 16);
   }
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
+  TRY(check_ctx(c));
+  if (!out || reps < 1) return fail(c, HZ_ERR_ARG, "bad profile arguments");
+  if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run first");
+  std::memset(out, 0, sizeof(*out));
+  const int64_t n = c->n;
+  const int m = c->restart;
+  const int jj = std::max(1, m / 2);
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  // finite, normal test data in the vectors and the Krylov basis
+  CU(cudaMemsetAsync(c->V, 0x3f, size_t(n) * (m + 1) * 16, st));
+  CU(cudaMemsetAsync(c->w, 0x3f, size_t(n) * 16, st));
+  CU(cudaMemsetAsync(c->b, 0x3f, size_t(n) * 16, st));
+  hz::launch_cgs(n, 0, c->V, n, nullptr, c->b, 0, c->partial, st);
+  hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+  hz::launch_init_cycle(c->nrm, c->g, m, c->scal + 2, c->scal + 3, st);
+  const double nt = 16.0;
+  auto run = [&](int ph) {
+    switch (ph) {
+      case HZ_PH_SPMV: hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, c->b, nullptr, c->w, st); break;
+      case HZ_PH_COARSE:
+        if (c->levels == 2) {
+          hz::launch_spmv_real(c->nH, c->d_Ztrp, c->d_Ztci, c->d_Ztv, c->b, c->rH, st);
+          hz::launch_gather(c->crs, c->rH, st);
+          hz::launch_solve(c->crs, st);
+          hz::launch_prolong(c->crs, nullptr, c->yH, st);
+          hz::launch_spmv_real(n, c->d_Zrp, c->d_Zci, c->d_Zv, c->yH, c->y, st);
+        }
+        break;
+      case HZ_PH_RESTRICT: hz::launch_gather(c->loc, c->b, st); break;
+      case HZ_PH_LOCAL_SOLVE: hz::launch_solve(c->loc, st); break;
+      case HZ_PH_PROLONG: hz::launch_prolong(c->loc, c->levels == 2 ? c->y : nullptr, c->t, st); break;
+      case HZ_PH_CGS2:
+        hz::launch_cgs(n, jj + 1, c->V, n, nullptr, c->w, jj + 1, c->partial, st);
+        hz::launch_reduce(c->partial, nb, jj + 1, c->h1, st);
+        hz::launch_cgs(n, jj + 1, c->V, n, c->h1, c->w, jj + 1, c->partial, st);
+        hz::launch_reduce(c->partial, nb, jj + 1, c->h2, st);
+        hz::launch_cgs(n, jj + 1, c->V, n, c->h2, c->w, 0, c->partial, st);
+        hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+        break;
+      case HZ_PH_PRECOND: apply_prec(c, c->b, c->t); break;
+      case HZ_PH_ITERATION: {
+        double2* zj = c->Zs + int64_t(jj) * n;
+        apply_prec(c, c->V + int64_t(jj) * n, zj);
+        hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, zj, nullptr, c->w, st);
+        hz::launch_cgs(n, jj + 1, c->V, n, nullptr, c->w, jj + 1, c->partial, st);
+        hz::launch_reduce(c->partial, nb, jj + 1, c->h1, st);
+        hz::launch_cgs(n, jj + 1, c->V, n, c->h1, c->w, jj + 1, c->partial, st);
+        hz::launch_reduce(c->partial, nb, jj + 1, c->h2, st);
+        hz::launch_cgs(n, jj + 1, c->V, n, c->h2, c->w, 0, c->partial, st);
+        hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+        hz::launch_givens(0, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, 1.0, c->scal, c->brk, c->scal + 1, st);
+        hz::launch_scale(n, c->w, c->scal + 1, c->V + int64_t(jj + 1) * n, st);
+        break;
+      }
+    }
+  };
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  for (int ph = 0; ph < HZ_PH_COUNT; ph++) {
+    run(ph);   // warm-up
+    const long long l0 = hz::launch_count();
+    CU(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; r++) run(ph);
+    CU(cudaEventRecord(e1, st));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    out->ms[ph] = double(ms) / reps;
+    out->launches[ph] = (hz::launch_count() - l0) / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(cudaGetLastError());
+  // algorithmic bytes and flops
+  const double nnz = double(c->nnz), dn = double(n);
+  out->bytes[HZ_PH_SPMV] = nnz * (nt + 4) + (dn + 1) * 8 + 2 * dn * nt;
+  out->flops[HZ_PH_SPMV] = 8 * nnz;
+  if (c->levels == 2) {
+    const double nz = double(c->zeta_nnz), nH = double(c->nH);
+    out->bytes[HZ_PH_COARSE] = 2 * nz * 12 + (dn + 1) * 8 + (nH + 1) * 8 + 2 * dn * nt + 2 * nH * nt +
+                               c->crs.gather_bytes + c->crs.solve_bytes + c->crs.prolong_bytes;
+    out->flops[HZ_PH_COARSE] = 2 * 4 * nz + c->crs.solve_flops;
+  }
+  out->bytes[HZ_PH_RESTRICT] = c->loc.gather_bytes;
+  out->bytes[HZ_PH_LOCAL_SOLVE] = c->loc.solve_bytes;
+  out->flops[HZ_PH_LOCAL_SOLVE] = c->loc.solve_flops;
+  out->bytes[HZ_PH_PROLONG] = c->loc.prolong_bytes + (c->levels == 2 ? dn * nt : 0.0);
+  out->flops[HZ_PH_PROLONG] = 4.0 * double(c->loc.prolong_nnz);
+  const double nc = jj + 1;
+  out->bytes[HZ_PH_CGS2] = (3 * nc + 5) * dn * nt;
+  out->flops[HZ_PH_CGS2] = (32 * nc + 12) * dn;
+  double pb = 0, pf = 0;
+  for (int ph : {HZ_PH_COARSE, HZ_PH_RESTRICT, HZ_PH_LOCAL_SOLVE, HZ_PH_PROLONG}) {
+    pb += out->bytes[ph];
+    pf += out->flops[ph];
+  }
+  if (c->levels == 2) {
+    pb += out->bytes[HZ_PH_SPMV];
+    pf += out->flops[HZ_PH_SPMV];
+  }
+  out->bytes[HZ_PH_PRECOND] = pb;
+  out->flops[HZ_PH_PRECOND] = pf;
+  out->bytes[HZ_PH_ITERATION] = pb + out->bytes[HZ_PH_SPMV] + out->bytes[HZ_PH_CGS2] + 2 * dn * nt;
+  out->flops[HZ_PH_ITERATION] = pf + out->flops[HZ_PH_SPMV] + out->flops[HZ_PH_CGS2];
   return HZ_OK;
 }

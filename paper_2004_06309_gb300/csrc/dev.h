@@ -50,8 +50,13 @@ struct FactorDev {
   int64_t* h_wg_ptr = nullptr;
   int64_t* h_cb_ptr = nullptr;
   int64_t* h_ea_ptr = nullptr;        // nlev * maxslot + 1, grouped (level, slot)
+  int64_t* h_ent_ptr = nullptr;       // nlev + 1: entries of each level's fronts
   int32_t max_slot = 0;
   int64_t scratch_elems = 0;          // max over levels of sum (m-k) k
+  // algorithmic cost of one forward+backward sweep (host-side)
+  double solve_bytes = 0, solve_flops = 0;
+  double gather_bytes = 0, prolong_bytes = 0;
+  int64_t prolong_nnz = 0;
   // numeric
   int precision = 0;                  // 0: complex128, 1: complex64
   void* panels = nullptr;             // factor store
@@ -70,12 +75,13 @@ struct DevStatus {
 };
 
 // ---- launchers (kernels.cu) -------------------------------------------------
+long long launch_count();
 void launch_fill_values(int64_t nnz, const double* K, const double2* M, const double2* B, double w,
                         double2* out, cudaStream_t st);
-void launch_front_fill(const FactorDev& F, double w, void* fronts, cudaStream_t st);
-void launch_factor_level(const FactorDev& F, int lev, void* fronts, void* scratch, DevStatus* status,
+// One assembly-tree level: zero and fill its fronts (A_i(omega) entries), extend-add the
+// children, factor, and copy the panels to the factor store.
+void launch_factor_level(const FactorDev& F, int lev, double w, void* fronts, void* scratch, DevStatus* status,
                          double tiny, cudaStream_t st);
-void launch_panel_copy(const FactorDev& F, const void* fronts, cudaStream_t st);
 
 void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st);
 void launch_solve(const FactorDev& F, cudaStream_t st);

@@ -50,8 +50,6 @@ struct Subdomain {
   std::vector<int64_t> elems;      // Gamma_i elements
   std::vector<int64_t> dofs;       // sorted global ids (R_i)
   std::vector<double> D;           // partition of unity on dofs
-  std::vector<int32_t> abc_faces;  // (face*3 vertex ids, owner elem) for absorbing terms
-  std::vector<int64_t> abc_owner;
   Parts A;                         // local operator pieces in local numbering
 };
 
@@ -68,7 +66,8 @@ struct SymbolicSet {
   int nlev = 0;
   std::vector<int32_t> lev_ptr, lev_sn;    // supernodes grouped by level
   // entries of the lower triangles: front position and frequency-free values
-  std::vector<int64_t> epos;
+  std::vector<int64_t> epos;           // grouped by level: ent_ptr[l] .. ent_ptr[l+1]
+  std::vector<int64_t> ent_ptr;
   std::vector<double> ek;
   std::vector<cplx> em, eb;
   // extend-add: relative positions of each child's contribution rows in its parent
@@ -79,10 +78,6 @@ struct SymbolicSet {
   std::vector<int64_t> cidx;
   int64_t front_elems = 0, panel_elems = 0, u_elems = 0;
   double flops = 0;                        // real flops of the numeric factorisation
-};
-
-struct SetupOptions {
-  int nsub = 1, overlap = 1, levels = 1, leaf = 64, maxsn = 128;
 };
 
 struct HostProblem {

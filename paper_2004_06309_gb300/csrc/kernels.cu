@@ -15,10 +15,16 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "dev.h"
 
 namespace hz {
+
+// Kernel launches issued by this library (for the launch count in hz_stats).
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+#define HZ_COUNT() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -112,6 +118,7 @@ __global__ void k_fill_values(int64_t nnz, const double* K, const double2* M, co
 void launch_fill_values(int64_t nnz, const double* K, const double2* M, const double2* B, double w,
                         double2* out, cudaStream_t st) {
   if (nnz == 0) return;
+  HZ_COUNT();
   k_fill_values<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, K, M, B, w, out);
 }
 
@@ -300,8 +307,16 @@ __global__ void __launch_bounds__(256) k_cb(const int4* tasks, const SnDev* sn, 
 }
 
 template <typename V>
-__global__ void k_panel_copy(const SnDev* sn, const V* fronts, V* panels) {
-  const SnDev S = sn[blockIdx.x];
+__global__ void k_front_zero(const int32_t* lev_sn, const SnDev* sn, V* fronts) {
+  const SnDev S = sn[lev_sn[blockIdx.x]];
+  const int64_t cnt = int64_t(S.m) * S.m;
+  V* f = fronts + S.frontoff;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) f[e] = czero<V>();
+}
+
+template <typename V>
+__global__ void k_panel_copy(const int32_t* lev_sn, const SnDev* sn, const V* fronts, V* panels) {
+  const SnDev S = sn[lev_sn[blockIdx.x]];
   const int64_t cnt = int64_t(S.m) * S.k;
   const V* src = fronts + S.frontoff;
   V* dst = panels + S.paneloff;
@@ -312,32 +327,45 @@ static size_t diag_smem(int kmax, size_t vs) { return (size_t(kmax + 1) * kmax +
 static size_t wg_smem(int kmax, size_t vs) { return (size_t(64) * kmax + kmax) * vs; }
 
 template <typename V>
-static void factor_level_t(const FactorDev& F, int lev, V* fronts, V* scratch, DevStatus* status, double tiny,
-                           cudaStream_t st) {
+static void factor_level_t(const FactorDev& F, int lev, double w, V* fronts, V* scratch, DevStatus* status,
+                           double tiny, cudaStream_t st) {
+  const int64_t nb = F.h_lev_ptr[lev + 1] - F.h_lev_ptr[lev];
+  const int32_t* lsn = F.lev_sn + F.h_lev_ptr[lev];
+  if (nb > 0) {
+    HZ_COUNT();
+    k_front_zero<V><<<unsigned(nb), 256, 0, st>>>(lsn, F.sn, fronts);
+  }
+  const int64_t e0 = F.h_ent_ptr[lev], e1 = F.h_ent_ptr[lev + 1];
+  if (e1 > e0) {
+    HZ_COUNT();
+    k_front_fill<V><<<grid_for(e1 - e0, 256), 256, 0, st>>>(e1 - e0, F.epos + e0, F.ek + e0, F.em + e0, F.eb + e0,
+                                                           w, fronts);
+  }
   // extend-add, one child slot per launch so that no parent entry is written twice
   for (int q = 0; q < F.max_slot; q++) {
     const int64_t b = F.h_ea_ptr[int64_t(lev) * F.max_slot + q], e = F.h_ea_ptr[int64_t(lev) * F.max_slot + q + 1];
-    if (e > b) k_extend_add<V><<<unsigned(e - b), 256, 0, st>>>(F.ea_tasks + b, F.sn, F.rel, F.reloff, fronts);
+    if (e > b) {
+      HZ_COUNT();
+      k_extend_add<V><<<unsigned(e - b), 256, 0, st>>>(F.ea_tasks + b, F.sn, F.rel, F.reloff, fronts);
+    }
   }
-  const int64_t nb = F.h_lev_ptr[lev + 1] - F.h_lev_ptr[lev];
   if (nb == 0) return;
   const size_t ds = diag_smem(F.maxk, sizeof(V));
-  k_diag<V><<<unsigned(nb), 256, ds, st>>>(F.lev_sn + F.h_lev_ptr[lev], F.sn, fronts, status, tiny);
+  HZ_COUNT();
+  k_diag<V><<<unsigned(nb), 256, ds, st>>>(lsn, F.sn, fronts, status, tiny);
   const int64_t wb = F.h_wg_ptr[lev], we = F.h_wg_ptr[lev + 1];
-  if (we > wb)
+  if (we > wb) {
+    HZ_COUNT();
     k_wg<V><<<unsigned(we - wb), 256, wg_smem(F.maxk, sizeof(V)), st>>>(F.wg_tasks + wb, F.sn, F.scr_off, fronts,
                                                                        scratch);
+  }
   const int64_t cbb = F.h_cb_ptr[lev], cbe = F.h_cb_ptr[lev + 1];
-  if (cbe > cbb) k_cb<V><<<unsigned(cbe - cbb), 256, 0, st>>>(F.cb_tasks + cbb, F.sn, F.scr_off, fronts, scratch);
-}
-
-void launch_front_fill(const FactorDev& F, double w, void* fronts, cudaStream_t st) {
-  const int64_t ne = F.nentries;
-  if (ne == 0) return;
-  if (F.precision == 0)
-    k_front_fill<double2><<<grid_for(ne, 256), 256, 0, st>>>(ne, F.epos, F.ek, F.em, F.eb, w, (double2*)fronts);
-  else
-    k_front_fill<float2><<<grid_for(ne, 256), 256, 0, st>>>(ne, F.epos, F.ek, F.em, F.eb, w, (float2*)fronts);
+  if (cbe > cbb) {
+    HZ_COUNT();
+    k_cb<V><<<unsigned(cbe - cbb), 256, 0, st>>>(F.cb_tasks + cbb, F.sn, F.scr_off, fronts, scratch);
+  }
+  HZ_COUNT();
+  k_panel_copy<V><<<unsigned(nb), 256, 0, st>>>(lsn, F.sn, fronts, (V*)F.panels);
 }
 
 static bool g_attr_done[2] = {false, false};
@@ -355,21 +383,13 @@ static void set_attrs(int prec, int kmax) {
   (void)kmax;
 }
 
-void launch_factor_level(const FactorDev& F, int lev, void* fronts, void* scratch, DevStatus* status,
+void launch_factor_level(const FactorDev& F, int lev, double w, void* fronts, void* scratch, DevStatus* status,
                          double tiny, cudaStream_t st) {
   set_attrs(F.precision, F.maxk);
   if (F.precision == 0)
-    factor_level_t<double2>(F, lev, (double2*)fronts, (double2*)scratch, status, tiny, st);
+    factor_level_t<double2>(F, lev, w, (double2*)fronts, (double2*)scratch, status, tiny, st);
   else
-    factor_level_t<float2>(F, lev, (float2*)fronts, (float2*)scratch, status, tiny, st);
-}
-
-void launch_panel_copy(const FactorDev& F, const void* fronts, cudaStream_t st) {
-  if (F.nsn == 0) return;
-  if (F.precision == 0)
-    k_panel_copy<double2><<<F.nsn, 256, 0, st>>>(F.sn, (const double2*)fronts, (double2*)F.panels);
-  else
-    k_panel_copy<float2><<<F.nsn, 256, 0, st>>>(F.sn, (const float2*)fronts, (float2*)F.panels);
+    factor_level_t<float2>(F, lev, w, (float2*)fronts, (float2*)scratch, status, tiny, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -477,21 +497,30 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
   V* u = (V*)F.u_ws;
   for (int l = 0; l < F.nlev; l++) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
-    if (e > b) k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+    if (e > b) {
+      HZ_COUNT();
+      k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+    }
   }
   const size_t sm = size_t(F.maxm) * sizeof(V);
   for (int l = F.nlev - 1; l >= 0; l--) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
-    if (e > b) k_bwd<V><<<unsigned(e - b), 256, sm, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x);
+    if (e > b) {
+      HZ_COUNT();
+      k_bwd<V><<<unsigned(e - b), 256, sm, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x);
+    }
   }
 }
 
 void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st) {
   if (F.ntot == 0) return;
-  if (F.precision == 0)
+  if (F.precision == 0) {
+    HZ_COUNT();
     k_gather<double2><<<grid_for(F.ntot, 256), 256, 0, st>>>(F.ntot, F.gidx, src, (double2*)F.t_loc);
-  else
+  } else {
+    HZ_COUNT();
     k_gather<float2><<<grid_for(F.ntot, 256), 256, 0, st>>>(F.ntot, F.gidx, src, (float2*)F.t_loc);
+  }
 }
 
 void launch_solve(const FactorDev& F, cudaStream_t st) {
@@ -501,12 +530,15 @@ void launch_solve(const FactorDev& F, cudaStream_t st) {
 
 void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st) {
   if (F.nglob == 0) return;
-  if (F.precision == 0)
+  if (F.precision == 0) {
+    HZ_COUNT();
     k_prolong<double2><<<grid_for(F.nglob, 256), 256, 0, st>>>(F.nglob, F.pptr, F.pidx, F.pw,
                                                                (const double2*)F.x_loc, y, z);
-  else
+  } else {
+    HZ_COUNT();
     k_prolong<float2><<<grid_for(F.nglob, 256), 256, 0, st>>>(F.nglob, F.pptr, F.pidx, F.pw,
                                                               (const float2*)F.x_loc, y, z);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -557,12 +589,14 @@ __global__ void __launch_bounds__(256) k_spmv_real(int64_t n, const int64_t* rp,
 void launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                  const double2* sub, double2* y, cudaStream_t st) {
   if (n == 0) return;
+  HZ_COUNT();
   k_spmv<8><<<grid_for(n * 8, 256, 152 * 32), 256, 0, st>>>(n, rp, ci, val, x, sub, y);
 }
 
 void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, const double2* x,
                       double2* y, cudaStream_t st) {
   if (n == 0) return;
+  HZ_COUNT();
   k_spmv_real<<<grid_for(n * 4, 256, 152 * 32), 256, 0, st>>>(n, rp, ci, val, x, y);
 }
 
@@ -644,6 +678,7 @@ void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const doubl
   const int nb = cgs_blocks();
   int64_t chunk = (n + nb - 1) / nb;
   chunk = (chunk + kCgsRows - 1) / kCgsRows * kCgsRows;
+  HZ_COUNT();
   k_cgs<<<nb, 256, 0, st>>>(n, ncols, V, ldv, h, w, ndot, partial, chunk);
 }
 
@@ -657,6 +692,7 @@ __global__ void k_reduce(const double2* partial, int nblk, double2* out) {
 
 void launch_reduce(const double2* partial, int nblk, int ncols, double2* out, cudaStream_t st) {
   (void)ncols;
+  HZ_COUNT();
   k_reduce<<<1, 96, 0, st>>>(partial, nblk, out);
 }
 
@@ -711,6 +747,7 @@ __global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, doub
 void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
                    const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown, double* invh,
                    cudaStream_t st) {
+  HZ_COUNT();
   k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, h1, h2, nrm, bnorm, est, breakdown, invh);
 }
 
@@ -724,6 +761,7 @@ __global__ void k_init_cycle(const double2* nrm2, double2* g, int m, double* inv
 }
 
 void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta, cudaStream_t st) {
+  HZ_COUNT();
   k_init_cycle<<<1, 64, 0, st>>>(nrm2, g, m, invbeta, beta);
 }
 
@@ -734,6 +772,7 @@ __global__ void k_scale(int64_t n, const double2* w, const double* s, double2* o
 }
 
 void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st) {
+  HZ_COUNT();
   k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, w, s, out);
 }
 
@@ -761,7 +800,9 @@ __global__ void k_gemv_add(int64_t n, int k, const double2* y, const double2* Zs
 
 void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y, const double2* Zs,
                      int64_t ldz, double2* x, cudaStream_t st) {
+  HZ_COUNT();
   k_backsub<<<1, 32, 0, st>>>(k, H, ldh, g, y);
+  HZ_COUNT();
   k_gemv_add<<<grid_for(n, 256), 256, 0, st>>>(n, k, y, Zs, ldz, x);
 }
 
@@ -771,6 +812,7 @@ __global__ void k_copy(int64_t n, const double2* a, double2* out) {
 }
 
 void launch_axpby_copy(int64_t n, const double2* a, double2* out, cudaStream_t st) {
+  HZ_COUNT();
   k_copy<<<grid_for(n, 256), 256, 0, st>>>(n, a, out);
 }
 

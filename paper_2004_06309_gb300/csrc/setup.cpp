@@ -327,6 +327,26 @@ static void add_face(Parts& P, const int64_t* ld, int nbf, int order, double are
     }
 }
 
+// Row a of the element stiffness and unit mass of element e.
+static void element_row(const Mesh& m, int order, int64_t e, int a, double* Kr, double* Mr) {
+  double g[4][3];
+  const double vol = tet_grads(m.xyz.data(), m.tets.data() + 4 * e, g);
+  double G[4][4];
+  for (int p = 0; p < 4; p++)
+    for (int q = 0; q < 4; q++) G[p][q] = g[p][0] * g[q][0] + g[p][1] * g[q][1] + g[p][2] * g[q][2];
+  const int o = order - 1, nb = order == 1 ? 4 : 10;
+  const RefTables& R = ref();
+  for (int b = 0; b < nb; b++) {
+    double s = 0;
+    for (int p = 0; p < 4; p++)
+      for (int q = 0; q < 4; q++) s += G[p][q] * R.S[o][a][b][p][q];
+    Kr[b] = vol * s;
+    Mr[b] = vol * R.M[o][a][b];
+  }
+}
+
+// Global K, M', B' assembled row by row (rows in parallel, each row's element
+// contributions added in increasing element order: deterministic).
 void assemble_global(const Mesh& m, const Dofs& d, Parts& A) {
   std::vector<int64_t> all(m.ne);
   std::iota(all.begin(), all.end(), 0);
@@ -336,10 +356,29 @@ void assemble_global(const Mesh& m, const Dofs& d, Parts& A) {
   A.M.assign(nnz, 0.0);
   A.B.assign(nnz, 0.0);
   const int nb = d.nb;
-  double Ke[100], Me[100];
-  for (int64_t e = 0; e < m.ne; e++) {
-    element(m, d.order, e, Ke, Me);
-    add_element(A, d.elem.data() + nb * e, nb, Ke, Me, 1.0 / (m.c[e] * m.c[e]));
+  const int64_t n = d.n;
+  std::vector<int64_t> iptr(n + 1, 0);
+  for (int64_t q = 0; q < m.ne * nb; q++) iptr[d.elem[q] + 1]++;
+  for (int64_t r = 0; r < n; r++) iptr[r + 1] += iptr[r];
+  std::vector<int64_t> inc(iptr[n]);
+  {
+    std::vector<int64_t> fill(iptr.begin(), iptr.end() - 1);
+    for (int64_t q = 0; q < m.ne * nb; q++) inc[fill[d.elem[q]]++] = q;   // (element, local node) pairs
+  }
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t r = 0; r < n; r++) {
+    double Kr[10], Mr[10];
+    for (int64_t t = iptr[r]; t < iptr[r + 1]; t++) {
+      const int64_t e = inc[t] / nb;
+      const int a = int(inc[t] % nb);
+      element_row(m, d.order, e, a, Kr, Mr);
+      const cplx w = 1.0 / (m.c[e] * m.c[e]);
+      for (int b = 0; b < nb; b++) {
+        const int64_t k = A.pat.find(r, d.elem[nb * e + b]);
+        A.K[k] += Kr[b];
+        A.M[k] += w * Mr[b];
+      }
+    }
   }
   const std::vector<int64_t> own = face_owners(m);
   int64_t fd[6];
@@ -540,6 +579,16 @@ void build_subdomains(const Mesh& m, const Dofs& d, const std::vector<int32_t>& 
 // interpolated from its parent coarse element alone) and the Galerkin pieces
 // E_K, E_M, E_B = sum over fine elements (faces) of Z_e^T X_e Z_e.
 // ---------------------------------------------------------------------------
+// Barycentric coordinates of p in a tet whose gradients g and first vertex x0 are known.
+static inline void bary_from(const double g[4][3], const double* x0, const double* p, double l[4]) {
+  double s = 0;
+  for (int k = 1; k < 4; k++) {
+    l[k] = g[k][0] * (p[0] - x0[0]) + g[k][1] * (p[1] - x0[1]) + g[k][2] * (p[2] - x0[2]);
+    s += l[k];
+  }
+  l[0] = 1.0 - s;
+}
+
 void build_coarse(HostProblem& P) {
   const Mesh& m = P.mesh;
   const Mesh& cm = P.cmesh;
@@ -552,42 +601,49 @@ void build_coarse(HostProblem& P) {
     if (!cd.is_dir[k]) P.cfree[k] = nH++;
   P.nH = nH;
   const int nb = d.nb;
-  // Z_e for every fine element: nb x nb (fine node a, coarse node b of the parent)
-  std::vector<double> Ze(size_t(m.ne) * nb * nb);
-  std::vector<int64_t> zrow_elem(d.n, -1), zrow_node(d.n, -1);
-  for (int64_t e = 0; e < m.ne; e++) {
-    const int64_t E = P.parent[e];
-    const int32_t* ct = cm.tets.data() + 4 * E;
-    for (int a = 0; a < nb; a++) {
-      const int64_t g = d.elem[nb * e + a];
-      double l[4], phi[10];
-      barycentric(cm.xyz.data(), ct, d.coord.data() + 3 * g, l);
-      eval_basis(d.order, l, phi);
-      for (int b = 0; b < nb; b++) {
-        double v = phi[b];
-        if (std::fabs(v) < 1e-12 || d.is_dir[g] || P.cfree[cd.elem[nb * E + b]] < 0) v = 0.0;
-        Ze[(size_t(e) * nb + a) * nb + b] = v;
-      }
-      if (zrow_elem[g] < 0) { zrow_elem[g] = e; zrow_node[g] = a; }
+  const int64_t ncE = cm.ne;
+  // Interpolation weights of the coarse basis of element E at fine node g (zeroed
+  // on fine Dirichlet nodes and for removed coarse Dirichlet dofs; rounding noise
+  // below 1e-12 dropped: the exact weights are dyadic rationals).
+  auto zrow = [&](int64_t E, const double g[4][3], int64_t node, double* out) {
+    double l[4], phi[10];
+    bary_from(g, cm.xyz.data() + 3 * int64_t(cm.tets[4 * E]), d.coord.data() + 3 * node, l);
+    eval_basis(d.order, l, phi);
+    for (int b = 0; b < nb; b++) {
+      double v = phi[b];
+      if (std::fabs(v) < 1e-12 || d.is_dir[node] || P.cfree[cd.elem[nb * E + b]] < 0) v = 0.0;
+      out[b] = v;
     }
+  };
+  // Z rows: for every fine node, the lowest fine element containing it
+  std::vector<int64_t> first_elem(d.n, -1);
+  for (int64_t e = m.ne - 1; e >= 0; e--)
+    for (int a = 0; a < nb; a++) first_elem[d.elem[nb * e + a]] = e;
+  std::vector<double> zval(size_t(d.n) * nb);
+#pragma omp parallel for schedule(static)
+  for (int64_t g = 0; g < d.n; g++) {
+    const int64_t E = P.parent[first_elem[g]];
+    double gr[4][3];
+    tet_grads(cm.xyz.data(), cm.tets.data() + 4 * E, gr);
+    zrow(E, gr, g, zval.data() + size_t(g) * nb);
   }
-  // Z (n x nH) rows from the lowest element containing each fine node
   P.Z.n = d.n;
   P.Z.ptr.assign(d.n + 1, 0);
   P.Z.col.clear();
   P.Zv.clear();
   for (int64_t g = 0; g < d.n; g++) {
-    const int64_t e = zrow_elem[g], a = zrow_node[g];
-    const int64_t E = P.parent[e];
-    std::vector<std::pair<int32_t, double>> row;
+    const int64_t E = P.parent[first_elem[g]];
+    std::pair<int32_t, double> row[10];
+    int cnt = 0;
     for (int b = 0; b < nb; b++) {
-      const double v = Ze[(size_t(e) * nb + a) * nb + b];
-      if (v != 0.0) row.push_back({int32_t(P.cfree[cd.elem[nb * E + b]]), v});
+      const double v = zval[size_t(g) * nb + b];
+      if (v != 0.0) row[cnt++] = {int32_t(P.cfree[cd.elem[nb * E + b]]), v};
     }
-    std::sort(row.begin(), row.end());
-    for (auto& pr : row) { P.Z.col.push_back(pr.first); P.Zv.push_back(pr.second); }
+    std::sort(row, row + cnt);
+    for (int q = 0; q < cnt; q++) { P.Z.col.push_back(row[q].first); P.Zv.push_back(row[q].second); }
     P.Z.ptr[g + 1] = int64_t(P.Z.col.size());
   }
+  std::vector<double>().swap(zval);
   // Z^T
   P.Zt.n = nH;
   P.Zt.ptr.assign(nH + 1, 0);
@@ -620,67 +676,94 @@ void build_coarse(HostProblem& P) {
       P.E.pat.ptr[P.cfree[r] + 1] = int64_t(P.E.pat.col.size());
     }
   }
+  // fine elements and absorbing faces grouped by coarse parent
+  std::vector<int64_t> cptr(ncE + 1, 0), kids(m.ne);
+  for (int64_t e = 0; e < m.ne; e++) cptr[P.parent[e] + 1]++;
+  for (int64_t E = 0; E < ncE; E++) cptr[E + 1] += cptr[E];
+  {
+    std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int64_t e = 0; e < m.ne; e++) kids[fill[P.parent[e]]++] = e;
+  }
+  const std::vector<int64_t> own = face_owners(m);
+  std::vector<int64_t> fptr(ncE + 1, 0), fids;
+  for (size_t f = 0; f < m.tag.size(); f++)
+    if (m.tag[f] == 1) fptr[P.parent[own[f]] + 1]++;
+  for (int64_t E = 0; E < ncE; E++) fptr[E + 1] += fptr[E];
+  fids.resize(fptr[ncE]);
+  {
+    std::vector<int64_t> fill(fptr.begin(), fptr.end() - 1);
+    for (size_t f = 0; f < m.tag.size(); f++)
+      if (m.tag[f] == 1) fids[fill[P.parent[own[f]]]++] = int64_t(f);
+  }
+  // Galerkin pieces per coarse element: sum over its fine children of Z_e^T X_e Z_e
+  const size_t nb2 = size_t(nb) * nb;
+  std::vector<double> EK(size_t(ncE) * nb2);
+  std::vector<cplx> EM(size_t(ncE) * nb2), EB(size_t(ncE) * nb2);
+  const RefTables& R = ref();
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t E = 0; E < ncE; E++) {
+    double gr[4][3];
+    tet_grads(cm.xyz.data(), cm.tets.data() + 4 * E, gr);
+    double* ek = EK.data() + size_t(E) * nb2;
+    cplx* em = EM.data() + size_t(E) * nb2;
+    cplx* eb = EB.data() + size_t(E) * nb2;
+    for (size_t q = 0; q < nb2; q++) { ek[q] = 0; em[q] = 0; eb[q] = 0; }
+    double Ke[100], Me[100], Z[100], T1[100], T2[100];
+    for (int64_t q = cptr[E]; q < cptr[E + 1]; q++) {
+      const int64_t e = kids[q];
+      element(m, d.order, e, Ke, Me);
+      for (int a = 0; a < nb; a++) zrow(E, gr, d.elem[nb * e + a], Z + a * nb);
+      for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++) {
+          double sk = 0, sm = 0;
+          for (int c = 0; c < nb; c++) { sk += Ke[a * nb + c] * Z[c * nb + b]; sm += Me[a * nb + c] * Z[c * nb + b]; }
+          T1[a * nb + b] = sk;
+          T2[a * nb + b] = sm;
+        }
+      const cplx w = 1.0 / (m.c[e] * m.c[e]);
+      for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++) {
+          double sk = 0, sm = 0;
+          for (int c = 0; c < nb; c++) { sk += Z[c * nb + a] * T1[c * nb + b]; sm += Z[c * nb + a] * T2[c * nb + b]; }
+          ek[a * nb + b] += sk;
+          em[a * nb + b] += w * sm;
+        }
+    }
+    for (int64_t q = fptr[E]; q < fptr[E + 1]; q++) {
+      const int64_t f = fids[q];
+      const int64_t e = own[f];
+      int64_t fd[6];
+      d.face_dofs(m.faces.data() + 3 * f, fd);
+      double Zf[60];
+      for (int z = 0; z < d.nbf; z++) zrow(E, gr, fd[z], Zf + z * nb);
+      const double area = tri_area(m.xyz.data(), m.faces.data() + 3 * f);
+      const cplx w = 1.0 / m.c[e];
+      for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++) {
+          double sacc = 0;
+          for (int p = 0; p < d.nbf; p++)
+            for (int r = 0; r < d.nbf; r++)
+              sacc += Zf[p * nb + a] * area * R.F[d.order - 1][p][r] * Zf[r * nb + b];
+          eb[a * nb + b] += w * sacc;
+        }
+    }
+  }
   const int64_t nnzE = P.E.pat.nnz();
   P.E.K.assign(nnzE, 0.0);
   P.E.M.assign(nnzE, 0.0);
   P.E.B.assign(nnzE, 0.0);
-  double Ke[100], Me[100], T1[100];
-  cplx TM[100];
-  std::vector<int64_t> cfd(nb);
-  for (int64_t e = 0; e < m.ne; e++) {
-    element(m, d.order, e, Ke, Me);
-    const double* Z = Ze.data() + size_t(e) * nb * nb;
-    const int64_t E = P.parent[e];
+  for (int64_t E = 0; E < ncE; E++) {
+    int64_t cfd[10];
     for (int b = 0; b < nb; b++) cfd[b] = P.cfree[cd.elem[nb * E + b]];
-    const cplx w = 1.0 / (m.c[e] * m.c[e]);
-    // T1 = K_e Z, TM = M_e Z
-    for (int a = 0; a < nb; a++)
-      for (int b = 0; b < nb; b++) {
-        double sk = 0, sm = 0;
-        for (int c = 0; c < nb; c++) { sk += Ke[a * nb + c] * Z[c * nb + b]; sm += Me[a * nb + c] * Z[c * nb + b]; }
-        T1[a * nb + b] = sk;
-        TM[a * nb + b] = sm;
-      }
     for (int a = 0; a < nb; a++) {
       if (cfd[a] < 0) continue;
       for (int b = 0; b < nb; b++) {
         if (cfd[b] < 0) continue;
-        double sk = 0, sm = 0;
-        for (int c = 0; c < nb; c++) { sk += Z[c * nb + a] * T1[c * nb + b]; sm += Z[c * nb + a] * TM[c * nb + b].real(); }
         const int64_t k = P.E.pat.find(cfd[a], cfd[b]);
-        P.E.K[k] += sk;
-        P.E.M[k] += w * sm;
-      }
-    }
-  }
-  // absorbing faces
-  const std::vector<int64_t> own = face_owners(m);
-  int64_t fd[6];
-  const RefTables& R = ref();
-  for (size_t f = 0; f < m.tag.size(); f++) {
-    if (m.tag[f] != 1) continue;
-    const int64_t e = own[f];
-    d.face_dofs(m.faces.data() + 3 * f, fd);
-    int li[6];
-    for (int z = 0; z < d.nbf; z++) {
-      li[z] = -1;
-      for (int a = 0; a < nb; a++)
-        if (d.elem[nb * e + a] == fd[z]) li[z] = a;
-    }
-    const double area = tri_area(m.xyz.data(), m.faces.data() + 3 * f);
-    const double* Z = Ze.data() + size_t(e) * nb * nb;
-    const int64_t E = P.parent[e];
-    for (int b = 0; b < nb; b++) cfd[b] = P.cfree[cd.elem[nb * E + b]];
-    const cplx w = 1.0 / m.c[e];
-    for (int a = 0; a < nb; a++) {
-      if (cfd[a] < 0) continue;
-      for (int b = 0; b < nb; b++) {
-        if (cfd[b] < 0) continue;
-        double s = 0;
-        for (int p = 0; p < d.nbf; p++)
-          for (int q = 0; q < d.nbf; q++)
-            s += Z[li[p] * nb + a] * area * R.F[d.order - 1][p][q] * Z[li[q] * nb + b];
-        if (s != 0.0) P.E.B[P.E.pat.find(cfd[a], cfd[b])] += w * s;
+        const size_t q = size_t(E) * nb2 + a * nb + b;
+        P.E.K[k] += EK[q];
+        P.E.M[k] += EM[q];
+        P.E.B[k] += EB[q];
       }
     }
   }

@@ -4,6 +4,9 @@
 // every index map the batched device factorisation and solves need.
 #include <algorithm>
 #include <cmath>
+#include <iterator>
+#include <map>
+#include <set>
 #include <numeric>
 
 #include "host.h"
@@ -212,14 +215,12 @@ void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, S
       S.sn_level[g] = O.level[s];
       maxlev = std::max(maxlev, O.level[s]);
       S.sn_rowoff[g + 1] = S.sn_rowoff[g] + m;
-      S.sn_frontoff[g + 1] = S.sn_frontoff[g] + m * m;
       S.sn_paneloff[g + 1] = S.sn_paneloff[g] + m * O.k[s];
       S.sn_uoff[g + 1] = S.sn_uoff[g] + (m - O.k[s]);
       const double k = O.k[s], r = double(m) - k;
       S.flops += 8.0 * (k * k * k / 3.0 + r * k * k + r * r * k / 2.0);
     }
   }
-  S.front_elems = S.sn_frontoff[ns];
   S.panel_elems = S.sn_paneloff[ns];
   S.u_elems = S.sn_uoff[ns];
   S.rowlist.resize(S.sn_rowoff[ns]);
@@ -238,20 +239,90 @@ void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, S
     std::vector<int32_t> fill(S.lev_ptr.begin(), S.lev_ptr.end() - 1);
     for (int32_t g = 0; g < ns; g++) S.lev_sn[fill[S.sn_level[g]]++] = g;
   }
-  // entries
+  // Frontal workspace: a static first-fit plan.  The front of supernode s is
+  // allocated when its level starts and released once its parent's level has
+  // absorbed it (extend-add), so only the live part of the tree is resident.
+  {
+    // best fit: free blocks indexed by size (for take) and by offset (to coalesce)
+    std::map<int64_t, int64_t> by_off;              // offset -> size
+    std::set<std::pair<int64_t, int64_t>> by_size;  // (size, offset)
+    int64_t top = 0, peak = 0;
+    auto erase_size = [&](int64_t sz, int64_t off) { by_size.erase({sz, off}); };
+    auto take = [&](int64_t sz) {
+      auto it = by_size.lower_bound({sz, int64_t(-1)});
+      if (it == by_size.end()) {
+        const int64_t off = top;
+        top += sz;
+        peak = std::max(peak, top);
+        return off;
+      }
+      const int64_t bsz = it->first, off = it->second;
+      by_size.erase(it);
+      by_off.erase(off);
+      if (bsz > sz) {
+        by_off[off + sz] = bsz - sz;
+        by_size.insert({bsz - sz, off + sz});
+      }
+      return off;
+    };
+    auto give = [&](int64_t off, int64_t sz) {
+      auto nx = by_off.lower_bound(off);
+      if (nx != by_off.end() && off + sz == nx->first) {
+        sz += nx->second;
+        erase_size(nx->second, nx->first);
+        nx = by_off.erase(nx);
+      }
+      if (nx != by_off.begin()) {
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == off) {
+          erase_size(pv->second, pv->first);
+          off = pv->first;
+          sz += pv->second;
+          by_off.erase(pv);
+        }
+      }
+      if (off + sz == top) {        // give the tail back to the unallocated end
+        top = off;
+        return;
+      }
+      by_off[off] = sz;
+      by_size.insert({sz, off});
+    };
+    std::vector<std::vector<int32_t>> kids(ns);
+    for (int32_t g = 0; g < ns; g++)
+      if (S.sn_parent[g] >= 0) kids[S.sn_parent[g]].push_back(g);
+    for (int l = 0; l < S.nlev; l++) {
+      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+        const int32_t g = S.lev_sn[q];
+        S.sn_frontoff[g] = take(int64_t(S.sn_m[g]) * S.sn_m[g]);
+      }
+      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+        const int32_t g = S.lev_sn[q];
+        for (int32_t c : kids[g]) give(S.sn_frontoff[c], int64_t(S.sn_m[c]) * S.sn_m[c]);
+        if (S.sn_parent[g] < 0) give(S.sn_frontoff[g], int64_t(S.sn_m[g]) * S.sn_m[g]);
+      }
+    }
+    S.front_elems = peak;
+  }
+  // entries, grouped by the level of the supernode owning their column
   int64_t ne = 0;
   for (int i = 0; i < nmat; i++) ne += int64_t(one[i].e_sn.size());
   S.epos.resize(ne);
   S.ek.resize(ne);
   S.em.resize(ne);
   S.eb.resize(ne);
+  S.ent_ptr.assign(S.nlev + 1, 0);
+  for (int i = 0; i < nmat; i++)
+    for (int32_t sl : one[i].e_sn) S.ent_ptr[S.sn_level[sn_base[i] + sl] + 1]++;
+  for (int l = 0; l < S.nlev; l++) S.ent_ptr[l + 1] += S.ent_ptr[l];
   {
-    int64_t q = 0;
+    std::vector<int64_t> fill(S.ent_ptr.begin(), S.ent_ptr.end() - 1);
     for (int i = 0; i < nmat; i++) {
       const SymOne& O = one[i];
       const Parts& A = *mats[i].A;
-      for (size_t t = 0; t < O.e_sn.size(); t++, q++) {
+      for (size_t t = 0; t < O.e_sn.size(); t++) {
         const int32_t g = sn_base[i] + O.e_sn[t];
+        const int64_t q = fill[S.sn_level[g]]++;
         S.epos[q] = S.sn_frontoff[g] + O.e_off[t];
         S.ek[q] = A.K[O.e_src[t]];
         S.em[q] = A.M[O.e_src[t]];

@@ -60,11 +60,19 @@ class Stats(C.Structure):
         ("nnz_factor_coarse", C.c_int64), ("nsupernodes", C.c_int64), ("nlevels", C.c_int32),
         ("nlevels_coarse", C.c_int32), ("front_bytes", C.c_int64), ("device_bytes", C.c_int64),
         ("factor_flops", C.c_double), ("setup_seconds", C.c_double), ("factor_seconds", C.c_double),
-        ("min_pivot", C.c_double),
+        ("min_pivot", C.c_double), ("launches", C.c_int64),
     ]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PHASES = ["spmv", "coarse", "restrict", "local_solve", "prolong", "cgs2", "precond", "iteration"]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("bytes", C.c_double * 8), ("flops", C.c_double * 8),
+                ("launches", C.c_int64 * 8)]
 
 
 # Every exported symbol and its signature: (restype, argtypes).
@@ -78,6 +86,7 @@ SIGNATURES = {
     "hz_apply_M": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "hz_plan": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(Options), C.POINTER(Stats)]),
     "hz_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "hz_profile": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Profile)]),
     "hz_ndofs": (C.c_int64, [C.c_void_p]),
     "hz_status_string": (C.c_char_p, [C.c_int]),
     "hz_last_error": (C.c_char_p, [C.c_void_p]),
@@ -223,6 +232,13 @@ class Solver:
         st = Stats()
         self._check(lib().hz_get_stats(self.h, C.byref(st)), "hz_get_stats")
         return st.as_dict()
+
+    def profile(self, reps=5):
+        """Per-phase device time (ms), algorithmic bytes, flops and launches of one iteration."""
+        pr = Profile()
+        self._check(lib().hz_profile(self.h, int(reps), C.byref(pr)), "hz_profile")
+        return {name: dict(ms=pr.ms[i], bytes=pr.bytes[i], flops=pr.flops[i], launches=pr.launches[i])
+                for i, name in enumerate(PHASES)}
 
     def point_sources(self, pts=None, device=False):
         pts = self.problem.sources if pts is None else pts
