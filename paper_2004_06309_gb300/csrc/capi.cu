@@ -149,8 +149,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     F.maxm = std::max(F.maxm, S.sn_m[s]);
   }
   const size_t vs = precision == 0 ? 16 : 8;
-  if (size_t(F.maxm) * vs > 227 * 1024)
-    return fail(c, HZ_ERR_ARG, "a supernode front is too large for the backward-solve staging; use more subdomains");
   TRY(upload(c, &F.sn, sn));
   TRY(upload(c, &F.rowlist, S.rowlist));
   TRY(upload(c, &F.cptr, S.cptr));
@@ -210,7 +208,9 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   }
   // task lists
   const int nlev = S.nlev;
-  std::vector<int2> fwd, bwd, wg, ea;
+  std::vector<int2> fwd, wg, ea;
+  std::vector<int4> bwd, bfin;
+  int64_t max_bwd_level = 0;
   std::vector<int4> cbt;
   std::vector<int64_t> scr_off(ns, 0);
   std::vector<std::vector<int32_t>> children(ns);
@@ -219,13 +219,14 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   int max_slot = 1;
   for (int s = 0; s < ns; s++) max_slot = std::max(max_slot, int(children[s].size()));
   F.max_slot = max_slot;
-  std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), wg_ptr(nlev + 1),
+  std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
       cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1);
   int64_t scratch = 0;
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
     fwd_ptr[l] = int64_t(fwd.size());
     bwd_ptr[l] = int64_t(bwd.size());
+    bfin_ptr[l] = int64_t(bfin.size());
     wg_ptr[l] = int64_t(wg.size());
     cb_ptr[l] = int64_t(cbt.size());
     int64_t lev_scr = 0;
@@ -233,7 +234,11 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
       for (int rb = 0; rb * 64 < m; rb++) fwd.push_back(make_int2(s, rb));
-      for (int cb = 0; cb * 32 < k; cb++) bwd.push_back(make_int2(s, cb));
+      const int nch = (m + 511) / 512;
+      for (int cb = 0; cb * 32 < k; cb++) {
+        bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
+        for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, 0));
+      }
       for (int rb = 0; rb * 32 < r; rb++) wg.push_back(make_int2(s, rb));
       const int T = (r + 31) / 32;
       for (int ti = 0; ti < T; ti++)
@@ -242,6 +247,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
       lev_scr += int64_t(r) * k;
     }
     scratch = std::max(scratch, lev_scr);
+    max_bwd_level = std::max(max_bwd_level, int64_t(bwd.size()) - bwd_ptr[l]);
     for (int q = 0; q < max_slot; q++) {
       ea_ptr[int64_t(l) * max_slot + q] = int64_t(ea.size());
       for (int32_t z = S.lev_ptr[l]; z < S.lev_ptr[l + 1]; z++) {
@@ -257,12 +263,14 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   lev_ptr[nlev] = S.lev_ptr[nlev];
   fwd_ptr[nlev] = int64_t(fwd.size());
   bwd_ptr[nlev] = int64_t(bwd.size());
+  bfin_ptr[nlev] = int64_t(bfin.size());
   wg_ptr[nlev] = int64_t(wg.size());
   cb_ptr[nlev] = int64_t(cbt.size());
   ea_ptr[int64_t(nlev) * max_slot] = int64_t(ea.size());
   F.scratch_elems = scratch;
   TRY(upload(c, &F.fwd_tasks, fwd));
   TRY(upload(c, &F.bwd_tasks, bwd));
+  TRY(upload(c, &F.bfin_tasks, bfin));
   TRY(upload(c, &F.wg_tasks, wg));
   TRY(upload(c, &F.cb_tasks, cbt));
   TRY(upload(c, &F.ea_tasks, ea));
@@ -276,6 +284,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_lev_ptr = hcopy(lev_ptr);
   F.h_fwd_ptr = hcopy(fwd_ptr);
   F.h_bwd_ptr = hcopy(bwd_ptr);
+  F.h_bfin_ptr = hcopy(bfin_ptr);
   F.h_wg_ptr = hcopy(wg_ptr);
   F.h_cb_ptr = hcopy(cb_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
@@ -287,6 +296,9 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   TRY(dalloc(c, (char**)&zl, F.ntot * int64_t(vs)));
   TRY(dalloc(c, (char**)&xl, F.ntot * int64_t(vs)));
   TRY(dalloc(c, (char**)&uw, std::max<int64_t>(F.u_elems, 1) * int64_t(vs)));
+  void* bp = nullptr;
+  TRY(dalloc(c, (char**)&bp, std::max<int64_t>(max_bwd_level, 1) * 32 * int64_t(vs)));
+  F.bwd_partial = bp;
   F.panels = pan;
   F.t_loc = tl;
   F.z_loc = zl;
@@ -299,11 +311,12 @@ void free_host_ptrs(hz::FactorDev& F) {
   delete[] F.h_lev_ptr;
   delete[] F.h_fwd_ptr;
   delete[] F.h_bwd_ptr;
+  delete[] F.h_bfin_ptr;
   delete[] F.h_wg_ptr;
   delete[] F.h_cb_ptr;
   delete[] F.h_ea_ptr;
   delete[] F.h_ent_ptr;
-  F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;
+  F.h_bfin_ptr = F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;
 }
 
 hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[3], double& min_pivot) {
@@ -597,7 +610,7 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     for (int64_t k = 0; k < P.nH; k++) gid[k] = k;
     hz::MatrixInput mi{&P.E, coords.data(), gid.data(), one.data()};
     phase("coarse space", tp);
-    hz::symbolic_batch({mi}, leaf, std::min(maxsn, 112), P.coarse);
+    hz::symbolic_batch({mi}, leaf, 112, P.coarse);
     phase("coarse symbolic", tp);
   }
   return HZ_OK;

@@ -38,7 +38,9 @@ struct FactorDev {
   double2* eb = nullptr;
   // task arrays (device) and per-level host offsets
   int2* fwd_tasks = nullptr;     // (sn, row block)
-  int2* bwd_tasks = nullptr;     // (sn, col block)
+  int4* bwd_tasks = nullptr;     // (sn, col block, row chunk, -): partial sums
+  int4* bfin_tasks = nullptr;    // (sn, col block, first partial task of the level, chunks)
+  void* bwd_partial = nullptr;   // 32 values per backward partial task (max over levels)
   int2* ea_tasks = nullptr;      // (child sn, col block)
   int2* wg_tasks = nullptr;      // (sn, row block of the off-diagonal part)
   int4* cb_tasks = nullptr;      // (sn, row tile, col tile, scratch-relative offset unused)
@@ -47,6 +49,7 @@ struct FactorDev {
   int64_t* h_lev_ptr = nullptr;       // nlev + 1 (host)
   int64_t* h_fwd_ptr = nullptr;       // nlev + 1
   int64_t* h_bwd_ptr = nullptr;
+  int64_t* h_bfin_ptr = nullptr;
   int64_t* h_wg_ptr = nullptr;
   int64_t* h_cb_ptr = nullptr;
   int64_t* h_ea_ptr = nullptr;        // nlev * maxslot + 1, grouped (level, slot)

@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
   V acc = czero<V>();
   if (r < m) {
     const int jmax = min(r, k);
+#pragma unroll 4
     for (int j = cg; j < jmax; j += 4) acc = cmad(P[r + int64_t(j) * m], b1[j], acc);
   }
   part[cg][rr] = acc;
@@ -444,29 +445,48 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
   }
 }
 
-// Backward, 32 pivot columns of one supernode per task:
-//   x[j] = z[j] + sum_{j<r<k} T[r][j] z[r] - sum_{r>=k} G[r][j] x[row r].
+// Backward, split over row chunks so that tall supernodes use many CTAs:
+//   partial[task][c] = sum over the task's rows r > j of P[r][j] vec[r],
+//   vec = (z, -x[ancestor rows]) for 32 pivot columns j of one supernode;
+// then x[j] = z[j] + sum of the partials in chunk order (deterministic).
+constexpr int kBwdRows = 512;
 template <typename V>
-__global__ void __launch_bounds__(256) k_bwd(const int2* tasks, const SnDev* sn, const int32_t* rowlist,
-                                             const V* panels, const V* zin, V* x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* vec = reinterpret_cast<V*>(smem_raw);
-  const int2 t = tasks[blockIdx.x];
+__global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const SnDev* sn, const int32_t* rowlist,
+                                                     const V* panels, const V* zin, const V* x, V* partial) {
+  __shared__ V vec[kBwdRows];
+  const int4 t = tasks[blockIdx.x];            // (sn, column block, row chunk, -)
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r0 = t.z * kBwdRows, r1 = min(m, r0 + kBwdRows);
   const int32_t* rl = rowlist + S.rowoff;
-  for (int r = tid; r < m; r += blockDim.x) vec[r] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
+  for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
   __syncthreads();
   const V* P = panels + S.paneloff;
+  V* out = partial + int64_t(blockIdx.x) * 32;
   for (int q = 0; q < 4; q++) {
-    const int j = t.y * 32 + wid + 8 * q;
-    if (j >= k) break;
-    V acc = (lane == 0) ? vec[j] : czero<V>();
-    const V* col = P + int64_t(j) * m;
-    for (int r = j + 1 + lane; r < m; r += 32) acc = cmad(col[r], vec[r], acc);
+    const int c = wid + 8 * q;
+    const int j = t.y * 32 + c;
+    V acc = czero<V>();
+    if (j < k) {
+      const V* col = P + int64_t(j) * m;
+#pragma unroll 4
+      for (int r = max(r0, j + 1) + lane; r < r1; r += 32) acc = cmad(col[r], vec[r - r0], acc);
+    }
     acc = warp_sum(acc);
-    if (lane == 0) x[S.first + j] = acc;
+    if (lane == 0) out[c] = acc;
   }
+}
+
+template <typename V>
+__global__ void k_bwd_final(const int4* tasks, const SnDev* sn, const V* zin, const V* partial, V* x) {
+  const int4 t = tasks[blockIdx.x];            // (sn, column block, first partial task, chunks)
+  const SnDev S = sn[t.x];
+  const int c = threadIdx.x;
+  const int j = t.y * 32 + c;
+  if (c >= 32 || j >= S.k) return;
+  V acc = zin[S.first + j];
+  for (int q = 0; q < t.w; q++) acc = cadd(acc, partial[int64_t(t.z + q) * 32 + c]);
+  x[S.first + j] = acc;
 }
 
 template <typename V>
@@ -485,16 +505,12 @@ __global__ void k_prolong(int64_t n, const int64_t* pptr, const int32_t* pidx, c
 
 template <typename V>
 static void solve_t(const FactorDev& F, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bwd<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr = true;
-  }
   const V* P = (const V*)F.panels;
   V* t = (V*)F.t_loc;
   V* z = (V*)F.z_loc;
   V* x = (V*)F.x_loc;
   V* u = (V*)F.u_ws;
+  V* part = (V*)F.bwd_partial;
   for (int l = 0; l < F.nlev; l++) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
@@ -502,12 +518,16 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
   }
-  const size_t sm = size_t(F.maxm) * sizeof(V);
   for (int l = F.nlev - 1; l >= 0; l--) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
-      k_bwd<V><<<unsigned(e - b), 256, sm, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x);
+      k_bwd_partial<V><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part);
+    }
+    const int64_t fb = F.h_bfin_ptr[l], fe = F.h_bfin_ptr[l + 1];
+    if (fe > fb) {
+      HZ_COUNT();
+      k_bwd_final<V><<<unsigned(fe - fb), 32, 0, st>>>(F.bfin_tasks + fb, F.sn, z, part, x);
     }
   }
 }
