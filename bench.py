@@ -32,6 +32,8 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal, from the platform f
 WORKLOADS = {
     "overthrust-5hz": dict(kind="overthrust", cells=(50, 50, 12), freq=5.0, nsub=64, overlap=2,
                            restart=50),
+    "overthrust-medium": dict(kind="overthrust", cells=(24, 24, 6), freq=2.5, nsub=16, overlap=2,
+                              restart=50),
     "overthrust-small": dict(kind="overthrust", cells=(12, 12, 3), freq=1.2, nsub=8, overlap=2,
                              restart=50),
     "tiny": dict(kind="tiny"),

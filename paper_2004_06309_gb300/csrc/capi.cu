@@ -122,8 +122,9 @@ std::vector<double2> to_d2(const std::vector<cplx>& v) {
 
 // Device copy of a symbolic set with its task lists.
 hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
-                        double maxabs[3]) {
+                        double maxabs[3], int bwd_rows) {
   F = hz::FactorDev();
+  F.bwd_rows = bwd_rows;
   F.precision = precision;
   F.nmat = S.nmat;
   F.nsn = int(S.sn_k.size());
@@ -234,7 +235,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
       for (int rb = 0; rb * 64 < m; rb++) fwd.push_back(make_int2(s, rb));
-      const int nch = (m + 511) / 512;
+      const int nch = (m + bwd_rows - 1) / bwd_rows;
       for (int cb = 0; cb * 32 < k; cb++) {
         bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
         for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, 0));
@@ -712,7 +713,10 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
   SETUP_TRY(upload(c, &c->d_M, to_d2(P.A.M)));
   SETUP_TRY(upload(c, &c->d_B, to_d2(P.A.B)));
   SETUP_TRY(dalloc(c, &c->d_A, c->nnz));
-  SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max));
+  // backward row chunks: long ones where the sweep streams complex64 panels from HBM,
+  // short ones where it is limited by FP64 arithmetic (more CTAs per supernode)
+  SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max,
+                          op->precision == HZ_MIXED ? 512 : 256));
   if (c->levels == 2) {
     SETUP_TRY(upload(c, &c->d_Zrp, P.Z.ptr));
     SETUP_TRY(upload(c, &c->d_Zci, P.Z.col));
@@ -720,7 +724,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     SETUP_TRY(upload(c, &c->d_Ztrp, P.Zt.ptr));
     SETUP_TRY(upload(c, &c->d_Ztci, P.Zt.col));
     SETUP_TRY(upload(c, &c->d_Ztv, P.Ztv));
-    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max));
+    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 128));
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));
   }

@@ -18,6 +18,7 @@ struct SnDev {
 struct FactorDev {
   int nmat = 0, nsn = 0, nlev = 0;
   int32_t maxk = 0, maxm = 0;
+  int32_t bwd_rows = 512;        // rows per backward partial task (<= 512)
   int64_t ntot = 0, nrows = 0, panel_elems = 0, u_elems = 0, front_elems = 0, nentries = 0;
   SnDev* sn = nullptr;
   int32_t* rowlist = nullptr;

@@ -452,12 +452,13 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
 constexpr int kBwdRows = 512;
 template <typename V>
 __global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const SnDev* sn, const int32_t* rowlist,
-                                                     const V* panels, const V* zin, const V* x, V* partial) {
+                                                     const V* panels, const V* zin, const V* x, V* partial,
+                                                     int rows) {
   __shared__ V vec[kBwdRows];
   const int4 t = tasks[blockIdx.x];            // (sn, column block, row chunk, -)
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int r0 = t.z * kBwdRows, r1 = min(m, r0 + kBwdRows);
+  const int r0 = t.z * rows, r1 = min(m, r0 + rows);
   const int32_t* rl = rowlist + S.rowoff;
   for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
   __syncthreads();
@@ -522,7 +523,8 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
-      k_bwd_partial<V><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part);
+      k_bwd_partial<V><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                         F.bwd_rows);
     }
     const int64_t fb = F.h_bfin_ptr[l], fe = F.h_bfin_ptr[l + 1];
     if (fe > fb) {
@@ -623,83 +625,88 @@ void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const dou
 // ---------------------------------------------------------------------------
 // GMRES: fused CGS passes and small dense updates
 // ---------------------------------------------------------------------------
-constexpr int kCgsRows = 32;
 constexpr int kMaxCols = 64;
 constexpr int kPartStride = kMaxCols + 1;
 int cgs_blocks() { return 152 * 4; }
 
-// One pass over V (n x ncols, column-major, ld ldv) and w:
-//   if h: w <- w - V h (in place);  partial[b][j] = sum conj(V[:,j]) w  (j < ndot);
-//   partial[b][64] = sum |w|^2.
-__global__ void __launch_bounds__(256) k_cgs(int64_t n, int ncols, const double2* V, int64_t ldv,
-                                             const double2* h, double2* w, int ndot, double2* partial,
-                                             int64_t chunk) {
-  __shared__ double2 Vt[kCgsRows * kMaxCols];
-  __shared__ double2 hs[kMaxCols];
-  __shared__ double2 red[8][kCgsRows];
-  __shared__ double2 ws[kCgsRows];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+// Multi-dot: partial[b][j] = sum over the block's rows of conj(V[r][j]) w[r] (j < ncols);
+// partial[b][64] = sum |w[r]|^2.  One warp per column, lanes over rows.
+__global__ void __launch_bounds__(256) k_mdot(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
+                                              const double2* __restrict__ w, double2* partial, int64_t chunk) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = blockIdx.x * chunk;
   const int64_t row1 = min(n, row0 + chunk);
-  const int nld = h ? ncols : ndot;
-  if (h)
-    for (int j = tid; j < ncols; j += blockDim.x) hs[j] = h[j];
-  double2 acc[8];
-  for (int q = 0; q < 8; q++) acc[q] = make_double2(0.0, 0.0);
-  double nrm = 0.0;
-  for (int64_t base = row0; base < row1; base += kCgsRows) {
-    const int nr = int(min(int64_t(kCgsRows), row1 - base));
-    for (int e = tid; e < kCgsRows * nld; e += blockDim.x) {
-      const int r = e % kCgsRows, j = e / kCgsRows;
-      Vt[e] = (r < nr) ? V[base + r + int64_t(j) * ldv] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    if (h) {
-      double2 p = make_double2(0.0, 0.0);
-      for (int j = wid; j < ncols; j += 8) p = cmad(Vt[lane + kCgsRows * j], hs[j], p);
-      red[wid][lane] = p;
-      __syncthreads();
-      if (wid == 0) {
-        double2 s = red[0][lane];
-        for (int q = 1; q < 8; q++) s = cadd(s, red[q][lane]);
-        double2 wv = make_double2(0.0, 0.0);
-        if (lane < nr) {
-          wv = csub(w[base + lane], s);
-          w[base + lane] = wv;
-        }
-        ws[lane] = wv;
-      }
-    } else if (wid == 0) {
-      ws[lane] = (lane < nr) ? w[base + lane] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    const double2 wl = ws[lane];
-    for (int q = 0; q < 8; q++) {
-      const int j = wid + 8 * q;
-      if (j < ndot) acc[q] = cmadc(Vt[lane + kCgsRows * j], wl, acc[q]);
-    }
-    if (wid == 0) nrm = xfma(wl.x, wl.x, xfma(wl.y, wl.y, nrm));
-    __syncthreads();
-  }
   double2* out = partial + int64_t(blockIdx.x) * kPartStride;
-  for (int q = 0; q < 8; q++) {
-    const int j = wid + 8 * q;
-    const double2 v = warp_sum(acc[q]);
-    if (lane == 0 && j < kMaxCols) out[j] = (j < ndot) ? v : make_double2(0.0, 0.0);
+  for (int j = wid; j < kMaxCols; j += 8) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (j < ncols) {
+      const double2* col = V + int64_t(j) * ldv;
+#pragma unroll 4
+      for (int64_t r = row0 + lane; r < row1; r += 32) acc = cmadc(col[r], w[r], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[j] = acc;
   }
   if (wid == 0) {
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    if (lane == 0) out[kMaxCols] = make_double2(nrm, 0.0);
+    double s = 0.0;
+    for (int64_t r = row0 + lane; r < row1; r += 32) {
+      const double2 v = w[r];
+      s = xfma(v.x, v.x, xfma(v.y, v.y, s));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[kMaxCols] = make_double2(s, 0.0);
   }
 }
 
+// Multi-axpy: w[r] -= sum_j V[r][j] h[j]; partial[b][64] = sum |w[r]|^2 (new w).
+__global__ void __launch_bounds__(256) k_maxpy(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
+                                               const double2* __restrict__ h, double2* w, double2* partial,
+                                               int64_t chunk) {
+  __shared__ double2 hs[kMaxCols];
+  __shared__ double red[8];
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  const int64_t row0 = blockIdx.x * chunk;
+  const int64_t row1 = min(n, row0 + chunk);
+  double s = 0.0;
+  for (int64_t r = row0 + threadIdx.x; r < row1; r += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 4
+    for (int j = 0; j < ncols; j++) acc = cmad(V[r + int64_t(j) * ldv], hs[j], acc);
+    const double2 v = csub(w[r], acc);
+    w[r] = v;
+    s = xfma(v.x, v.x, xfma(v.y, v.y, s));
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; q++) t += red[q];
+    partial[int64_t(blockIdx.x) * kPartStride + kMaxCols] = make_double2(t, 0.0);
+  }
+}
+
+static int64_t cgs_chunk(int64_t n) {
+  const int nb = cgs_blocks();
+  int64_t chunk = (n + nb - 1) / nb;
+  return (chunk + 31) / 32 * 32;
+}
+
+// ndot > 0 and h == null: dots of w with V (and |w|^2); h != null: w -= V h (and |w|^2),
+// followed by the dots of the updated w when ndot > 0.
 void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const double2* h, double2* w, int ndot,
                 double2* partial, cudaStream_t st) {
   const int nb = cgs_blocks();
-  int64_t chunk = (n + nb - 1) / nb;
-  chunk = (chunk + kCgsRows - 1) / kCgsRows * kCgsRows;
-  HZ_COUNT();
-  k_cgs<<<nb, 256, 0, st>>>(n, ncols, V, ldv, h, w, ndot, partial, chunk);
+  const int64_t chunk = cgs_chunk(n);
+  if (h) {
+    HZ_COUNT();
+    k_maxpy<<<nb, 256, 0, st>>>(n, ncols, V, ldv, h, w, partial, chunk);
+  }
+  if (ndot > 0 || !h) {
+    HZ_COUNT();
+    k_mdot<<<nb, 256, 0, st>>>(n, ndot, V, ldv, w, partial, chunk);
+  }
 }
 
 __global__ void k_reduce(const double2* partial, int nblk, double2* out) {
