@@ -130,25 +130,31 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.nsn = int(S.sn_k.size());
   F.nlev = S.nlev;
   F.ntot = S.voff.back();
-  F.panel_elems = S.panel_elems;
+  F.panel_elems = 0;   // set below from the padded layout
   F.u_elems = S.u_elems;
   F.front_elems = S.front_elems;
   F.nentries = int64_t(S.epos.size());
   F.nglob = nglob;
   const int ns = F.nsn;
   std::vector<hz::SnDev> sn(ns);
+  int64_t panel_off = 0;
   for (int s = 0; s < ns; s++) {
     sn[s].k = S.sn_k[s];
     sn[s].m = S.sn_m[s];
     sn[s].first = S.sn_first[s];
     sn[s].parent = S.sn_parent[s];
     sn[s].rowoff = S.sn_rowoff[s];
-    sn[s].paneloff = S.sn_paneloff[s];
+    // complex64 panels: columns padded to 4 rows (32 bytes) for 16-byte vector loads
+    sn[s].ld = precision == 0 ? S.sn_m[s] : (S.sn_m[s] + 3) / 4 * 4;
+    sn[s].pad_ = 0;
+    sn[s].paneloff = panel_off;
+    panel_off += int64_t(sn[s].ld) * S.sn_k[s];
     sn[s].uoff = S.sn_uoff[s];
     sn[s].frontoff = S.sn_frontoff[s];
     F.maxk = std::max(F.maxk, S.sn_k[s]);
     F.maxm = std::max(F.maxm, S.sn_m[s]);
   }
+  F.panel_elems = panel_off;
   const size_t vs = precision == 0 ? 16 : 8;
   TRY(upload(c, &F.sn, sn));
   TRY(upload(c, &F.rowlist, S.rowlist));

@@ -5,9 +5,10 @@
 
 namespace hz {
 
-// One supernode of a batched multifrontal factorisation (48 bytes).
+// One supernode of a batched multifrontal factorisation (56 bytes).
 struct SnDev {
   int32_t k, m, first, parent;   // pivots, front order, first vector index, parent (-1 root)
+  int32_t ld, pad_;              // panel leading dimension (m, or m rounded up to 4 for complex64)
   int64_t rowoff;                // into rowlist / cptr slots
   int64_t paneloff;              // panel (m x k, column-major, ld m) in the factor store
   int64_t uoff;                  // update vector (m - k) in the solve workspace

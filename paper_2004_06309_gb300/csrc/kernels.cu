@@ -317,10 +317,13 @@ __global__ void k_front_zero(const int32_t* lev_sn, const SnDev* sn, V* fronts) 
 template <typename V>
 __global__ void k_panel_copy(const int32_t* lev_sn, const SnDev* sn, const V* fronts, V* panels) {
   const SnDev S = sn[lev_sn[blockIdx.x]];
-  const int64_t cnt = int64_t(S.m) * S.k;
+  const int64_t cnt = int64_t(S.ld) * S.k;
   const V* src = fronts + S.frontoff;
   V* dst = panels + S.paneloff;
-  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) dst[e] = src[e];
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int64_t j = e / S.ld, r = e % S.ld;
+    dst[e] = (r < S.m) ? src[r + j * S.m] : czero<V>();    // padding rows are zero
+  }
 }
 
 static size_t diag_smem(int kmax, size_t vs) { return (size_t(kmax + 1) * kmax + 2 * kmax) * vs; }
@@ -429,14 +432,14 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
   if (r < m) {
     const int jmax = min(r, k);
 #pragma unroll 4
-    for (int j = cg; j < jmax; j += 4) acc = cmad(P[r + int64_t(j) * m], b1[j], acc);
+    for (int j = cg; j < jmax; j += 4) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
   }
   part[cg][rr] = acc;
   __syncthreads();
   if (cg == 0 && r < m) {
     const V tot = cadd(cadd(part[0][rr], part[1][rr]), cadd(part[2][rr], part[3][rr]));
     if (r < k) {
-      zout[S.first + r] = cmul(P[r + int64_t(r) * m], cadd(b1[r], tot));
+      zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
     } else {
       V b2 = czero<V>();
       for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
@@ -469,9 +472,96 @@ __global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const Sn
     const int j = t.y * 32 + c;
     V acc = czero<V>();
     if (j < k) {
-      const V* col = P + int64_t(j) * m;
+      const V* col = P + int64_t(j) * S.ld;
 #pragma unroll 4
       for (int r = max(r0, j + 1) + lane; r < r1; r += 32) acc = cmad(col[r], vec[r - r0], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[c] = acc;
+  }
+}
+
+// complex64 forward with 16-byte loads: each lane owns two consecutive rows of a
+// 64-row block, the eight warps split the pivot columns.
+__global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+                                                 const int64_t* cidx, const float2* panels, const float2* tin,
+                                                 float2* zout, float2* u) {
+  __shared__ float2 b1[kMaxK];
+  __shared__ float2 part[8][kFwdRows];
+  const int2 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t* cp = cptr + S.rowoff;
+  for (int j = tid; j < k; j += blockDim.x) {
+    float2 acc = tin[S.first + j];
+    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+    b1[j] = acc;
+  }
+  __syncthreads();
+  const int r = t.y * kFwdRows + 2 * lane;          // rows r, r + 1 (r even, ld % 4 == 0)
+  const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
+  const int64_t ld4 = S.ld / 2;
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+  if (r < m) {
+    const int j0 = min(r, k), j1 = min(r + 1, k);
+#pragma unroll 4
+    for (int j = wid; j < j1; j += 8) {
+      const float4 p = P4[int64_t(j) * ld4];
+      const float2 bj = b1[j];
+      a1 = cmad(make_float2(p.z, p.w), bj, a1);
+      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+    }
+  }
+  part[wid][2 * lane] = a0;
+  part[wid][2 * lane + 1] = a1;
+  __syncthreads();
+  if (tid < kFwdRows) {
+    const int rr = t.y * kFwdRows + tid;
+    if (rr < m) {
+      float2 tot = part[0][tid];
+      for (int q = 1; q < 8; q++) tot = cadd(tot, part[q][tid]);
+      const float2* P = panels + S.paneloff;
+      if (rr < k) {
+        zout[S.first + rr] = cmul(P[rr + int64_t(rr) * S.ld], cadd(b1[rr], tot));
+      } else {
+        float2 b2 = make_float2(0.f, 0.f);
+        for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+        u[S.uoff + (rr - k)] = csub(b2, tot);
+      }
+    }
+  }
+}
+
+// complex64 backward partial sums with 16-byte loads (two rows per lane).
+__global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, const SnDev* sn,
+                                                         const int32_t* rowlist, const float2* panels,
+                                                         const float2* zin, const float2* x, float2* partial,
+                                                         int rows) {
+  __shared__ __align__(16) float2 vec[kBwdRows + 2];
+  const int4 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r0 = t.z * rows, r1 = min(m, r0 + rows);
+  const int32_t* rl = rowlist + S.rowoff;
+  for (int r = r0 + tid; r < r0 + rows + 2; r += blockDim.x)
+    vec[r - r0] = (r < r1) ? ((r < k) ? zin[S.first + r] : cneg(x[rl[r]])) : make_float2(0.f, 0.f);
+  __syncthreads();
+  float2* out = partial + int64_t(blockIdx.x) * 32;
+  const float4* vec4 = reinterpret_cast<const float4*>(vec);
+  for (int q = 0; q < 4; q++) {
+    const int c = wid + 8 * q;
+    const int j = t.y * 32 + c;
+    float2 acc = make_float2(0.f, 0.f);
+    if (j < k) {
+      const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j) * S.ld);
+      const int rs = max(r0, (j + 1) & ~1);          // first even row of the pair holding row j + 1
+#pragma unroll 4
+      for (int r = rs + 2 * lane; r < r1; r += 64) {
+        const float4 p = col[r >> 1];
+        const float4 v = vec4[(r - r0) >> 1];
+        if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
+        acc = cmad(make_float2(p.z, p.w), make_float2(v.z, v.w), acc);
+      }
     }
     acc = warp_sum(acc);
     if (lane == 0) out[c] = acc;
@@ -516,15 +606,22 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
-      k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+      if constexpr (sizeof(V) == 8)
+        k_fwd_c64<<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+      else
+        k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
   }
   for (int l = F.nlev - 1; l >= 0; l--) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
-      k_bwd_partial<V><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                         F.bwd_rows);
+      if constexpr (sizeof(V) == 8)
+        k_bwd_partial_c64<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                           F.bwd_rows);
+      else
+        k_bwd_partial<V><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                           F.bwd_rows);
     }
     const int64_t fb = F.h_bfin_ptr[l], fe = F.h_bfin_ptr[l + 1];
     if (fe > fb) {
