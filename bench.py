@@ -212,7 +212,9 @@ def main():
 
     precs = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
     results = {}
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream, so that the library can capture its iterations as CUDA graphs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     for pname in precs:
         G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream)
         tf = time.time()

@@ -44,7 +44,11 @@ struct hz_ctx {
   double2 *rH = nullptr, *yH = nullptr;
   double2 *partial = nullptr, *h1 = nullptr, *h2 = nullptr, *nrm = nullptr;
   double2 *H = nullptr, *sn = nullptr, *g = nullptr, *ysol = nullptr;
-  double *cs = nullptr, *scal = nullptr;   // scal: est, invh, invbeta, beta
+  double *cs = nullptr, *scal = nullptr;   // scal: est, invh, invbeta, beta, |b|
+  // one CUDA graph per inner-iteration index j (captured on first use)
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<long long> gcount;
+  bool graphs = true;
   int* brk = nullptr;
   hz::DevStatus* status = nullptr;
   double* h_pin = nullptr;                 // pinned: est, invh, invbeta, beta, brk, norm
@@ -373,12 +377,6 @@ void apply_prec(hz_ctx* c, const double2* v, double2* z) {
   }
 }
 
-hz_status read_scalars(hz_ctx* c) {
-  CU(cudaMemcpyAsync(c->h_pin, c->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-  CU(cudaMemcpyAsync(c->h_pin + 4, c->brk, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  CU(cudaStreamSynchronize(c->st));
-  return HZ_OK;
-}
 
 hz_status norm2(hz_ctx* c, const double2* v, double& out) {
   const int nb = hz::cgs_blocks();
@@ -387,6 +385,64 @@ hz_status norm2(hz_ctx* c, const double2* v, double& out) {
   CU(cudaMemcpyAsync(c->h_pin + 5, &c->nrm[64].x, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CU(cudaStreamSynchronize(c->st));
   out = std::sqrt(c->h_pin[5]);
+  return HZ_OK;
+}
+
+// Kernels of inner iteration j: z_j = M^{-1} v_j, w = A z_j, CGS2 against v_0..v_j,
+// Givens update, v_{j+1} = w / h_{j+1,j}, and the copy of the residual estimate and
+// breakdown flag to pinned host memory.  The same sequence serves eager launches
+// and the capture of iteration j's CUDA graph.
+void iteration_kernels(hz_ctx* c, int j) {
+  const int64_t n = c->n;
+  const int m = c->restart;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  double2* vj = c->V + int64_t(j) * n;
+  double2* zj = c->Zs + int64_t(j) * n;
+  apply_prec(c, vj, zj);
+  hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, zj, nullptr, c->w, st);
+  hz::launch_cgs(n, j + 1, c->V, n, nullptr, c->w, j + 1, c->partial, st);   // h1, |w|
+  hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
+  hz::launch_cgs(n, j + 1, c->V, n, c->h1, c->w, j + 1, c->partial, st);     // w -= V h1; h2
+  hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
+  hz::launch_cgs(n, j + 1, c->V, n, c->h2, c->w, 0, c->partial, st);         // w -= V h2; |w|
+  hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+  hz::launch_givens(j, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, c->scal + 4, c->scal, c->brk,
+                    c->scal + 1, st);
+  hz::launch_scale(n, c->w, c->scal + 1, c->V + int64_t(j + 1) * n, st);
+  cudaMemcpyAsync(c->h_pin, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(c->h_pin + 4, c->brk, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+// Runs iteration j (as a CUDA graph when the stream can be captured) and waits for it.
+hz_status run_iteration(hz_ctx* c, int j) {
+  cudaStream_t st = c->st;
+  if (c->graphs && st != nullptr) {
+    if (!c->gexec[j]) {
+      const long long l0 = hz::launch_count();
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        iteration_kernels(c, j);
+        if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) {
+          if (cudaGraphInstantiate(&c->gexec[j], g, 0) != cudaSuccess) c->gexec[j] = nullptr;
+          cudaGraphDestroy(g);
+        }
+      }
+      cudaGetLastError();
+      c->gcount[j] = hz::launch_count() - l0;
+      hz::add_launches(-c->gcount[j]);          // capture itself launches nothing
+      if (!c->gexec[j]) c->graphs = false;     // this stream cannot be captured: stay eager
+    }
+    if (c->gexec[j]) {
+      CU(cudaGraphLaunch(c->gexec[j], st));
+      hz::add_launches(c->gcount[j]);
+      CU(cudaStreamSynchronize(st));
+      return HZ_OK;
+    }
+  }
+  iteration_kernels(c, j);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
   return HZ_OK;
 }
 
@@ -407,10 +463,10 @@ hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
     info->status = HZ_ERR_BREAKDOWN;
     return HZ_OK;
   }
-  double* d_est = c->scal;
-  double* d_invh = c->scal + 1;
   double* d_invbeta = c->scal + 2;
   double* d_beta = c->scal + 3;
+  c->h_pin[6] = bnorm;
+  CU(cudaMemcpyAsync(c->scal + 4, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
   // r = b
   hz::launch_axpby_copy(n, c->b, c->w, st);
   hz::launch_cgs(n, 0, c->V, n, nullptr, c->w, 0, c->partial, st);
@@ -422,18 +478,7 @@ hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
     int k = 0;
     bool stop_nonfinite = false;
     for (int j = 0; j < m; j++) {
-      double2* vj = c->V + int64_t(j) * n;
-      double2* zj = c->Zs + int64_t(j) * n;
-      apply_prec(c, vj, zj);
-      hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, zj, nullptr, c->w, st);
-      hz::launch_cgs(n, j + 1, c->V, n, nullptr, c->w, j + 1, c->partial, st);   // h1, |w|
-      hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
-      hz::launch_cgs(n, j + 1, c->V, n, c->h1, c->w, j + 1, c->partial, st);     // w -= V h1; h2
-      hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
-      hz::launch_cgs(n, j + 1, c->V, n, c->h2, c->w, 0, c->partial, st);         // w -= V h2; |w|
-      hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
-      hz::launch_givens(j, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, bnorm, d_est, c->brk, d_invh, st);
-      TRY(read_scalars(c));
+      TRY(run_iteration(c, j));
       its++;
       k = j + 1;
       const double est = c->h_pin[0];
@@ -441,7 +486,6 @@ hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
       std::memcpy(&brk, c->h_pin + 4, sizeof(int));
       if (!std::isfinite(est)) { stop_nonfinite = true; break; }
       if (brk || est <= tol || its >= c->max_iter) break;
-      hz::launch_scale(n, c->w, d_invh, c->V + int64_t(j + 1) * n, st);
     }
     if (stop_nonfinite) {
       info->iterations = its;
@@ -514,6 +558,8 @@ void hz_free(hz_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   c->sizes.clear();
+  for (cudaGraphExec_t g : c->gexec)
+    if (g) cudaGraphExecDestroy(g);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   free_host_ptrs(c->loc);
   free_host_ptrs(c->crs);
@@ -752,7 +798,10 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
   SETUP_TRY(dalloc(c, &c->g, m + 1));
   SETUP_TRY(dalloc(c, &c->ysol, m));
   SETUP_TRY(dalloc(c, &c->cs, m));
-  SETUP_TRY(dalloc(c, &c->scal, 4));
+  SETUP_TRY(dalloc(c, &c->scal, 8));
+  c->gexec.assign(m, nullptr);
+  c->gcount.assign(m, 0);
+  c->graphs = std::getenv("HZ_NO_GRAPHS") == nullptr;
   SETUP_TRY(dalloc(c, &c->brk, 1));
   SETUP_TRY(dalloc(c, &c->status, 1));
   if (cudaMallocHost((void**)&c->h_pin, 8 * sizeof(double)) != cudaSuccess) {
@@ -871,6 +920,8 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   hz::launch_cgs(n, 0, c->V, n, nullptr, c->b, 0, c->partial, st);
   hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
   hz::launch_init_cycle(c->nrm, c->g, m, c->scal + 2, c->scal + 3, st);
+  c->h_pin[6] = 1.0;
+  CU(cudaMemcpyAsync(c->scal + 4, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
   const double nt = 16.0;
   auto run = [&](int ph) {
     switch (ph) {
@@ -906,7 +957,8 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
         hz::launch_reduce(c->partial, nb, jj + 1, c->h2, st);
         hz::launch_cgs(n, jj + 1, c->V, n, c->h2, c->w, 0, c->partial, st);
         hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
-        hz::launch_givens(0, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, 1.0, c->scal, c->brk, c->scal + 1, st);
+        hz::launch_givens(0, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, c->scal + 4, c->scal, c->brk,
+                          c->scal + 1, st);
         hz::launch_scale(n, c->w, c->scal + 1, c->V + int64_t(jj + 1) * n, st);
         break;
       }

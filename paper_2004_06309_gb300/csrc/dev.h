@@ -81,6 +81,7 @@ struct DevStatus {
 
 // ---- launchers (kernels.cu) -------------------------------------------------
 long long launch_count();
+void add_launches(long long n);   // kernels replayed inside a CUDA graph launch
 void launch_fill_values(int64_t nnz, const double* K, const double2* M, const double2* B, double w,
                         double2* out, cudaStream_t st);
 // One assembly-tree level: zero and fill its fronts (A_i(omega) entries), extend-add the
@@ -101,7 +102,7 @@ void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const doubl
                 int ndot, double2* partial, cudaStream_t st);
 void launch_reduce(const double2* partial, int nblk, int ncols, double2* out, cudaStream_t st);
 void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
-                   const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown,
+                   const double2* h2, const double2* nrm, const double* bnorm, double* est, int* breakdown,
                    double* invh, cudaStream_t st);
 void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta, cudaStream_t st);
 void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st);

@@ -24,6 +24,7 @@ namespace hz {
 // Kernel launches issued by this library (for the launch count in hz_stats).
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 #define HZ_COUNT() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 // ---------------------------------------------------------------------------
@@ -569,15 +570,20 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
 }
 
 template <typename V>
-__global__ void k_bwd_final(const int4* tasks, const SnDev* sn, const V* zin, const V* partial, V* x) {
+__global__ void __launch_bounds__(256) k_bwd_final(const int4* tasks, const SnDev* sn, const V* zin,
+                                                   const V* partial, V* x) {
   const int4 t = tasks[blockIdx.x];            // (sn, column block, first partial task, chunks)
   const SnDev S = sn[t.x];
-  const int c = threadIdx.x;
-  const int j = t.y * 32 + c;
-  if (c >= 32 || j >= S.k) return;
-  V acc = zin[S.first + j];
-  for (int q = 0; q < t.w; q++) acc = cadd(acc, partial[int64_t(t.z + q) * 32 + c]);
-  x[S.first + j] = acc;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 4; q++) {
+    const int c = wid + 8 * q;
+    const int j = t.y * 32 + c;
+    if (j >= S.k) break;
+    V acc = czero<V>();
+    for (int ch = lane; ch < t.w; ch += 32) acc = cadd(acc, partial[int64_t(t.z + ch) * 32 + c]);
+    acc = warp_sum(acc);
+    if (lane == 0) x[S.first + j] = cadd(zin[S.first + j], acc);
+  }
 }
 
 template <typename V>
@@ -626,7 +632,7 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     const int64_t fb = F.h_bfin_ptr[l], fe = F.h_bfin_ptr[l + 1];
     if (fe > fb) {
       HZ_COUNT();
-      k_bwd_final<V><<<unsigned(fe - fb), 32, 0, st>>>(F.bfin_tasks + fb, F.sn, z, part, x);
+      k_bwd_final<V><<<unsigned(fe - fb), 256, 0, st>>>(F.bfin_tasks + fb, F.sn, z, part, x);
     }
   }
 }
@@ -806,18 +812,26 @@ void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const doubl
   }
 }
 
-__global__ void k_reduce(const double2* partial, int nblk, double2* out) {
-  const int j = threadIdx.x;
-  if (j > kMaxCols) return;
+// out[j] = sum over blocks of partial[b][j]; one CTA per j, fixed-order tree.
+__global__ void __launch_bounds__(256) k_reduce(const double2* partial, int nblk, double2* out) {
+  __shared__ double2 red[256];
+  const int j = blockIdx.x;
   double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; b++) s = cadd(s, partial[int64_t(b) * kPartStride + j]);
-  out[j] = s;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s = cadd(s, partial[int64_t(b) * kPartStride + j]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = red[0];
 }
 
+// Sums all 65 slots (columns and the norm slot 64).
 void launch_reduce(const double2* partial, int nblk, int ncols, double2* out, cudaStream_t st) {
   (void)ncols;
   HZ_COUNT();
-  k_reduce<<<1, 96, 0, st>>>(partial, nblk, out);
+  k_reduce<<<kMaxCols + 1, 256, 0, st>>>(partial, nblk, out);
 }
 
 // Complex Givens rotation zeroing b: rho = sqrt(|a|^2+|b|^2), c = |a|/rho,
@@ -838,8 +852,9 @@ __device__ void givens_cs(double2 a, double2 b, double& c, double2& s) {
 }
 
 __global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
-                         const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown,
-                         double* invh) {
+                         const double2* h2, const double2* nrm, const double* bnorm_p, double* est,
+                         int* breakdown, double* invh) {
+  const double bnorm = *bnorm_p;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double2* col = H + int64_t(j) * (m + 1);
   for (int i = 0; i <= j; i++) col[i] = cadd(h1[i], h2[i]);
@@ -869,8 +884,8 @@ __global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, doub
 }
 
 void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
-                   const double2* h2, const double2* nrm, double bnorm, double* est, int* breakdown, double* invh,
-                   cudaStream_t st) {
+                   const double2* h2, const double2* nrm, const double* bnorm, double* est, int* breakdown,
+                   double* invh, cudaStream_t st) {
   HZ_COUNT();
   k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, h1, h2, nrm, bnorm, est, breakdown, invh);
 }

@@ -148,3 +148,25 @@ def test_one_subdomain_is_one_iteration(hzmod):
     x, info = G.solve(S.rhs()[:, 0])
     assert info[0][0] == 1 and info[0][2] < 1e-10
     G.close()
+
+
+def test_graph_path_matches_eager_path(hzmod):
+    """On a non-default stream every inner iteration runs as a captured CUDA graph; the
+    result must be bitwise identical to the eager launches on the default stream."""
+    import torch
+    p = synth.small_overthrust(levels=2, cells=(4, 4, 2), freq=0.5, nsub=8)
+    S = OracleSolver(p)
+    b = S.rhs()[:, 0]
+    G0 = hzmod.Solver(p)
+    G0.factor()
+    x0, i0 = G0.solve(b)
+    G0.close()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        G1 = hzmod.Solver(p, stream=s)
+        G1.factor()
+        x1, i1 = G1.solve(b)
+        x2, i2 = G1.solve(b)           # second solve replays the captured graphs
+        G1.close()
+    assert i0 == i1 == i2
+    assert np.array_equal(x0, x1) and np.array_equal(x1, x2)
