@@ -463,78 +463,54 @@ __global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const Sn
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
-  // each warp carries four columns; their first elements are loaded before staging
-  const V* col[4];
-  int jc[4];
-  V pf[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    jc[q] = t.y * 32 + wid + 8 * q;
-    col[q] = panels + S.paneloff + int64_t(min(jc[q], k - 1)) * S.ld;
-    const int rf = max(r0, jc[q] + 1) + lane;
-    pf[q] = (jc[q] < k && rf < r1) ? col[q][rf] : czero<V>();
-  }
   const int32_t* rl = rowlist + S.rowoff;
   for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
   __syncthreads();
+  const V* P = panels + S.paneloff;
   V* out = partial + int64_t(blockIdx.x) * 32;
-#pragma unroll
   for (int q = 0; q < 4; q++) {
+    const int c = wid + 8 * q;
+    const int j = t.y * 32 + c;
     V acc = czero<V>();
-    if (jc[q] < k) {
-      int r = max(r0, jc[q] + 1) + lane;
-      V p = pf[q];
-      while (r < r1) {
-        const int rn = r + 32;
-        const V pn = (rn < r1) ? col[q][rn] : czero<V>();
-        acc = cmad(p, vec[r - r0], acc);
-        p = pn;
-        r = rn;
-      }
+    if (j < k) {
+      const V* col = P + int64_t(j) * S.ld;
+#pragma unroll 4
+      for (int r = max(r0, j + 1) + lane; r < r1; r += 32) acc = cmad(col[r], vec[r - r0], acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) out[wid + 8 * q] = acc;
+    if (lane == 0) out[c] = acc;
   }
 }
 
 // complex64 forward with 16-byte loads: each lane owns two consecutive rows of a
-// 64-row block, the eight warps split the pivot columns.  The panel values are
-// loaded into registers right after the supernode descriptor, so that the HBM
-// stream overlaps the dependent gathers that assemble the right-hand side b1.
+// 64-row block, the eight warps split the pivot columns.
 __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                                  const int64_t* cidx, const float2* panels, const float2* tin,
                                                  float2* zout, float2* u) {
-  constexpr int Q = kMaxK / 8;
   __shared__ float2 b1[kMaxK];
   __shared__ float2 part[8][kFwdRows];
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t* cp = cptr + S.rowoff;
+  for (int j = tid; j < k; j += blockDim.x) {
+    float2 acc = tin[S.first + j];
+    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+    b1[j] = acc;
+  }
+  __syncthreads();
   const int r = t.y * kFwdRows + 2 * lane;          // rows r, r + 1 (r even, ld % 4 == 0)
   const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
   const int64_t ld4 = S.ld / 2;
-  const int j0 = min(r, k), j1 = (r < m) ? min(r + 1, k) : 0;
-  float4 pv[Q];
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const int j = wid + 8 * q;
-    pv[q] = (j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  const int64_t* cp = cptr + S.rowoff;
-  for (int jj = tid; jj < k; jj += blockDim.x) {
-    float2 acc = tin[S.first + jj];
-    for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
-    b1[jj] = acc;
-  }
-  __syncthreads();
   float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const int j = wid + 8 * q;
-    if (j < j1) {
+  if (r < m) {
+    const int j0 = min(r, k), j1 = min(r + 1, k);
+#pragma unroll 4
+    for (int j = wid; j < j1; j += 8) {
+      const float4 p = P4[int64_t(j) * ld4];
       const float2 bj = b1[j];
-      a1 = cmad(make_float2(pv[q].z, pv[q].w), bj, a1);
-      if (j < j0) a0 = cmad(make_float2(pv[q].x, pv[q].y), bj, a0);
+      a1 = cmad(make_float2(p.z, p.w), bj, a1);
+      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
     }
   }
   part[wid][2 * lane] = a0;
@@ -557,9 +533,7 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
   }
 }
 
-// complex64 backward partial sums with 16-byte loads (two rows per lane); each
-// warp carries four columns at once, and its first row pair is loaded before the
-// right-hand side is staged.
+// complex64 backward partial sums with 16-byte loads (two rows per lane).
 __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, const SnDev* sn,
                                                          const int32_t* rowlist, const float2* panels,
                                                          const float2* zin, const float2* x, float2* partial,
@@ -569,43 +543,29 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
-  const float4* col[4];
-  int jc[4], rs[4];
-  float4 pf[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    jc[q] = t.y * 32 + wid + 8 * q;
-    const int jq = min(jc[q], k - 1);
-    col[q] = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(jq) * S.ld);
-    rs[q] = max(r0, (jc[q] + 1) & ~1);                 // first even row of the pair holding row j + 1
-    const int rf = rs[q] + 2 * lane;
-    pf[q] = (jc[q] < k && rf < r1) ? col[q][rf >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
   const int32_t* rl = rowlist + S.rowoff;
   for (int r = r0 + tid; r < r0 + rows + 2; r += blockDim.x)
     vec[r - r0] = (r < r1) ? ((r < k) ? zin[S.first + r] : cneg(x[rl[r]])) : make_float2(0.f, 0.f);
   __syncthreads();
-  const float4* vec4 = reinterpret_cast<const float4*>(vec);
   float2* out = partial + int64_t(blockIdx.x) * 32;
-#pragma unroll
+  const float4* vec4 = reinterpret_cast<const float4*>(vec);
   for (int q = 0; q < 4; q++) {
+    const int c = wid + 8 * q;
+    const int j = t.y * 32 + c;
     float2 acc = make_float2(0.f, 0.f);
-    if (jc[q] < k) {
-      const int j = jc[q];
-      int r = rs[q] + 2 * lane;
-      float4 p = pf[q];
-      while (r < r1) {
-        const int rn = r + 64;
-        const float4 pn = (rn < r1) ? col[q][rn >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < k) {
+      const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j) * S.ld);
+      const int rs = max(r0, (j + 1) & ~1);          // first even row of the pair holding row j + 1
+#pragma unroll 4
+      for (int r = rs + 2 * lane; r < r1; r += 64) {
+        const float4 p = col[r >> 1];
         const float4 v = vec4[(r - r0) >> 1];
         if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
         acc = cmad(make_float2(p.z, p.w), make_float2(v.z, v.w), acc);
-        p = pn;
-        r = rn;
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) out[wid + 8 * q] = acc;
+    if (lane == 0) out[c] = acc;
   }
 }
 
