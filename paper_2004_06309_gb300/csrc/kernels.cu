@@ -483,7 +483,9 @@ __global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const Sn
 }
 
 // complex64 forward with 16-byte loads: each lane owns two consecutive rows of a
-// 64-row block, the eight warps split the pivot columns.
+// 64-row block, the eight warps split the pivot columns.  Panel loads run in a
+// 4-deep software pipeline whose first batch is issued before the dependent
+// gathers that assemble the right-hand side b1.
 __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                                  const int64_t* cidx, const float2* panels, const float2* tin,
                                                  float2* zout, float2* u) {
@@ -492,25 +494,38 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r = t.y * kFwdRows + 2 * lane;          // rows r, r + 1 (r even, ld % 4 == 0)
+  const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r) + int64_t(wid) * (S.ld / 2);
+  const int64_t step = int64_t(4) * S.ld;            // 8 columns, in float4 units
+  const int j0 = min(r, k), j1 = (r < m) ? min(r + 1, k) : 0;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 pv[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) pv[q] = (wid + 8 * q < j1) ? P4[q * step] : zero4;
   const int64_t* cp = cptr + S.rowoff;
-  for (int j = tid; j < k; j += blockDim.x) {
-    float2 acc = tin[S.first + j];
-    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
-    b1[j] = acc;
+  for (int jj = tid; jj < k; jj += blockDim.x) {
+    float2 acc = tin[S.first + jj];
+    for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+    b1[jj] = acc;
   }
   __syncthreads();
-  const int r = t.y * kFwdRows + 2 * lane;          // rows r, r + 1 (r even, ld % 4 == 0)
-  const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
-  const int64_t ld4 = S.ld / 2;
   float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-  if (r < m) {
-    const int j0 = min(r, k), j1 = min(r + 1, k);
-#pragma unroll 4
-    for (int j = wid; j < j1; j += 8) {
-      const float4 p = P4[int64_t(j) * ld4];
-      const float2 bj = b1[j];
-      a1 = cmad(make_float2(p.z, p.w), bj, a1);
-      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+  for (int q0 = 0; wid + 8 * q0 < j1; q0 += 4) {
+    float4 nx[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int jn = wid + 8 * (q0 + 4 + q);
+      nx[q] = (jn < j1) ? P4[(q0 + 4 + q) * step] : zero4;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int j = wid + 8 * (q0 + q);
+      if (j < j1) {
+        const float2 bj = b1[j];
+        a1 = cmad(make_float2(pv[q].z, pv[q].w), bj, a1);
+        if (j < j0) a0 = cmad(make_float2(pv[q].x, pv[q].y), bj, a0);
+      }
+      pv[q] = nx[q];
     }
   }
   part[wid][2 * lane] = a0;
