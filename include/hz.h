@@ -181,6 +181,15 @@ hz_status hz_apply_M(hz_ctx* ctx, const void* v_dev, void* z_dev);
    front_bytes on top).  Lets a caller admit work against an HBM budget. */
 hz_status hz_plan(const hz_mesh_desc* mesh, const hz_options* opt, hz_stats* out);
 
+/* One CGS2 orthogonalisation step of the Arnoldi process (two classical
+   Gram-Schmidt passes, the orthogonalisation the GMRES iteration uses):
+     h1 = V^H w,  w <- w - V h1,  h2 = V^H w,  w <- w - V h2,  h = h1 + h2.
+   V: device complex128, n x ncols column-major with leading dimension ldv >= n
+   (n = hz_ndofs(ctx)); w: device complex128 length n, overwritten in place;
+   h: device complex128, ncols entries; *wnorm (host) = ||w|| after the step.
+   1 <= ncols <= 64.  Uses the context's stream and workspace; synchronous. */
+hz_status hz_cgs2(hz_ctx* ctx, const void* V, int64_t ldv, int32_t ncols, void* w, void* h, double* wnorm);
+
 /* Time each phase of one inner iteration (reps runs each, after one warm-up run)
    with CUDA events on the context's stream, on the current factors; fills
    algorithmic bytes and flops per run.  Overwrites the Krylov workspace.

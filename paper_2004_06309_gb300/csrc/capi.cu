@@ -1015,3 +1015,26 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   out->flops[HZ_PH_ITERATION] = pf + out->flops[HZ_PH_SPMV] + out->flops[HZ_PH_CGS2];
   return HZ_OK;
 }
+
+extern "C" hz_status hz_cgs2(hz_ctx* c, const void* V, int64_t ldv, int32_t ncols, void* w, void* h, double* wnorm) {
+  TRY(check_ctx(c));
+  if (!V || !w || !h || !wnorm) return fail(c, HZ_ERR_ARG, "null pointer");
+  if (ncols < 1 || ncols > 64) return fail(c, HZ_ERR_ARG, "ncols must be in [1, 64]");
+  if (ldv < c->n) return fail(c, HZ_ERR_ARG, "ldv < n");
+  const int64_t n = c->n;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  const double2* Vd = (const double2*)V;
+  double2* wd = (double2*)w;
+  hz::launch_cgs(n, ncols, Vd, ldv, nullptr, wd, ncols, c->partial, st);
+  hz::launch_reduce(c->partial, nb, ncols, c->h1, st);
+  hz::launch_cgs(n, ncols, Vd, ldv, c->h1, wd, ncols, c->partial, st);
+  hz::launch_reduce(c->partial, nb, ncols, c->h2, st);
+  hz::launch_cgs(n, ncols, Vd, ldv, c->h2, wd, 0, c->partial, st);
+  hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+  hz::launch_add2(ncols, c->h1, c->h2, (double2*)h, st);
+  CU(cudaMemcpyAsync(c->h_pin + 5, &c->nrm[64].x, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *wnorm = std::sqrt(c->h_pin[5]);
+  return HZ_OK;
+}

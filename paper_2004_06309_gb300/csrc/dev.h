@@ -108,6 +108,7 @@ void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, 
 void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st);
 void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y,
                      const double2* Zs, int64_t ldz, double2* x, cudaStream_t st);
+void launch_add2(int n, const double2* a, const double2* b, double2* out, cudaStream_t st);
 void launch_axpby_copy(int64_t n, const double2* a, double2* out, cudaStream_t st);
 
 }  // namespace hz

@@ -960,6 +960,15 @@ void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2*
   k_gemv_add<<<grid_for(n, 256), 256, 0, st>>>(n, k, y, Zs, ldz, x);
 }
 
+__global__ void k_add2(int n, const double2* a, const double2* b, double2* out) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = cadd(a[i], b[i]);
+}
+
+void launch_add2(int n, const double2* a, const double2* b, double2* out, cudaStream_t st) {
+  HZ_COUNT();
+  k_add2<<<1, 64, 0, st>>>(n, a, b, out);
+}
+
 __global__ void k_copy(int64_t n, const double2* a, double2* out) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     out[i] = a[i];

@@ -87,6 +87,8 @@ SIGNATURES = {
     "hz_plan": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(Options), C.POINTER(Stats)]),
     "hz_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "hz_profile": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Profile)]),
+    "hz_cgs2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                          C.POINTER(C.c_double)]),
     "hz_ndofs": (C.c_int64, [C.c_void_p]),
     "hz_status_string": (C.c_char_p, [C.c_int]),
     "hz_last_error": (C.c_char_p, [C.c_void_p]),
@@ -278,6 +280,17 @@ class Solver:
         if one:
             X = X[:, 0]
         return X, inf
+
+    def cgs2(self, V, w):
+        """One CGS2 step: w (CUDA, length n) is orthogonalised in place against the columns of
+        V (CUDA, n x ncols); returns (h, ||w||)."""
+        Vt = V.T.contiguous() if V.dim() == 2 else V          # column-major storage
+        ncols = Vt.shape[0]
+        h = self.torch.empty(ncols, dtype=self.torch.complex128, device=w.device)
+        nrm = C.c_double()
+        self._check(lib().hz_cgs2(self.h, C.c_void_p(Vt.data_ptr()), self.n, ncols, C.c_void_p(w.data_ptr()),
+                                  C.c_void_p(h.data_ptr()), C.byref(nrm)), "hz_cgs2")
+        return h, nrm.value
 
     def apply_A(self, x):
         y = self.torch.empty_like(x)

@@ -93,6 +93,26 @@ def test_device_path_and_multiple_rhs(pair):
         assert np.linalg.norm(B[:, j] - S.A @ X[:, j]) / np.linalg.norm(B[:, j]) <= p.tol
 
 
+def test_cgs2_matches_two_gram_schmidt_passes(pair):
+    """hz_cgs2 against the oracle's CGS2 formulas (krylov.fgmres: two classical passes)."""
+    import torch
+    p, S, G = pair
+    rng = np.random.default_rng(5)
+    for ncols in (1, 7, 33):
+        V = rng.standard_normal((S.n, ncols)) + 1j * rng.standard_normal((S.n, ncols))
+        V, _ = np.linalg.qr(V)
+        w = rng.standard_normal(S.n) + 1j * rng.standard_normal(S.n)
+        h1 = V.conj().T @ w
+        w1 = w - V @ h1
+        h2 = V.conj().T @ w1
+        w2 = w1 - V @ h2
+        wd = torch.from_numpy(w).cuda()
+        h, nrm = G.cgs2(torch.from_numpy(V).cuda(), wd)
+        assert np.allclose(h.cpu().numpy(), h1 + h2, rtol=0, atol=1e-12 * np.abs(h1).max())
+        assert np.allclose(wd.cpu().numpy(), w2, rtol=0, atol=1e-12 * np.abs(w).max())
+        assert abs(nrm - np.linalg.norm(w2)) <= 1e-12 * np.linalg.norm(w2)
+
+
 def test_point_sources_match_oracle(pair):
     p, S, G = pair
     pts = np.array([[0.31, 0.47, 0.52]]) * p.mesh.xyz.max(axis=0)
