@@ -190,6 +190,27 @@ hz_status hz_plan(const hz_mesh_desc* mesh, const hz_options* opt, hz_stats* out
    1 <= ncols <= 64.  Uses the context's stream and workspace; synchronous. */
 hz_status hz_cgs2(hz_ctx* ctx, const void* V, int64_t ldv, int32_t ncols, void* w, void* h, double* wnorm);
 
+/* hz_cgs2 without any device allocation, for callers that cannot allocate: code
+   that runs where cudaMalloc is not allowed (a runtime whose memory pool owns the
+   whole device, a latency-bound loop that must not stall on an allocation) or that
+   has no hz context.  The paper has no counterpart; this is a deployment variant
+   of the CGS2 step above.
+   V: device complex128, n x ncols column-major, leading dimension ldv >= n;
+   w: device complex128 length n, orthogonalised in place; h: device complex128,
+   ncols entries (h1 + h2); *wnorm: device double, ||w|| after the step.
+   Asynchronous on `stream` (a cudaStream_t; 0 = legacy default stream).
+   The per-block partial sums live in one file-scope device array (635,440 bytes,
+   sized for at most 64 columns), which every GPU that loads the library keeps
+   until the process exits.  ncols outside [1, 64] returns HZ_ERR_ARG with a
+   message on stderr.  The first call on a device looks the array's device address
+   up (cudaGetSymbolAddress, once per device, with that device current); make that
+   first call before any stream capture.  All calls share the array and it keeps
+   the last call's contents: calls that overlap on the GPU (different streams, or
+   different host threads on one device) race on it and must be serialised by the
+   caller. */
+hz_status hz_cgs2_noalloc(const void* V, int64_t n, int64_t ldv, int32_t ncols, void* w, void* h,
+                          void* wnorm, uintptr_t stream);
+
 /* Time each phase of one inner iteration (reps runs each, after one warm-up run)
    with CUDA events on the context's stream, on the current factors; fills
    algorithmic bytes and flops per run.  Overwrites the Krylov workspace.

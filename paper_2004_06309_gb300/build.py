@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "symbolic.cpp", "kernels.cu", "capi.cu"]
+SOURCES = ["setup.cpp", "symbolic.cpp", "kernels.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["host.h", "dev.h"]
 
 

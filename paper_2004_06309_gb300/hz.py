@@ -89,6 +89,8 @@ SIGNATURES = {
     "hz_profile": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Profile)]),
     "hz_cgs2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
                           C.POINTER(C.c_double)]),
+    "hz_cgs2_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "hz_ndofs": (C.c_int64, [C.c_void_p]),
     "hz_status_string": (C.c_char_p, [C.c_int]),
     "hz_last_error": (C.c_char_p, [C.c_void_p]),
