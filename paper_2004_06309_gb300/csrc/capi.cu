@@ -776,7 +776,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     SETUP_TRY(upload(c, &c->d_Ztrp, P.Zt.ptr));
     SETUP_TRY(upload(c, &c->d_Ztci, P.Zt.col));
     SETUP_TRY(upload(c, &c->d_Ztv, P.Ztv));
-    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 128));
+    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256));
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));
   }

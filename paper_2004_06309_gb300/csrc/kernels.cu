@@ -429,13 +429,17 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
   const int rr = tid & (kFwdRows - 1), cg = tid / kFwdRows;
   const int r = t.y * kFwdRows + rr;
   const V* P = panels + S.paneloff;
-  V acc = czero<V>();
+  V acc = czero<V>(), acc2 = czero<V>();
   if (r < m) {
     const int jmax = min(r, k);
-#pragma unroll 4
-    for (int j = cg; j < jmax; j += 4) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+    int j = cg;
+    for (; j + 4 < jmax; j += 8) {
+      acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+      acc2 = cmad(P[r + int64_t(j + 4) * S.ld], b1[j + 4], acc2);
+    }
+    if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
   }
-  part[cg][rr] = acc;
+  part[cg][rr] = cadd(acc, acc2);
   __syncthreads();
   if (cg == 0 && r < m) {
     const V tot = cadd(cadd(part[0][rr], part[1][rr]), cadd(part[2][rr], part[3][rr]));
@@ -479,6 +483,45 @@ __global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const Sn
     }
     acc = warp_sum(acc);
     if (lane == 0) out[c] = acc;
+  }
+}
+
+// complex128 backward partial sums, transposed mapping for FP64 throughput: thread
+// (c, s) sums column j = 32 * block + c over slice s (of 8) of the chunk's rows,
+// reading its column sequentially (L1 reuse of each 128-byte line); the 8 slice
+// sums are then added in a fixed order.  No shuffle reductions on the FP64 pipe.
+__global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, const SnDev* sn,
+                                                          const int32_t* rowlist, const double2* panels,
+                                                          const double2* zin, const double2* x,
+                                                          double2* partial, int rows) {
+  __shared__ double2 vec[kBwdRows];
+  __shared__ double2 red[8][33];
+  const int4 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, tid = threadIdx.x, c = tid & 31, s = tid >> 5;
+  const int r0 = t.z * rows, r1 = min(m, r0 + rows);
+  const int32_t* rl = rowlist + S.rowoff;
+  for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
+  __syncthreads();
+  const int j = t.y * 32 + c;
+  const int slice = (rows + 7) / 8;
+  const int ra = max(r0 + s * slice, j + 1), rb = min(r1, r0 + (s + 1) * slice);
+  double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+  if (j < k) {
+    const double2* col = panels + S.paneloff + int64_t(j) * S.ld;
+    int r = ra;
+    for (; r + 1 < rb; r += 2) {
+      a0 = cmad(col[r], vec[r - r0], a0);
+      a1 = cmad(col[r + 1], vec[r + 1 - r0], a1);
+    }
+    if (r < rb) a0 = cmad(col[r], vec[r - r0], a0);
+  }
+  red[s][c] = cadd(a0, a1);
+  __syncthreads();
+  if (s == 0) {
+    double2 tot = red[0][c];
+    for (int q = 1; q < 8; q++) tot = cadd(tot, red[q][c]);
+    partial[int64_t(blockIdx.x) * 32 + c] = tot;
   }
 }
 
@@ -641,8 +684,8 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
         k_bwd_partial_c64<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
                                                            F.bwd_rows);
       else
-        k_bwd_partial<V><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                           F.bwd_rows);
+        k_bwd_partial_c128<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                            F.bwd_rows);
     }
     const int64_t fb = F.h_bfin_ptr[l], fe = F.h_bfin_ptr[l + 1];
     if (fe > fb) {
