@@ -220,7 +220,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   // task lists
   const int nlev = S.nlev;
   std::vector<int2> fwd, wg, ea;
-  std::vector<int32_t> small;
   std::vector<int4> bwd, bfin;
   int64_t max_bwd_level = 0;
   std::vector<int4> cbt;
@@ -231,13 +230,11 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   int max_slot = 1;
   for (int s = 0; s < ns; s++) max_slot = std::max(max_slot, int(children[s].size()));
   F.max_slot = max_slot;
-  std::vector<int64_t> small_ptr(nlev + 1);
   std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
       cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1);
   int64_t scratch = 0;
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
-    small_ptr[l] = int64_t(small.size());
     fwd_ptr[l] = int64_t(fwd.size());
     bwd_ptr[l] = int64_t(bwd.size());
     bfin_ptr[l] = int64_t(bfin.size());
@@ -247,15 +244,11 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
-      if (m <= 256) {
-        small.push_back(s);        // both sweeps of this supernode run warp-per-supernode
-      } else {
-        for (int rb = 0; rb * 64 < m; rb++) fwd.push_back(make_int2(s, rb));
-        const int nch = (m + bwd_rows - 1) / bwd_rows;
-        for (int cb = 0; cb * 32 < k; cb++) {
-          bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
-          for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, 0));
-        }
+      for (int rb = 0; rb * 64 < m; rb++) fwd.push_back(make_int2(s, rb));
+      const int nch = (m + bwd_rows - 1) / bwd_rows;
+      for (int cb = 0; cb * 32 < k; cb++) {
+        bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
+        for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, 0));
       }
       for (int rb = 0; rb * 32 < r; rb++) wg.push_back(make_int2(s, rb));
       const int T = (r + 31) / 32;
@@ -279,7 +272,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     }
   }
   lev_ptr[nlev] = S.lev_ptr[nlev];
-  small_ptr[nlev] = int64_t(small.size());
   fwd_ptr[nlev] = int64_t(fwd.size());
   bwd_ptr[nlev] = int64_t(bwd.size());
   bfin_ptr[nlev] = int64_t(bfin.size());
@@ -290,7 +282,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   TRY(upload(c, &F.fwd_tasks, fwd));
   TRY(upload(c, &F.bwd_tasks, bwd));
   TRY(upload(c, &F.bfin_tasks, bfin));
-  TRY(upload(c, &F.small_sn, small));
   TRY(upload(c, &F.wg_tasks, wg));
   TRY(upload(c, &F.cb_tasks, cbt));
   TRY(upload(c, &F.ea_tasks, ea));
@@ -305,7 +296,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_fwd_ptr = hcopy(fwd_ptr);
   F.h_bwd_ptr = hcopy(bwd_ptr);
   F.h_bfin_ptr = hcopy(bfin_ptr);
-  F.h_small_ptr = hcopy(small_ptr);
   F.h_wg_ptr = hcopy(wg_ptr);
   F.h_cb_ptr = hcopy(cb_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
@@ -333,12 +323,11 @@ void free_host_ptrs(hz::FactorDev& F) {
   delete[] F.h_fwd_ptr;
   delete[] F.h_bwd_ptr;
   delete[] F.h_bfin_ptr;
-  delete[] F.h_small_ptr;
   delete[] F.h_wg_ptr;
   delete[] F.h_cb_ptr;
   delete[] F.h_ea_ptr;
   delete[] F.h_ent_ptr;
-  F.h_small_ptr = F.h_bfin_ptr = F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;
+  F.h_bfin_ptr = F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;
 }
 
 hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[3], double& min_pivot) {

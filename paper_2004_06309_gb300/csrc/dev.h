@@ -48,8 +48,6 @@ struct FactorDev {
   int4* cb_tasks = nullptr;      // (sn, row tile, col tile, scratch-relative offset unused)
   int64_t* scr_off = nullptr;    // per supernode: offset of its W block in the level scratch
   int32_t* lev_sn = nullptr;
-  int32_t* small_sn = nullptr;        // per level: supernodes with m <= 256 (warp-per-supernode sweeps)
-  int64_t* h_small_ptr = nullptr;     // nlev + 1 (host)
   int64_t* h_lev_ptr = nullptr;       // nlev + 1 (host)
   int64_t* h_fwd_ptr = nullptr;       // nlev + 1
   int64_t* h_bwd_ptr = nullptr;

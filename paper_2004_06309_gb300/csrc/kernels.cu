@@ -627,79 +627,6 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
   }
 }
 
-// Small supernodes (m <= 256): one warp per supernode, eight per CTA.
-// Forward: lanes own rows; the warp gathers b1 itself, so no CTA barrier is needed.
-constexpr int kSmallM = 256;
-template <typename V>
-__global__ void __launch_bounds__(256) k_fwd_small(const int32_t* list, int count, const SnDev* sn,
-                                                   const int64_t* cptr, const int64_t* cidx, const V* panels,
-                                                   const V* tin, V* zout, V* u) {
-  __shared__ V b1s[8][kMaxK];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int idx = blockIdx.x * 8 + wid;
-  if (idx >= count) return;
-  const SnDev S = sn[list[idx]];
-  const int k = S.k, m = S.m;
-  V* b1 = b1s[wid];
-  const int64_t* cp = cptr + S.rowoff;
-  for (int j = lane; j < k; j += 32) {
-    V acc = tin[S.first + j];
-    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
-    b1[j] = acc;
-  }
-  __syncwarp();
-  const V* P = panels + S.paneloff;
-  for (int rb = 0; rb < m; rb += 32) {
-    const int r = rb + lane;
-    if (r >= m) break;
-    const int jmax = min(r, k);
-    V a0 = czero<V>(), a1 = czero<V>();
-    int j = 0;
-    for (; j + 1 < jmax; j += 2) {
-      a0 = cmad(P[r + int64_t(j) * S.ld], b1[j], a0);
-      a1 = cmad(P[r + int64_t(j + 1) * S.ld], b1[j + 1], a1);
-    }
-    if (j < jmax) a0 = cmad(P[r + int64_t(j) * S.ld], b1[j], a0);
-    const V tot = cadd(a0, a1);
-    if (r < k) {
-      zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
-    } else {
-      V b2 = czero<V>();
-      for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
-      u[S.uoff + (r - k)] = csub(b2, tot);
-    }
-  }
-}
-
-// Backward for small supernodes: one warp per supernode, lanes own pivot columns and
-// walk them sequentially (each 128-byte line is reused from L1).
-template <typename V>
-__global__ void __launch_bounds__(256) k_bwd_small(const int32_t* list, int count, const SnDev* sn,
-                                                   const int32_t* rowlist, const V* panels, const V* zin, V* x) {
-  __shared__ V vecs[8][kSmallM];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int idx = blockIdx.x * 8 + wid;
-  if (idx >= count) return;
-  const SnDev S = sn[list[idx]];
-  const int k = S.k, m = S.m;
-  V* vec = vecs[wid];
-  const int32_t* rl = rowlist + S.rowoff;
-  for (int r = lane; r < m; r += 32) vec[r] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
-  __syncwarp();
-  const V* P = panels + S.paneloff;
-  for (int j = lane; j < k; j += 32) {
-    const V* col = P + int64_t(j) * S.ld;
-    V a0 = czero<V>(), a1 = czero<V>();
-    int r = j + 1;
-    for (; r + 1 < m; r += 2) {
-      a0 = cmad(col[r], vec[r], a0);
-      a1 = cmad(col[r + 1], vec[r + 1], a1);
-    }
-    if (r < m) a0 = cmad(col[r], vec[r], a0);
-    x[S.first + j] = cadd(vec[j], cadd(a0, a1));
-  }
-}
-
 template <typename V>
 __global__ void __launch_bounds__(256) k_bwd_final(const int4* tasks, const SnDev* sn, const V* zin,
                                                    const V* partial, V* x) {
@@ -740,12 +667,6 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
   V* u = (V*)F.u_ws;
   V* part = (V*)F.bwd_partial;
   for (int l = 0; l < F.nlev; l++) {
-    const int64_t sb = F.h_small_ptr[l], se = F.h_small_ptr[l + 1];
-    if (se > sb) {
-      HZ_COUNT();
-      k_fwd_small<V><<<unsigned((se - sb + 7) / 8), 256, 0, st>>>(F.small_sn + sb, int(se - sb), F.sn, F.cptr,
-                                                                   F.cidx, P, t, z, u);
-    }
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
@@ -756,12 +677,6 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     }
   }
   for (int l = F.nlev - 1; l >= 0; l--) {
-    const int64_t sb = F.h_small_ptr[l], se = F.h_small_ptr[l + 1];
-    if (se > sb) {
-      HZ_COUNT();
-      k_bwd_small<V><<<unsigned((se - sb + 7) / 8), 256, 0, st>>>(F.small_sn + sb, int(se - sb), F.sn,
-                                                                   F.rowlist, P, z, x);
-    }
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
