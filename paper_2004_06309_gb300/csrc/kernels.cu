@@ -525,26 +525,19 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
   }
 }
 
-// complex64 forward with 16-byte loads: each lane owns two consecutive rows of a
-// 64-row block, the eight warps split the pivot columns.  Panel loads run in a
-// 4-deep software pipeline whose first batch is issued before the dependent
-// gathers that assemble the right-hand side b1.
+// complex64 forward, 256 rows of one supernode per task: thread t owns the row pair
+// (2p, 2p+1), p = t % 128, for the pivot columns of parity t / 128, with 16-byte
+// loads; the right-hand side b1 is gathered once per 256 rows.
+constexpr int kFwdRowsC64 = 256;
 __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                                  const int64_t* cidx, const float2* panels, const float2* tin,
                                                  float2* zout, float2* u) {
   __shared__ float2 b1[kMaxK];
-  __shared__ float2 part[8][kFwdRows];
+  __shared__ float2 part[2][kFwdRowsC64];
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
-  const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int r = t.y * kFwdRows + 2 * lane;          // rows r, r + 1 (r even, ld % 4 == 0)
-  const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r) + int64_t(wid) * (S.ld / 2);
-  const int64_t step = int64_t(4) * S.ld;            // 8 columns, in float4 units
-  const int j0 = min(r, k), j1 = (r < m) ? min(r + 1, k) : 0;
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 pv[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) pv[q] = (wid + 8 * q < j1) ? P4[q * step] : zero4;
+  const int k = S.k, m = S.m, tid = threadIdx.x;
+  const int pr = tid & 127, cg = tid >> 7;
   const int64_t* cp = cptr + S.rowoff;
   for (int jj = tid; jj < k; jj += blockDim.x) {
     float2 acc = tin[S.first + jj];
@@ -552,41 +545,42 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
     b1[jj] = acc;
   }
   __syncthreads();
-  float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-  for (int q0 = 0; wid + 8 * q0 < j1; q0 += 4) {
-    float4 nx[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int jn = wid + 8 * (q0 + 4 + q);
-      nx[q] = (jn < j1) ? P4[(q0 + 4 + q) * step] : zero4;
+  const int r = t.y * kFwdRowsC64 + 2 * pr;          // rows r, r + 1 (r even, ld % 4 == 0)
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
+  if (r < m) {
+    const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
+    const int64_t ld4 = S.ld / 2;
+    const int j0 = min(r, k), j1 = min(r + 1, k);
+    int j = cg;
+    for (; j + 2 < j1; j += 4) {                       // two independent chains
+      const float4 p = P4[int64_t(j) * ld4];
+      const float4 q = P4[int64_t(j + 2) * ld4];
+      const float2 bj = b1[j], bq = b1[j + 2];
+      a1 = cmad(make_float2(p.z, p.w), bj, a1);
+      c1 = cmad(make_float2(q.z, q.w), bq, c1);
+      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+      if (j + 2 < j0) c0 = cmad(make_float2(q.x, q.y), bq, c0);
     }
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int j = wid + 8 * (q0 + q);
-      if (j < j1) {
-        const float2 bj = b1[j];
-        a1 = cmad(make_float2(pv[q].z, pv[q].w), bj, a1);
-        if (j < j0) a0 = cmad(make_float2(pv[q].x, pv[q].y), bj, a0);
-      }
-      pv[q] = nx[q];
+    if (j < j1) {
+      const float4 p = P4[int64_t(j) * ld4];
+      const float2 bj = b1[j];
+      a1 = cmad(make_float2(p.z, p.w), bj, a1);
+      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
     }
   }
-  part[wid][2 * lane] = a0;
-  part[wid][2 * lane + 1] = a1;
+  part[cg][2 * pr] = cadd(a0, c0);
+  part[cg][2 * pr + 1] = cadd(a1, c1);
   __syncthreads();
-  if (tid < kFwdRows) {
-    const int rr = t.y * kFwdRows + tid;
-    if (rr < m) {
-      float2 tot = part[0][tid];
-      for (int q = 1; q < 8; q++) tot = cadd(tot, part[q][tid]);
-      const float2* P = panels + S.paneloff;
-      if (rr < k) {
-        zout[S.first + rr] = cmul(P[rr + int64_t(rr) * S.ld], cadd(b1[rr], tot));
-      } else {
-        float2 b2 = make_float2(0.f, 0.f);
-        for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
-        u[S.uoff + (rr - k)] = csub(b2, tot);
-      }
+  const int rr = t.y * kFwdRowsC64 + tid;
+  if (rr < m) {
+    const float2 tot = cadd(part[0][tid], part[1][tid]);
+    const float2* P = panels + S.paneloff;
+    if (rr < k) {
+      zout[S.first + rr] = cmul(P[rr + int64_t(rr) * S.ld], cadd(b1[rr], tot));
+    } else {
+      float2 b2 = make_float2(0.f, 0.f);
+      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+      u[S.uoff + (rr - k)] = csub(b2, tot);
     }
   }
 }
