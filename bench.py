@@ -145,6 +145,8 @@ def main():
     ap.add_argument("--workload", default="overthrust-5hz", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf", type=int, default=0, help="nested-dissection leaf size (0: library default)")
+    ap.add_argument("--maxsn", type=int, default=0, help="widest supernode (0: library default)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -216,7 +218,8 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     for pname in precs:
-        G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream)
+        G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream,
+                      leaf_size=args.leaf, max_snode=args.maxsn)
         tf = time.time()
         G.factor()
         torch.cuda.synchronize()
