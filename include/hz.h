@@ -84,7 +84,7 @@ typedef struct {
   int32_t precision;        /* HZ_FP64, or HZ_MIXED: subdomain factors/solves c64    */
   int32_t max_iter;         /* total inner-iteration limit per right-hand side       */
   int32_t leaf_size;        /* nested-dissection leaf size (0: default 64)           */
-  int32_t max_snode;        /* widest supernode (0: default 96; capped at 112 for
+  int32_t max_snode;        /* widest supernode (0: default 128; capped at 112 for
                                HZ_FP64 and 128 for HZ_MIXED)                      */
   uint64_t hbm_budget;      /* bytes; 0 = unlimited                                  */
   const int32_t* elem_part; /* ne part ids in [0, nsub) (host); NULL = built-in RCB  */

@@ -634,7 +634,7 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
   phase("subdomains + local A_i", tp);
   const int prec_k = op->precision == HZ_FP64 ? 112 : 128;
   int leaf = op->leaf_size > 0 ? op->leaf_size : 64;
-  int maxsn = op->max_snode > 0 ? op->max_snode : 96;
+  int maxsn = op->max_snode > 0 ? op->max_snode : 128;
   maxsn = std::min(maxsn, prec_k);
   leaf = std::max(leaf, 1);
   {
