@@ -283,6 +283,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   TRY(upload(c, &F.fwd_tasks, fwd));
   TRY(upload(c, &F.bwd_tasks, bwd));
   TRY(upload(c, &F.bfin_tasks, bfin));
+  TRY(upload(c, &F.bwd_counters, std::vector<unsigned int>(std::max<size_t>(bfin.size(), 1), 0u)));
   TRY(upload(c, &F.wg_tasks, wg));
   TRY(upload(c, &F.cb_tasks, cbt));
   TRY(upload(c, &F.ea_tasks, ea));

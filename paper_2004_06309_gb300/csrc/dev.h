@@ -40,8 +40,9 @@ struct FactorDev {
   double2* eb = nullptr;
   // task arrays (device) and per-level host offsets
   int2* fwd_tasks = nullptr;     // (sn, row block)
-  int4* bwd_tasks = nullptr;     // (sn, col block, row chunk, -): partial sums
-  int4* bfin_tasks = nullptr;    // (sn, col block, first partial task of the level, chunks)
+  int4* bwd_tasks = nullptr;     // (sn, col block, row chunk, global bfin index): partial sums
+  int4* bfin_tasks = nullptr;    // (sn, col block, first partial task of its level, chunks), all levels
+  unsigned int* bwd_counters = nullptr;  // one per bfin task: partial-sum CTAs done (reset by the last)
   void* bwd_partial = nullptr;   // 32 values per backward partial task (max over levels)
   int2* ea_tasks = nullptr;      // (child sn, col block)
   int2* wg_tasks = nullptr;      // (sn, row block of the off-diagonal part)

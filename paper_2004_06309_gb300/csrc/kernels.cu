@@ -458,31 +458,41 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
 //   vec = (z, -x[ancestor rows]) for 32 pivot columns j of one supernode;
 // then x[j] = z[j] + sum of the partials in chunk order (deterministic).
 constexpr int kBwdRows = 512;
+// Fused second stage of the backward sweep ("last block done"): every partial-sum
+// CTA of a (supernode, column block) publishes its 32 sums, fences, and bumps the
+// pair's counter; the CTA that brings it to `chunks` adds the partials in chunk
+// order (deterministic), writes x, and resets the counter for the next sweep.
+// No CTA ever waits on another.
 template <typename V>
-__global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const SnDev* sn, const int32_t* rowlist,
-                                                     const V* panels, const V* zin, const V* x, V* partial,
-                                                     int rows) {
-  __shared__ V vec[kBwdRows];
-  const int4 t = tasks[blockIdx.x];            // (sn, column block, row chunk, -)
-  const SnDev S = sn[t.x];
-  const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int r0 = t.z * rows, r1 = min(m, r0 + rows);
-  const int32_t* rl = rowlist + S.rowoff;
-  for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
+__device__ __forceinline__ void bwd_finish(const int4 fin, const SnDev& S, const V* zin, const V* partial_level,
+                                           V* x, unsigned int* counter) {
+  __shared__ unsigned int ticket;
+  __threadfence();
   __syncthreads();
-  const V* P = panels + S.paneloff;
-  V* out = partial + int64_t(blockIdx.x) * 32;
-  for (int q = 0; q < 4; q++) {
-    const int c = wid + 8 * q;
-    const int j = t.y * 32 + c;
-    V acc = czero<V>();
-    if (j < k) {
-      const V* col = P + int64_t(j) * S.ld;
-#pragma unroll 4
-      for (int r = max(r0, j + 1) + lane; r < r1; r += 32) acc = cmad(col[r], vec[r - r0], acc);
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != unsigned(fin.w) - 1) return;
+  __threadfence();
+  const int c = threadIdx.x;
+  if (c < 32) {
+    const int j = fin.y * 32 + c;
+    if (j < S.k) {
+      V acc = czero<V>();
+      for (int ch = 0; ch < fin.w; ch++) {
+        const V* pp = partial_level + int64_t(fin.z + ch) * 32 + c;
+        V v;
+        if constexpr (sizeof(V) == 8) {
+          const float2 t = __ldcg(reinterpret_cast<const float2*>(pp));
+          v.x = t.x; v.y = t.y;
+        } else {
+          const double2 t = __ldcg(reinterpret_cast<const double2*>(pp));
+          v.x = t.x; v.y = t.y;
+        }
+        acc = cadd(acc, v);
+      }
+      x[S.first + j] = cadd(zin[S.first + j], acc);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) out[c] = acc;
+    if (c == 0) *counter = 0u;
   }
 }
 
@@ -492,8 +502,8 @@ __global__ void __launch_bounds__(256) k_bwd_partial(const int4* tasks, const Sn
 // sums are then added in a fixed order.  No shuffle reductions on the FP64 pipe.
 __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, const SnDev* sn,
                                                           const int32_t* rowlist, const double2* panels,
-                                                          const double2* zin, const double2* x,
-                                                          double2* partial, int rows) {
+                                                          const double2* zin, double2* x, double2* partial,
+                                                          int rows, const int4* fins, unsigned int* counters) {
   __shared__ double2 vec[kBwdRows];
   __shared__ double2 red[8][33];
   const int4 t = tasks[blockIdx.x];
@@ -523,6 +533,7 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
     for (int q = 1; q < 8; q++) tot = cadd(tot, red[q][c]);
     partial[int64_t(blockIdx.x) * 32 + c] = tot;
   }
+  bwd_finish<double2>(fins[t.w], S, zin, partial, x, counters + t.w);
 }
 
 // complex64 forward, 256 rows of one supernode per task: thread t owns the row pair
@@ -588,8 +599,8 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
 // complex64 backward partial sums with 16-byte loads (two rows per lane).
 __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, const SnDev* sn,
                                                          const int32_t* rowlist, const float2* panels,
-                                                         const float2* zin, const float2* x, float2* partial,
-                                                         int rows) {
+                                                         const float2* zin, float2* x, float2* partial,
+                                                         int rows, const int4* fins, unsigned int* counters) {
   __shared__ __align__(16) float2 vec[kBwdRows + 2];
   const int4 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
@@ -619,23 +630,7 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
     acc = warp_sum(acc);
     if (lane == 0) out[c] = acc;
   }
-}
-
-template <typename V>
-__global__ void __launch_bounds__(256) k_bwd_final(const int4* tasks, const SnDev* sn, const V* zin,
-                                                   const V* partial, V* x) {
-  const int4 t = tasks[blockIdx.x];            // (sn, column block, first partial task, chunks)
-  const SnDev S = sn[t.x];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = 0; q < 4; q++) {
-    const int c = wid + 8 * q;
-    const int j = t.y * 32 + c;
-    if (j >= S.k) break;
-    V acc = czero<V>();
-    for (int ch = lane; ch < t.w; ch += 32) acc = cadd(acc, partial[int64_t(t.z + ch) * 32 + c]);
-    acc = warp_sum(acc);
-    if (lane == 0) x[S.first + j] = cadd(zin[S.first + j], acc);
-  }
+  bwd_finish<float2>(fins[t.w], S, zin, partial, x, counters + t.w);
 }
 
 template <typename V>
@@ -676,15 +671,10 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       HZ_COUNT();
       if constexpr (sizeof(V) == 8)
         k_bwd_partial_c64<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                           F.bwd_rows);
+                                                           F.bwd_rows, F.bfin_tasks, F.bwd_counters);
       else
         k_bwd_partial_c128<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                            F.bwd_rows);
-    }
-    const int64_t fb = F.h_bfin_ptr[l], fe = F.h_bfin_ptr[l + 1];
-    if (fe > fb) {
-      HZ_COUNT();
-      k_bwd_final<V><<<unsigned(fe - fb), 256, 0, st>>>(F.bfin_tasks + fb, F.sn, z, part, x);
+                                                            F.bwd_rows, F.bfin_tasks, F.bwd_counters);
     }
   }
 }
