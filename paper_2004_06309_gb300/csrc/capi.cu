@@ -248,8 +248,9 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
       for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
       const int nch = (m + bwd_rows - 1) / bwd_rows;
       for (int cb = 0; cb * 32 < k; cb++) {
+        const int fin = int(bfin.size());          // global index: its counter and its record
         bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
-        for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, 0));
+        for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, fin));
       }
       for (int rb = 0; rb * 32 < r; rb++) wg.push_back(make_int2(s, rb));
       const int T = (r + 31) / 32;
