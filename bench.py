@@ -130,6 +130,19 @@ def oracle_subprocess(steps, warmup):
     raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
 
 
+def max_over_ranks(x, dist, device):
+    """Slowest rank's time: the whole-job figure of a replicas-only run."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, max_seconds):
+    """Whole-job throughput: units all ranks processed / slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
 def scaled_rhs_per_s(sample, n_full, it_full):
     """Oracle throughput on the sample, scaled to the full workload by dofs x iterations."""
     work_ratio = (sample["n"] * sample["iterations"]) / float(n_full * max(it_full, 1))
@@ -145,6 +158,10 @@ def main():
     ap.add_argument("--workload", default="overthrust-5hz", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block", type=int, default=0,
+                    help="pseudo-block FGMRES block size (right-hand sides sharing each operator application)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="right-hand sides per step (sources from the 16 x 8 surface grid at 50 m depth)")
     ap.add_argument("--leaf", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--maxsn", type=int, default=0, help="widest supernode (0: library default)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -206,11 +223,7 @@ def main():
         torch.cuda.synchronize()
 
     def maxall(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, dist, "cuda") if dist else x
 
     precs = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
     results = {}
@@ -219,12 +232,17 @@ def main():
     torch.cuda.set_stream(stream)
     for pname in precs:
         G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream,
-                      leaf_size=args.leaf, max_snode=args.maxsn)
+                      leaf_size=args.leaf, max_snode=args.maxsn, block_size=args.block)
         tf = time.time()
         G.factor()
         torch.cuda.synchronize()
         t_factor = time.time() - tf
-        b_host = G.point_sources(prob.sources)[:, 0].copy()
+        if args.nrhs > 1:
+            import synth
+            srcs = synth.surface_source_grid()[: args.nrhs]
+            b_host = np.asfortranarray(G.point_sources(srcs))
+        else:
+            b_host = G.point_sources(prob.sources)[:, 0].copy()
         b_dev = torch.from_numpy(b_host).cuda()
         for _ in range(args.warmup):
             x, info = G.solve(b_dev)
@@ -238,7 +256,7 @@ def main():
         for s in range(args.steps):
             x, info = G.solve(b_dev)
             ev[s + 1].record(stream)
-            its.append(info[0][0])
+            its.append(max(i[0] for i in info))
         barrier()
         ck = clocks.stop()
         launches = G.stats()["launches"] - st0
@@ -270,7 +288,7 @@ def main():
     R = results[main_p]
     n = R["n"]
     K = args.steps
-    value = world * K / (R["total_ms"] / 1e3)
+    value = job_throughput(K * args.nrhs, world, R["total_ms"] / 1e3)
 
     def lat(r):
         s = sorted(r["step_ms"])
@@ -305,14 +323,14 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "n_dofs": n, "nsub": prob.nsub, "overlap": prob.overlap,
                    "levels": 2 if prob.levels == 2 else 1, "restart": prob.restart, "tol": 1e-6,
-                   "rhs_per_step": 1, "freq_hz": prob.freq,
+                   "rhs_per_step": args.nrhs, "block_size": args.block, "freq_hz": prob.freq,
                    "l2": "inputs larger than L2 (factors >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "iterations": R["iterations"][-1], "rel_residual": R["rel"],
         "latency_ms": lat(R),
         "factor_seconds": R["t_factor"],
-        "e2e": {"value": world * K / R["e2e_s"], "unit": "RHS/s", "h2d_bytes_per_step": n * 16,
-                "d2h_bytes_per_step": n * 16},
+        "e2e": {"value": world * K * args.nrhs / R["e2e_s"], "unit": "RHS/s",
+                "h2d_bytes_per_step": n * 16 * args.nrhs, "d2h_bytes_per_step": n * 16 * args.nrhs},
         "gpu_launches": R["launches"],
         "clocks": R["clocks"],
         "roofline": roof,
@@ -324,10 +342,10 @@ def main():
     }
     if "fp64" in results and main_p != "fp64":
         F = results["fp64"]
-        line["fp64"] = {"value": world * K / (F["total_ms"] / 1e3), "ms_per_step": F["total_ms"] / K,
+        line["fp64"] = {"value": world * K * args.nrhs / (F["total_ms"] / 1e3), "ms_per_step": F["total_ms"] / K,
                         "iterations": F["iterations"][-1], "rel_residual": F["rel"], "latency_ms": lat(F),
                         "factor_seconds": F["t_factor"],
-                        "e2e_value": world * K / F["e2e_s"],
+                        "e2e_value": world * K * args.nrhs / F["e2e_s"],
                         "phases_ms": {k: round(v["ms"], 4) for k, v in F["profile"].items()},
                         "clocks": F["clocks"]}
     if not args.no_cpu_baseline and world == 1:

@@ -89,6 +89,13 @@ typedef struct {
   uint64_t hbm_budget;      /* bytes; 0 = unlimited                                  */
   const int32_t* elem_part; /* ne part ids in [0, nsub) (host); NULL = built-in RCB  */
   uintptr_t stream;         /* cudaStream_t; 0 = legacy default stream               */
+  int32_t block_size;       /* pseudo-block FGMRES: right-hand sides solved together,
+                               each with its own Krylov space, sharing every operator
+                               and preconditioner application (multi-RHS remark of the
+                               method section; pseudo-block GMRES of the experiments
+                               section).  0/1: one at a time; 2..16 (padded to 4, 8 or
+                               16).  Results per right-hand side are those of a solve
+                               alone up to rounding.                                  */
 } hz_options;
 
 typedef struct {

@@ -54,6 +54,14 @@ struct hz_ctx {
   double* h_pin = nullptr;                 // pinned: est, invh, invbeta, beta, brk, norm
   bool factored = false;
   hz_stats stats{};
+  // pseudo-block state (block_size > 1): S right-hand sides, interleaved operator blocks
+  int S = 0;
+  double2 *Vb = nullptr, *Zb = nullptr, *Wc = nullptr, *Bc = nullptr, *Xc = nullptr;   // per-RHS columns
+  double2 *Xi = nullptr, *Yi = nullptr, *Ti = nullptr, *Wi = nullptr, *yi = nullptr;   // interleaved n x S
+  double2 *rHi = nullptr, *yHi = nullptr;                                              // interleaved nH x S
+  double2 *Hb = nullptr, *snb = nullptr, *gb = nullptr, *yb = nullptr;
+  double *csb = nullptr, *scalb = nullptr;
+  int* brkb = nullptr;
   std::vector<void*> allocs;
   std::vector<size_t> sizes;
   int64_t bytes = 0;
@@ -126,7 +134,7 @@ std::vector<double2> to_d2(const std::vector<cplx>& v) {
 
 // Device copy of a symbolic set with its task lists.
 hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
-                        double maxabs[3], int bwd_rows) {
+                        double maxabs[3], int bwd_rows, int nrhs_block) {
   F = hz::FactorDev();
   F.bwd_rows = bwd_rows;
   F.precision = precision;
@@ -303,6 +311,53 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_cb_ptr = hcopy(cb_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
   F.h_ent_ptr = hcopy(S.ent_ptr);
+  // batched sweeps for nrhs_block right-hand sides (pseudo-block FGMRES)
+  if (nrhs_block > 1) {
+    F.mS = nrhs_block;
+    F.mbwd_rows = 128;
+    std::vector<int2> mf;
+    std::vector<int4> mb, mfin;
+    std::vector<int64_t> mf_ptr(nlev + 1), mb_ptr(nlev + 1);
+    int64_t max_mb = 0;
+    for (int l = 0; l < nlev; l++) {
+      mf_ptr[l] = int64_t(mf.size());
+      mb_ptr[l] = int64_t(mb.size());
+      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+        const int s = S.lev_sn[q];
+        const int k = S.sn_k[s], m = S.sn_m[s];
+        for (int rb = 0; rb * 64 < m; rb++) mf.push_back(make_int2(s, rb));
+        const int nch = (m + F.mbwd_rows - 1) / F.mbwd_rows;
+        for (int cb = 0; cb * 32 < k; cb++) {
+          const int fin = int(mfin.size());
+          mfin.push_back(make_int4(s, cb, int(int64_t(mb.size()) - mb_ptr[l]), nch));
+          for (int ch = 0; ch < nch; ch++) mb.push_back(make_int4(s, cb, ch, fin));
+        }
+      }
+      max_mb = std::max(max_mb, int64_t(mb.size()) - mb_ptr[l]);
+    }
+    mf_ptr[nlev] = int64_t(mf.size());
+    mb_ptr[nlev] = int64_t(mb.size());
+    TRY(upload(c, &F.mfwd_tasks, mf));
+    TRY(upload(c, &F.mbwd_tasks, mb));
+    TRY(upload(c, &F.mbfin_tasks, mfin));
+    TRY(upload(c, &F.mbwd_counters, std::vector<unsigned int>(std::max<size_t>(mfin.size(), 1), 0u)));
+    F.h_mfwd_ptr = new int64_t[nlev + 1];
+    F.h_mbwd_ptr = new int64_t[nlev + 1];
+    std::copy(mf_ptr.begin(), mf_ptr.end(), F.h_mfwd_ptr);
+    std::copy(mb_ptr.begin(), mb_ptr.end(), F.h_mbwd_ptr);
+    const int64_t vsz = int64_t(vs) * nrhs_block;
+    void *a = nullptr, *b = nullptr, *d = nullptr, *e = nullptr, *f = nullptr;
+    TRY(dalloc(c, (char**)&a, F.ntot * vsz));
+    TRY(dalloc(c, (char**)&b, F.ntot * vsz));
+    TRY(dalloc(c, (char**)&d, F.ntot * vsz));
+    TRY(dalloc(c, (char**)&e, std::max<int64_t>(F.u_elems, 1) * vsz));
+    TRY(dalloc(c, (char**)&f, std::max<int64_t>(max_mb, 1) * 32 * vsz));
+    F.mt_loc = a;
+    F.mz_loc = b;
+    F.mx_loc = d;
+    F.mu_ws = e;
+    F.mbwd_partial = f;
+  }
   // numeric storage and solve workspaces
   void *pan = nullptr, *tl = nullptr, *zl = nullptr, *xl = nullptr, *uw = nullptr;
   TRY(dalloc(c, (char**)&pan, F.panel_elems * int64_t(vs)));
@@ -330,6 +385,9 @@ void free_host_ptrs(hz::FactorDev& F) {
   delete[] F.h_cb_ptr;
   delete[] F.h_ea_ptr;
   delete[] F.h_ent_ptr;
+  delete[] F.h_mfwd_ptr;
+  delete[] F.h_mbwd_ptr;
+  F.h_mfwd_ptr = F.h_mbwd_ptr = nullptr;
   F.h_bfin_ptr = F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;
 }
 
@@ -514,6 +572,145 @@ hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
     }
     // nrm still holds |r|^2 from norm2 for the next cycle
   }
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo-block FGMRES: S right-hand sides, one Krylov space each, advanced in
+// lock-step cycles.  Every preconditioner and operator application works on the S
+// vectors at once (interleaved per row), so each factor panel is read once for S
+// right-hand sides; orthogonalisation, Givens updates and stopping decisions stay
+// per right-hand side, exactly as in fgmres_one.
+// ---------------------------------------------------------------------------
+void apply_prec_multi(hz_ctx* c, const double2* X, double2* Y) {
+  const int S = c->S;
+  cudaStream_t st = c->st;
+  if (c->levels == 2) {
+    hz::launch_spmv_real_multi(c->nH, S, c->d_Ztrp, c->d_Ztci, c->d_Ztv, X, c->rHi, st);   // Z^T v
+    hz::launch_local_multi(c->crs, S, c->rHi, nullptr, c->yHi, st);                       // E^{-1}
+    hz::launch_spmv_real_multi(c->n, S, c->d_Zrp, c->d_Zci, c->d_Zv, c->yHi, c->yi, st);  // y = Z y_H
+    hz::launch_spmv_multi(c->n, S, c->d_rp, c->d_ci, c->d_A, c->yi, X, c->Ti, st);         // t = v - A y
+    hz::launch_local_multi(c->loc, S, c->Ti, c->yi, Y, st);                               // y + M_1^{-1} t
+  } else {
+    hz::launch_local_multi(c->loc, S, X, nullptr, Y, st);
+  }
+}
+
+hz_status fgmres_block(hz_ctx* c, int nact, double tol, hz_rhs_info* info) {
+  const int S = c->S, m = c->restart;
+  const int64_t n = c->n;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  std::vector<double> bnorm(S, 0.0);
+  std::vector<int> its(S, 0), kcyc(S, 0);
+  std::vector<char> done(S, 1), act(S, 0);
+  auto V = [&](int i) { return c->Vb + int64_t(i) * n * (m + 1); };
+  auto Zc = [&](int i) { return c->Zb + int64_t(i) * n * m; };
+  auto col = [&](double2* base, int i) { return base + int64_t(i) * n; };
+  auto scal = [&](int i) { return c->scalb + int64_t(i) * 8; };
+  CU(cudaMemsetAsync(c->Xc, 0, size_t(S) * n * 16, st));
+  for (int i = 0; i < nact; i++) {
+    TRY(norm2(c, col(c->Bc, i), bnorm[i]));
+    info[i].iterations = 0;
+    info[i].status = HZ_OK;
+    info[i].rel_residual = 0.0;
+    if (bnorm[i] == 0.0) continue;
+    if (!std::isfinite(bnorm[i])) {
+      info[i].status = HZ_ERR_BREAKDOWN;
+      info[i].rel_residual = NAN;
+      continue;
+    }
+    done[i] = 0;
+    c->h_pin[6] = bnorm[i];
+    CU(cudaMemcpyAsync(scal(i) + 4, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
+    hz::launch_axpby_copy(n, col(c->Bc, i), col(c->Wc, i), st);                // r = b
+    hz::launch_cgs(n, 0, V(i), n, nullptr, col(c->Wc, i), 0, c->partial, st);
+    hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+    hz::launch_init_cycle(c->nrm, c->gb + int64_t(i) * (m + 1), m, scal(i) + 2, scal(i) + 3, st);
+    hz::launch_scale(n, col(c->Wc, i), scal(i) + 2, V(i), st);
+    CU(cudaStreamSynchronize(st));
+  }
+  double* hs = c->h_pin + 8;                      // S x 8 scalars
+  int* hb = reinterpret_cast<int*>(c->h_pin + 8 + 8 * 16);
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < S; i++) {
+      act[i] = !done[i];
+      kcyc[i] = 0;
+      any = any || act[i];
+    }
+    if (!any) break;
+    for (int j = 0; j < m; j++) {
+      bool running = false;
+      for (int i = 0; i < S; i++) running = running || act[i];
+      if (!running) break;
+      hz::launch_interleave(n, S, nact, V(0) + int64_t(j) * n, n * (m + 1), c->Xi, st);
+      apply_prec_multi(c, c->Xi, c->Yi);
+      hz::launch_deinterleave(n, S, nact, c->Yi, Zc(0) + int64_t(j) * n, n * m, st);
+      hz::launch_spmv_multi(n, S, c->d_rp, c->d_ci, c->d_A, c->Yi, nullptr, c->Wi, st);
+      hz::launch_deinterleave(n, S, nact, c->Wi, c->Wc, n, st);
+      for (int i = 0; i < S; i++) {
+        if (!act[i]) continue;
+        double2* w = col(c->Wc, i);
+        hz::launch_cgs(n, j + 1, V(i), n, nullptr, w, j + 1, c->partial, st);
+        hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
+        hz::launch_cgs(n, j + 1, V(i), n, c->h1, w, j + 1, c->partial, st);
+        hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
+        hz::launch_cgs(n, j + 1, V(i), n, c->h2, w, 0, c->partial, st);
+        hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+        hz::launch_givens(j, m, c->Hb + int64_t(i) * (m + 1) * m, c->csb + int64_t(i) * m, c->snb + int64_t(i) * m,
+                          c->gb + int64_t(i) * (m + 1), c->h1, c->h2, c->nrm, scal(i) + 4, scal(i), c->brkb + i,
+                          scal(i) + 1, st);
+        hz::launch_scale(n, w, scal(i) + 1, V(i) + int64_t(j + 1) * n, st);
+      }
+      CU(cudaMemcpyAsync(hs, c->scalb, size_t(S) * 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CU(cudaMemcpyAsync(hb, c->brkb, size_t(S) * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      for (int i = 0; i < S; i++) {
+        if (!act[i]) continue;
+        its[i]++;
+        kcyc[i] = j + 1;
+        const double est = hs[8 * i];
+        if (!std::isfinite(est)) {
+          act[i] = 0;
+          done[i] = 1;
+          info[i].iterations = its[i];
+          info[i].status = HZ_ERR_BREAKDOWN;
+          info[i].rel_residual = NAN;
+          kcyc[i] = 0;
+          continue;
+        }
+        if (hb[i] || est <= tol || its[i] >= c->max_iter) act[i] = 0;
+      }
+    }
+    // end of cycle: x_i += Z_i y_i, true residual, restart the unconverged
+    for (int i = 0; i < S; i++) {
+      if (done[i] || kcyc[i] == 0) continue;
+      double2* xi = col(c->Xc, i);
+      hz::launch_update_x(n, kcyc[i], c->Hb + int64_t(i) * (m + 1) * m, m + 1, c->gb + int64_t(i) * (m + 1),
+                          c->yb + int64_t(i) * m, Zc(i), n, xi, st);
+      hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, xi, col(c->Bc, i), col(c->Wc, i), st);
+      double rn = 0;
+      TRY(norm2(c, col(c->Wc, i), rn));
+      const double rel = rn / bnorm[i];
+      info[i].iterations = its[i];
+      info[i].rel_residual = rel;
+      if (!std::isfinite(rel)) {
+        info[i].status = HZ_ERR_BREAKDOWN;
+        done[i] = 1;
+      } else if (rel <= tol) {
+        done[i] = 1;
+      } else if (its[i] >= c->max_iter) {
+        info[i].status = HZ_ERR_NOT_CONVERGED;
+        done[i] = 1;
+      } else {
+        hz::launch_init_cycle(c->nrm, c->gb + int64_t(i) * (m + 1), m, scal(i) + 2, scal(i) + 3, st);
+        hz::launch_scale(n, col(c->Wc, i), scal(i) + 2, V(i), st);
+      }
+    }
+    CU(cudaGetLastError());
+  }
+  CU(cudaStreamSynchronize(st));
+  return HZ_OK;
 }
 
 hz_status check_ctx(hz_ctx* c) {
@@ -770,8 +967,16 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
   SETUP_TRY(dalloc(c, &c->d_A, c->nnz));
   // backward row chunks: long ones where the sweep streams complex64 panels from HBM,
   // short ones where it is limited by FP64 arithmetic (more CTAs per supernode)
+  {
+    const int bs = op->block_size;
+    c->S = bs <= 1 ? 0 : (bs <= 4 ? 4 : (bs <= 8 ? 8 : 16));
+    if (bs > 16) {
+      c->err = "block_size must be at most 16";
+      return bail(HZ_ERR_ARG);
+    }
+  }
   SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max,
-                          op->precision == HZ_MIXED ? 512 : 256));
+                          op->precision == HZ_MIXED ? 512 : 256, c->S));
   if (c->levels == 2) {
     SETUP_TRY(upload(c, &c->d_Zrp, P.Z.ptr));
     SETUP_TRY(upload(c, &c->d_Zci, P.Z.col));
@@ -779,7 +984,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     SETUP_TRY(upload(c, &c->d_Ztrp, P.Zt.ptr));
     SETUP_TRY(upload(c, &c->d_Ztci, P.Zt.col));
     SETUP_TRY(upload(c, &c->d_Ztv, P.Ztv));
-    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256));
+    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S));
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));
   }
@@ -807,7 +1012,32 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
   c->graphs = std::getenv("HZ_NO_GRAPHS") == nullptr;
   SETUP_TRY(dalloc(c, &c->brk, 1));
   SETUP_TRY(dalloc(c, &c->status, 1));
-  if (cudaMallocHost((void**)&c->h_pin, 8 * sizeof(double)) != cudaSuccess) {
+  if (c->S) {
+    const int S = c->S;
+    SETUP_TRY(dalloc(c, &c->Vb, int64_t(S) * n * (m + 1)));
+    SETUP_TRY(dalloc(c, &c->Zb, int64_t(S) * n * m));
+    SETUP_TRY(dalloc(c, &c->Wc, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->Bc, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->Xc, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->Xi, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->Yi, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->Ti, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->Wi, int64_t(S) * n));
+    SETUP_TRY(dalloc(c, &c->yi, int64_t(S) * n));
+    if (c->levels == 2) {
+      SETUP_TRY(dalloc(c, &c->rHi, int64_t(S) * c->nH));
+      SETUP_TRY(dalloc(c, &c->yHi, int64_t(S) * c->nH));
+    }
+    SETUP_TRY(dalloc(c, &c->Hb, int64_t(S) * (m + 1) * m));
+    SETUP_TRY(dalloc(c, &c->snb, int64_t(S) * m));
+    SETUP_TRY(dalloc(c, &c->gb, int64_t(S) * (m + 1)));
+    SETUP_TRY(dalloc(c, &c->yb, int64_t(S) * m));
+    SETUP_TRY(dalloc(c, &c->csb, int64_t(S) * m));
+    SETUP_TRY(dalloc(c, &c->scalb, int64_t(S) * 8));
+    SETUP_TRY(dalloc(c, &c->brkb, int64_t(S)));
+  }
+  // pinned scalars: 8 for the single-RHS loop, then 16 x 8 per-RHS scalars and 16 flags
+  if (cudaMallocHost((void**)&c->h_pin, (8 + 8 * 16 + 16) * sizeof(double)) != cudaSuccess) {
     c->err = "cudaMallocHost failed";
     return bail(HZ_ERR_CUDA);
   }
@@ -865,6 +1095,24 @@ extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double t
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run before hz_solve");
   const int64_t n = c->n;
   hz_status worst = HZ_OK;
+  if (c->S && nrhs > 1) {
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    std::vector<hz_rhs_info> inf(c->S);
+    for (int32_t j0 = 0; j0 < nrhs; j0 += c->S) {
+      const int nact = std::min<int>(c->S, nrhs - j0);
+      CU(cudaMemsetAsync(c->Bc, 0, size_t(c->S) * n * 16, c->st));
+      CU(cudaMemcpyAsync(c->Bc, (const double2*)rhs + int64_t(j0) * n, size_t(nact) * n * 16, kin, c->st));
+      TRY(fgmres_block(c, nact, tol, inf.data()));
+      CU(cudaMemcpyAsync((double2*)x + int64_t(j0) * n, c->Xc, size_t(nact) * n * 16, kout, c->st));
+      for (int i = 0; i < nact; i++) {
+        if (info) info[j0 + i] = inf[i];
+        if (inf[i].status != HZ_OK && worst == HZ_OK) worst = hz_status(inf[i].status);
+      }
+    }
+    CU(cudaStreamSynchronize(c->st));
+    return worst;
+  }
   for (int32_t j = 0; j < nrhs; j++) {
     const double2* bj = (const double2*)rhs + int64_t(j) * n;
     double2* xj = (double2*)x + int64_t(j) * n;

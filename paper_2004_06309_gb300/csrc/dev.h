@@ -66,6 +66,20 @@ struct FactorDev {
   // numeric
   int precision = 0;                  // 0: complex128, 1: complex64
   void* panels = nullptr;             // factor store
+  // batched (S right-hand sides) sweep tasks and workspaces, built when block_size > 1
+  int32_t mS = 0;
+  int2* mfwd_tasks = nullptr;
+  int4* mbwd_tasks = nullptr;
+  int4* mbfin_tasks = nullptr;
+  unsigned int* mbwd_counters = nullptr;
+  int64_t* h_mfwd_ptr = nullptr;
+  int64_t* h_mbwd_ptr = nullptr;
+  int32_t mbwd_rows = 128;
+  void* mt_loc = nullptr;
+  void* mz_loc = nullptr;
+  void* mx_loc = nullptr;
+  void* mu_ws = nullptr;
+  void* mbwd_partial = nullptr;
   // solve workspaces (typed by precision)
   void* t_loc = nullptr;
   void* z_loc = nullptr;
@@ -94,6 +108,16 @@ void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st);
 void launch_solve(const FactorDev& F, cudaStream_t st);
 void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st);
 
+void launch_local_multi(const FactorDev& F, int S, const double2* src, const double2* y, double2* dst,
+                        cudaStream_t st);
+void launch_interleave(int64_t n, int S, int active, const double2* cols, int64_t stride, double2* inter,
+                       cudaStream_t st);
+void launch_deinterleave(int64_t n, int S, int active, const double2* inter, double2* cols, int64_t stride,
+                         cudaStream_t st);
+void launch_spmv_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
+                       const double2* sub, double2* y, cudaStream_t st);
+void launch_spmv_real_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double* val,
+                            const double2* x, double2* y, cudaStream_t st);
 void launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                  const double2* sub, double2* y, cudaStream_t st);
 void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, const double2* x,

@@ -709,6 +709,294 @@ void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream
 }
 
 // ---------------------------------------------------------------------------
+// batched preconditioner for S right-hand sides (pseudo-block GMRES):
+// vectors are interleaved per row, X[r * S + i].  Each factor panel element is
+// read once and used for all S right-hand sides.
+// ---------------------------------------------------------------------------
+template <typename V, int S>
+__global__ void k_gather_multi(int64_t ntot, const int32_t* gidx, const double2* src, V* dst) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < ntot * S; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t q = e / S;
+    const int i = int(e % S);
+    dst[e] = from2<V>(src[int64_t(gidx[q]) * S + i]);
+  }
+}
+
+template <typename V, int S>
+__global__ void k_prolong_multi(int64_t n, const int64_t* pptr, const int32_t* pidx, const double* pw, const V* xl,
+                                const double2* y, double2* z) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = e / S;
+    const int i = int(e % S);
+    double2 acc = y ? y[e] : make_double2(0.0, 0.0);
+    for (int64_t q = pptr[g]; q < pptr[g + 1]; q++) {
+      const double2 v = to2(xl[int64_t(pidx[q]) * S + i]);
+      acc.x = xfma(pw[q], v.x, acc.x);
+      acc.y = xfma(pw[q], v.y, acc.y);
+    }
+    z[e] = acc;
+  }
+}
+
+// Forward, 64 rows x S right-hand sides per task; 128 threads = 64 rows x 2 column parities.
+template <typename V, int S>
+__global__ void __launch_bounds__(128) k_fwd_multi(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+                                                   const int64_t* cidx, const V* panels, const V* tin, V* zout,
+                                                   V* u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* b1 = reinterpret_cast<V*>(smem_raw);               // kMaxK x S
+  V* part = b1 + kMaxK * S;                               // 2 x 64 x S
+  const int2 t = tasks[blockIdx.x];
+  const SnDev Sn = sn[t.x];
+  const int k = Sn.k, m = Sn.m, tid = threadIdx.x;
+  const int64_t* cp = cptr + Sn.rowoff;
+  for (int e = tid; e < k * S; e += blockDim.x) {
+    const int j = e / S, i = e % S;
+    V acc = tin[int64_t(Sn.first + j) * S + i];
+    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c] * S + i]);
+    b1[e] = acc;
+  }
+  __syncthreads();
+  const int rr = tid & 63, cg = tid >> 6;
+  const int r = t.y * 64 + rr;
+  V acc[S];
+#pragma unroll
+  for (int i = 0; i < S; i++) acc[i] = czero<V>();
+  if (r < m) {
+    const int jmax = min(r, k);
+    const V* P = panels + Sn.paneloff + r;
+    for (int j = cg; j < jmax; j += 2) {
+      const V p = P[int64_t(j) * Sn.ld];
+      const V* bj = b1 + j * S;
+#pragma unroll
+      for (int i = 0; i < S; i++) acc[i] = cmad(p, bj[i], acc[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < S; i++) part[(cg * 64 + rr) * S + i] = acc[i];
+  __syncthreads();
+  for (int e = tid; e < 64 * S; e += blockDim.x) {
+    const int row = e / S, i = e % S;
+    const int rw = t.y * 64 + row;
+    if (rw >= m) continue;
+    const V tot = cadd(part[row * S + i], part[(64 + row) * S + i]);
+    if (rw < k) {
+      zout[int64_t(Sn.first + rw) * S + i] = cmul(panels[Sn.paneloff + rw + int64_t(rw) * Sn.ld], cadd(b1[rw * S + i], tot));
+    } else {
+      V b2 = czero<V>();
+      for (int64_t c = cp[rw]; c < cp[rw + 1]; c++) b2 = cadd(b2, u[cidx[c] * S + i]);
+      u[(Sn.uoff + (rw - k)) * S + i] = csub(b2, tot);
+    }
+  }
+}
+
+// Backward partial sums for S right-hand sides: thread (c, slice) owns pivot column
+// 32 * block + c over a quarter of the chunk's rows; slices are added in a fixed
+// order; the last CTA of a (supernode, column block) finishes x (no waits).
+template <typename V, int S>
+__global__ void __launch_bounds__(128) k_bwd_multi(const int4* tasks, const SnDev* sn, const int32_t* rowlist,
+                                                   const V* panels, const V* zin, V* x, V* partial, int rows,
+                                                   const int4* fins, unsigned int* counters) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* vec = reinterpret_cast<V*>(smem_raw);              // rows x S
+  V* red = vec + rows * S;                                // 4 x 32 x S
+  __shared__ unsigned int ticket;
+  const int4 t = tasks[blockIdx.x];
+  const SnDev Sn = sn[t.x];
+  const int k = Sn.k, m = Sn.m, tid = threadIdx.x, c = tid & 31, sl = tid >> 5;
+  const int r0 = t.z * rows, r1 = min(m, r0 + rows);
+  const int32_t* rl = rowlist + Sn.rowoff;
+  for (int e = tid; e < (r1 - r0) * S; e += blockDim.x) {
+    const int r = r0 + e / S, i = e % S;
+    vec[e] = (r < k) ? zin[int64_t(Sn.first + r) * S + i] : cneg(x[int64_t(rl[r]) * S + i]);
+  }
+  __syncthreads();
+  const int j = t.y * 32 + c;
+  const int slice = (rows + 3) / 4;
+  const int ra = max(r0 + sl * slice, j + 1), rb = min(r1, r0 + (sl + 1) * slice);
+  V acc[S];
+#pragma unroll
+  for (int i = 0; i < S; i++) acc[i] = czero<V>();
+  if (j < k) {
+    const V* col = panels + Sn.paneloff + int64_t(j) * Sn.ld;
+    for (int r = ra; r < rb; r++) {
+      const V p = col[r];
+      const V* vr = vec + (r - r0) * S;
+#pragma unroll
+      for (int i = 0; i < S; i++) acc[i] = cmad(p, vr[i], acc[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < S; i++) red[(sl * 32 + c) * S + i] = acc[i];
+  __syncthreads();
+  V* out = partial + int64_t(blockIdx.x) * 32 * S;
+  for (int e = tid; e < 32 * S; e += blockDim.x) {
+    V tot = red[e];
+    for (int q = 1; q < 4; q++) tot = cadd(tot, red[q * 32 * S + e]);
+    out[e] = tot;
+  }
+  // fused second stage
+  const int4 fin = fins[t.w];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(counters + t.w, 1u);
+  __syncthreads();
+  if (ticket != unsigned(fin.w) - 1) return;
+  __threadfence();
+  for (int e = tid; e < 32 * S; e += blockDim.x) {
+    const int cc = e / S, i = e % S;
+    const int jj = fin.y * 32 + cc;
+    if (jj >= k) continue;
+    V a = czero<V>();
+    for (int ch = 0; ch < fin.w; ch++) {
+      const V* pp = partial + (int64_t(fin.z + ch) * 32 + cc) * S + i;
+      V v;
+      if constexpr (sizeof(V) == 8) {
+        const float2 q2 = __ldcg(reinterpret_cast<const float2*>(pp));
+        v.x = q2.x; v.y = q2.y;
+      } else {
+        const double2 q2 = __ldcg(reinterpret_cast<const double2*>(pp));
+        v.x = q2.x; v.y = q2.y;
+      }
+      a = cadd(a, v);
+    }
+    x[int64_t(Sn.first + jj) * S + i] = cadd(zin[int64_t(Sn.first + jj) * S + i], a);
+  }
+  if (tid == 0) counters[t.w] = 0u;
+}
+
+template <typename V, int S>
+static void solve_multi_t(const FactorDev& F, const V* t_in, V* z, V* x, V* u, V* part, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fwd_multi<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_bwd_multi<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  const V* P = (const V*)F.panels;
+  const size_t fsm = size_t(kMaxK * S + 2 * 64 * S) * sizeof(V);
+  for (int l = 0; l < F.nlev; l++) {
+    const int64_t b = F.h_mfwd_ptr[l], e = F.h_mfwd_ptr[l + 1];
+    if (e > b) {
+      HZ_COUNT();
+      k_fwd_multi<V, S><<<unsigned(e - b), 128, fsm, st>>>(F.mfwd_tasks + b, F.sn, F.cptr, F.cidx, P, t_in, z, u);
+    }
+  }
+  const size_t bsm = size_t(F.mbwd_rows * S + 4 * 32 * S) * sizeof(V);
+  for (int l = F.nlev - 1; l >= 0; l--) {
+    const int64_t b = F.h_mbwd_ptr[l], e = F.h_mbwd_ptr[l + 1];
+    if (e > b) {
+      HZ_COUNT();
+      k_bwd_multi<V, S><<<unsigned(e - b), 128, bsm, st>>>(F.mbwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                           F.mbwd_rows, F.mbfin_tasks, F.mbwd_counters);
+    }
+  }
+}
+
+template <typename V, int S>
+static void prec_multi_t(const FactorDev& F, const double2* src, const double2* y, double2* dst, cudaStream_t st) {
+  V* t = (V*)F.mt_loc;
+  HZ_COUNT();
+  k_gather_multi<V, S><<<grid_for(F.ntot * S, 256), 256, 0, st>>>(F.ntot, F.gidx, src, t);
+  solve_multi_t<V, S>(F, t, (V*)F.mz_loc, (V*)F.mx_loc, (V*)F.mu_ws, (V*)F.mbwd_partial, st);
+  HZ_COUNT();
+  k_prolong_multi<V, S><<<grid_for(F.nglob * S, 256), 256, 0, st>>>(F.nglob, F.pptr, F.pidx, F.pw,
+                                                                   (const V*)F.mx_loc, y, dst);
+}
+
+// dst = y + sum_i R_i^T D_i A_i^{-1} R_i src  (S interleaved right-hand sides)
+void launch_local_multi(const FactorDev& F, int S, const double2* src, const double2* y, double2* dst,
+                        cudaStream_t st) {
+  if (F.precision == 0) {
+    if (S == 4) prec_multi_t<double2, 4>(F, src, y, dst, st);
+    else if (S == 8) prec_multi_t<double2, 8>(F, src, y, dst, st);
+    else prec_multi_t<double2, 16>(F, src, y, dst, st);
+  } else {
+    if (S == 4) prec_multi_t<float2, 4>(F, src, y, dst, st);
+    else if (S == 8) prec_multi_t<float2, 8>(F, src, y, dst, st);
+    else prec_multi_t<float2, 16>(F, src, y, dst, st);
+  }
+}
+
+// interleaved <-> per-right-hand-side column layouts
+__global__ void k_interleave(int64_t n, int S, int active, const double2* cols, int64_t stride, double2* inter) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / S;
+    const int i = int(e % S);
+    inter[e] = (i < active) ? cols[i * stride + r] : make_double2(0.0, 0.0);
+  }
+}
+__global__ void k_deinterleave(int64_t n, int S, int active, const double2* inter, double2* cols, int64_t stride) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / S;
+    const int i = int(e % S);
+    if (i < active) cols[i * stride + r] = inter[e];
+  }
+}
+void launch_interleave(int64_t n, int S, int active, const double2* cols, int64_t stride, double2* inter,
+                       cudaStream_t st) {
+  HZ_COUNT();
+  k_interleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, active, cols, stride, inter);
+}
+void launch_deinterleave(int64_t n, int S, int active, const double2* inter, double2* cols, int64_t stride,
+                         cudaStream_t st) {
+  HZ_COUNT();
+  k_deinterleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, active, inter, cols, stride);
+}
+
+// Y = A X (or SUB - A X) for S interleaved vectors; lanes of a warp split the right-hand sides.
+template <int S>
+__global__ void __launch_bounds__(256) k_spmv_multi(int64_t n, const int64_t* rp, const int32_t* ci,
+                                                    const double2* val, const double2* x, const double2* sub,
+                                                    double2* y) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = e / S;
+    const int i = int(e % S);
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    const int64_t q1 = rp[row + 1];
+    int64_t q = rp[row];
+    for (; q + 1 < q1; q += 2) {
+      a0 = cmad(val[q], x[int64_t(ci[q]) * S + i], a0);
+      a1 = cmad(val[q + 1], x[int64_t(ci[q + 1]) * S + i], a1);
+    }
+    if (q < q1) a0 = cmad(val[q], x[int64_t(ci[q]) * S + i], a0);
+    const double2 acc = cadd(a0, a1);
+    y[e] = sub ? csub(sub[e], acc) : acc;
+  }
+}
+template <int S>
+__global__ void __launch_bounds__(256) k_spmv_real_multi(int64_t n, const int64_t* rp, const int32_t* ci,
+                                                         const double* val, const double2* x, double2* y) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = e / S;
+    const int i = int(e % S);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t q = rp[row]; q < rp[row + 1]; q++) {
+      const double2 v = x[int64_t(ci[q]) * S + i];
+      acc.x = xfma(val[q], v.x, acc.x);
+      acc.y = xfma(val[q], v.y, acc.y);
+    }
+    y[e] = acc;
+  }
+}
+void launch_spmv_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
+                       const double2* sub, double2* y, cudaStream_t st) {
+  HZ_COUNT();
+  const unsigned g = grid_for(n * S, 256, 152 * 32);
+  if (S == 4) k_spmv_multi<4><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+  else if (S == 8) k_spmv_multi<8><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+  else k_spmv_multi<16><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+}
+void launch_spmv_real_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double* val,
+                            const double2* x, double2* y, cudaStream_t st) {
+  HZ_COUNT();
+  const unsigned g = grid_for(n * S, 256, 152 * 32);
+  if (S == 4) k_spmv_real_multi<4><<<g, 256, 0, st>>>(n, rp, ci, val, x, y);
+  else if (S == 8) k_spmv_real_multi<8><<<g, 256, 0, st>>>(n, rp, ci, val, x, y);
+  else k_spmv_real_multi<16><<<g, 256, 0, st>>>(n, rp, ci, val, x, y);
+}
+
+// ---------------------------------------------------------------------------
 // sparse matrix-vector products
 // ---------------------------------------------------------------------------
 template <int TPR>

@@ -46,6 +46,7 @@ class Options(C.Structure):
         ("restart", C.c_int32), ("precision", C.c_int32), ("max_iter", C.c_int32),
         ("leaf_size", C.c_int32), ("max_snode", C.c_int32),
         ("hbm_budget", C.c_uint64), ("elem_part", C.c_void_p), ("stream", C.c_void_p),
+        ("block_size", C.c_int32),
     ]
 
 
@@ -163,7 +164,7 @@ class _MeshArrays:
 
 
 def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=2000, leaf_size=0,
-                 max_snode=0, hbm_budget=0, elem_part=None, stream=0):
+                 max_snode=0, hbm_budget=0, elem_part=None, stream=0, block_size=0):
     o = Options()
     o.nsub, o.overlap, o.levels, o.restart = int(nsub), int(overlap), int(levels), int(restart)
     o.precision, o.max_iter = int(precision), int(max_iter)
@@ -172,6 +173,7 @@ def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=200
     part = None if elem_part is None else _c(elem_part, np.int32)
     o.elem_part = _ptr(part)
     o.stream = int(stream) if stream else None
+    o.block_size = int(block_size)
     return o, part
 
 
