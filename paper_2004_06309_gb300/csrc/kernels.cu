@@ -869,8 +869,9 @@ template <typename V, int S>
 static void solve_multi_t(const FactorDev& F, const V* t_in, V* z, V* x, V* u, V* part, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fwd_multi<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_bwd_multi<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // at most 64 KB are used (S = 16, complex128); leave room for the static shared variables
+    cudaFuncSetAttribute(k_fwd_multi<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_bwd_multi<V, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const V* P = (const V*)F.panels;
