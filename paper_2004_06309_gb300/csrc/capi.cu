@@ -49,6 +49,7 @@ struct hz_ctx {
   std::vector<cudaGraphExec_t> gexec;
   std::vector<long long> gcount;
   bool graphs = true;
+  int spmv_lanes = 0;                      // autotuned at the first hz_factor (0: not yet)
   int* brk = nullptr;
   hz::DevStatus* status = nullptr;
   double* h_pin = nullptr;                 // pinned: est, invh, invbeta, beta, brk, norm
@@ -713,6 +714,35 @@ hz_status fgmres_block(hz_ctx* c, int nact, double tol, hz_rhs_info* info) {
   return HZ_OK;
 }
 
+// Autotuner: lanes per row of the complex SpMV, timed on this matrix (3 runs each
+// after a warm-up, CUDA events on the context stream); the fastest is kept.
+hz_status tune_spmv(hz_ctx* c) {
+  CU(cudaMemsetAsync(c->b, 0x3f, size_t(c->n) * 16, c->st));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int pick = 8;
+  for (int t : {2, 4, 8, 16}) {
+    hz::set_spmv_lanes(t);
+    hz::launch_spmv(c->n, c->d_rp, c->d_ci, c->d_A, c->b, nullptr, c->w, c->st);
+    CU(cudaEventRecord(e0, c->st));
+    for (int r = 0; r < 3; r++) hz::launch_spmv(c->n, c->d_rp, c->d_ci, c->d_A, c->b, nullptr, c->w, c->st);
+    CU(cudaEventRecord(e1, c->st));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->spmv_lanes = pick;
+  return HZ_OK;
+}
+
 hz_status check_ctx(hz_ctx* c) {
   if (!c) return HZ_ERR_ARG;
   cudaError_t e = cudaSetDevice(c->device);
@@ -1060,6 +1090,8 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
   c->factored = false;
   const double w = 2.0 * M_PI * freq_hz;
   hz::launch_fill_values(c->nnz, c->d_K, c->d_M, c->d_B, w, c->d_A, c->st);
+  if (c->spmv_lanes == 0) TRY(tune_spmv(c));
+  hz::set_spmv_lanes(c->spmv_lanes);
   double minp = 1e300;
   TRY(factor_one(c, c->loc, w, c->loc_max, minp));
   if (c->levels == 2) TRY(factor_one(c, c->crs, w, c->crs_max, minp));
@@ -1072,6 +1104,7 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
 
 extern "C" hz_status hz_apply_A(hz_ctx* c, const void* x, void* y) {
   TRY(check_ctx(c));
+  if (c->spmv_lanes) hz::set_spmv_lanes(c->spmv_lanes);
   if (!x || !y) return fail(c, HZ_ERR_ARG, "null vector");
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run first (A depends on the frequency)");
   hz::launch_spmv(c->n, c->d_rp, c->d_ci, c->d_A, (const double2*)x, nullptr, (double2*)y, c->st);
@@ -1081,6 +1114,7 @@ extern "C" hz_status hz_apply_A(hz_ctx* c, const void* x, void* y) {
 
 extern "C" hz_status hz_apply_M(hz_ctx* c, const void* v, void* z) {
   TRY(check_ctx(c));
+  if (c->spmv_lanes) hz::set_spmv_lanes(c->spmv_lanes);
   if (!v || !z) return fail(c, HZ_ERR_ARG, "null vector");
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run first");
   apply_prec(c, (const double2*)v, (double2*)z);
@@ -1091,6 +1125,7 @@ extern "C" hz_status hz_apply_M(hz_ctx* c, const void* v, void* z) {
 extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double tol, void* x, int32_t on_device,
                               hz_rhs_info* info) {
   TRY(check_ctx(c));
+  if (c->spmv_lanes) hz::set_spmv_lanes(c->spmv_lanes);
   if (!rhs || !x || nrhs < 0 || !(tol > 0.0)) return fail(c, HZ_ERR_ARG, "bad solve arguments");
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run before hz_solve");
   const int64_t n = c->n;
@@ -1156,6 +1191,7 @@ extern "C" hz_status hz_point_sources(hz_ctx* c, const double* xyz, int32_t nsrc
 
 extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   TRY(check_ctx(c));
+  if (c->spmv_lanes) hz::set_spmv_lanes(c->spmv_lanes);
   if (!out || reps < 1) return fail(c, HZ_ERR_ARG, "bad profile arguments");
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run first");
   std::memset(out, 0, sizeof(*out));

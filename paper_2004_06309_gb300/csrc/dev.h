@@ -118,6 +118,7 @@ void launch_spmv_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, c
                        const double2* sub, double2* y, cudaStream_t st);
 void launch_spmv_real_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double* val,
                             const double2* x, double2* y, cudaStream_t st);
+void set_spmv_lanes(int tpr);     // 2, 4, 8 or 16 lanes per row (calling thread)
 void launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                  const double2* sub, double2* y, cudaStream_t st);
 void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, const double2* x,

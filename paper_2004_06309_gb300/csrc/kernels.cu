@@ -1042,11 +1042,20 @@ __global__ void __launch_bounds__(256) k_spmv_real(int64_t n, const int64_t* rp,
   }
 }
 
+// Lanes per row for the complex SpMV (set per context by its autotuner).
+static thread_local int g_spmv_tpr = 8;
+void set_spmv_lanes(int tpr) { g_spmv_tpr = tpr; }
+
 void launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                  const double2* sub, double2* y, cudaStream_t st) {
   if (n == 0) return;
   HZ_COUNT();
-  k_spmv<8><<<grid_for(n * 8, 256, 152 * 32), 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+  const int t = g_spmv_tpr;
+  const unsigned g = grid_for(n * t, 256, 152 * 32);
+  if (t == 2) k_spmv<2><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+  else if (t == 4) k_spmv<4><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+  else if (t == 16) k_spmv<16><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
+  else k_spmv<8><<<g, 256, 0, st>>>(n, rp, ci, val, x, sub, y);
 }
 
 void launch_spmv_real(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, const double2* x,
