@@ -410,32 +410,16 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
 //   rows >= k:  u = (children's updates) - G b1.
 constexpr int kMaxK = 128;
 // ROWS rows of one supernode per task; the 256 threads split into 256 / ROWS column groups.
-// With ROWS = 16 (long chains of single supernodes, where latency rules) every thread
-// loads its at most 8 panel values into registers before the right-hand-side gather,
-// so the HBM round trips overlap instead of following one another.
 template <typename V, int ROWS>
 __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                              const int64_t* cidx, const V* panels, const V* tin, V* zout,
                                              V* u) {
   constexpr int CG = 256 / ROWS;
-  constexpr int NPF = (ROWS == 16) ? kMaxK / CG : 1;     // prefetched columns per thread
   __shared__ V b1[kMaxK];
   __shared__ V part[CG][ROWS];
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
-  const int rr = tid % ROWS, cg = tid / ROWS;
-  const int r = t.y * ROWS + rr;
-  const V* P = panels + S.paneloff;
-  const int jmax = (r < m) ? min(r, k) : 0;
-  V pv[NPF];
-  if constexpr (ROWS == 16) {
-#pragma unroll
-    for (int q = 0; q < NPF; q++) {
-      const int j = cg + q * CG;
-      pv[q] = (j < jmax) ? P[r + int64_t(j) * S.ld] : czero<V>();
-    }
-  }
   const int64_t* cp = cptr + S.rowoff;
   for (int j = tid; j < k; j += blockDim.x) {
     V acc = tin[S.first + j];
@@ -443,15 +427,12 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
     b1[j] = acc;
   }
   __syncthreads();
+  const int rr = tid % ROWS, cg = tid / ROWS;
+  const int r = t.y * ROWS + rr;
+  const V* P = panels + S.paneloff;
   V acc = czero<V>(), acc2 = czero<V>();
-  if constexpr (ROWS == 16) {
-#pragma unroll
-    for (int q = 0; q < NPF; q += 2) {
-      const int j = cg + q * CG;
-      if (j < jmax) acc = cmad(pv[q], b1[j], acc);
-      if (j + CG < jmax) acc2 = cmad(pv[q + 1], b1[j + CG], acc2);
-    }
-  } else {
+  if (r < m) {
+    const int jmax = min(r, k);
     int j = cg;
     for (; j + CG < jmax; j += 2 * CG) {
       acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
@@ -531,35 +512,21 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, c = tid & 31, s = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
-  const int j = t.y * 32 + c;
-  const int slice = (rows + 7) / 8;
-  const int ra = max(r0 + s * slice, j + 1), rb = min(r1, r0 + (s + 1) * slice);
-  const double2* col = panels + S.paneloff + int64_t(min(j, k - 1)) * S.ld;
-  // short slices (64-row chunks): load the slice before staging the right-hand side
-  constexpr int NPF = 8;
-  double2 pv[NPF];
-  const bool pref = slice <= NPF;
-#pragma unroll
-  for (int q = 0; q < NPF; q++) pv[q] = (pref && j < k && ra + q < rb) ? col[ra + q] : make_double2(0.0, 0.0);
   const int32_t* rl = rowlist + S.rowoff;
   for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
   __syncthreads();
+  const int j = t.y * 32 + c;
+  const int slice = (rows + 7) / 8;
+  const int ra = max(r0 + s * slice, j + 1), rb = min(r1, r0 + (s + 1) * slice);
   double2 a0 = make_double2(0.0, 0.0), a1 = a0;
   if (j < k) {
-    if (pref) {
-#pragma unroll
-      for (int q = 0; q < NPF; q += 2) {
-        if (ra + q < rb) a0 = cmad(pv[q], vec[ra + q - r0], a0);
-        if (ra + q + 1 < rb) a1 = cmad(pv[q + 1], vec[ra + q + 1 - r0], a1);
-      }
-    } else {
-      int r = ra;
-      for (; r + 1 < rb; r += 2) {
-        a0 = cmad(col[r], vec[r - r0], a0);
-        a1 = cmad(col[r + 1], vec[r + 1 - r0], a1);
-      }
-      if (r < rb) a0 = cmad(col[r], vec[r - r0], a0);
+    const double2* col = panels + S.paneloff + int64_t(j) * S.ld;
+    int r = ra;
+    for (; r + 1 < rb; r += 2) {
+      a0 = cmad(col[r], vec[r - r0], a0);
+      a1 = cmad(col[r + 1], vec[r + 1 - r0], a1);
     }
+    if (r < rb) a0 = cmad(col[r], vec[r - r0], a0);
   }
   red[s][c] = cadd(a0, a1);
   __syncthreads();
