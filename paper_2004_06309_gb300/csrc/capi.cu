@@ -135,10 +135,9 @@ std::vector<double2> to_d2(const std::vector<cplx>& v) {
 
 // Device copy of a symbolic set with its task lists.
 hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
-                        double maxabs[3], int bwd_rows, int nrhs_block, int fwd_rows) {
+                        double maxabs[3], int bwd_rows, int nrhs_block) {
   F = hz::FactorDev();
   F.bwd_rows = bwd_rows;
-  F.fwd_rows = fwd_rows;
   F.precision = precision;
   F.nmat = S.nmat;
   F.nsn = int(S.sn_k.size());
@@ -254,7 +253,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
-      const int frows = precision == 0 ? fwd_rows : 256;     // forward task rows (k_fwd / k_fwd_c64)
+      const int frows = precision == 0 ? 64 : 256;     // forward task rows (k_fwd / k_fwd_c64)
       for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
       const int nch = (m + bwd_rows - 1) / bwd_rows;
       for (int cb = 0; cb * 32 < k; cb++) {
@@ -1007,7 +1006,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     }
   }
   SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max,
-                          op->precision == HZ_MIXED ? 512 : 256, c->S, 64));
+                          op->precision == HZ_MIXED ? 512 : 256, c->S));
   if (c->levels == 2) {
     SETUP_TRY(upload(c, &c->d_Zrp, P.Z.ptr));
     SETUP_TRY(upload(c, &c->d_Zci, P.Z.col));
@@ -1015,9 +1014,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     SETUP_TRY(upload(c, &c->d_Ztrp, P.Zt.ptr));
     SETUP_TRY(upload(c, &c->d_Ztci, P.Zt.col));
     SETUP_TRY(upload(c, &c->d_Ztv, P.Ztv));
-    // the coarse factor is one matrix whose tree top is a long chain of single supernodes:
-    // short tasks spread each link's FP64 work over all SMs
-    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 64, c->S, 16));
+    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S));
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));
   }

@@ -20,7 +20,6 @@ struct FactorDev {
   int nmat = 0, nsn = 0, nlev = 0;
   int32_t maxk = 0, maxm = 0;
   int32_t bwd_rows = 512;        // rows per backward partial task (<= 512)
-  int32_t fwd_rows = 64;         // rows per forward task (complex128 kernels: 16 or 64)
   int64_t ntot = 0, nrows = 0, panel_elems = 0, u_elems = 0, front_elems = 0, nentries = 0;
   SnDev* sn = nullptr;
   int32_t* rowlist = nullptr;

@@ -408,15 +408,14 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
 // Forward, 64 rows of one supernode per task:
 //   b1 = t[pivots] + children's updates;  rows < k:  z = D^{-1} (T b1);
 //   rows >= k:  u = (children's updates) - G b1.
+constexpr int kFwdRows = 64;
 constexpr int kMaxK = 128;
-// ROWS rows of one supernode per task; the 256 threads split into 256 / ROWS column groups.
-template <typename V, int ROWS>
+template <typename V>
 __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                              const int64_t* cidx, const V* panels, const V* tin, V* zout,
                                              V* u) {
-  constexpr int CG = 256 / ROWS;
   __shared__ V b1[kMaxK];
-  __shared__ V part[CG][ROWS];
+  __shared__ V part[4][kFwdRows];
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
@@ -427,24 +426,23 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
     b1[j] = acc;
   }
   __syncthreads();
-  const int rr = tid % ROWS, cg = tid / ROWS;
-  const int r = t.y * ROWS + rr;
+  const int rr = tid & (kFwdRows - 1), cg = tid / kFwdRows;
+  const int r = t.y * kFwdRows + rr;
   const V* P = panels + S.paneloff;
   V acc = czero<V>(), acc2 = czero<V>();
   if (r < m) {
     const int jmax = min(r, k);
     int j = cg;
-    for (; j + CG < jmax; j += 2 * CG) {
+    for (; j + 4 < jmax; j += 8) {
       acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
-      acc2 = cmad(P[r + int64_t(j + CG) * S.ld], b1[j + CG], acc2);
+      acc2 = cmad(P[r + int64_t(j + 4) * S.ld], b1[j + 4], acc2);
     }
     if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
   }
   part[cg][rr] = cadd(acc, acc2);
   __syncthreads();
   if (cg == 0 && r < m) {
-    V tot = part[0][rr];
-    for (int q = 1; q < CG; q++) tot = cadd(tot, part[q][rr]);
+    const V tot = cadd(cadd(part[0][rr], part[1][rr]), cadd(part[2][rr], part[3][rr]));
     if (r < k) {
       zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
     } else {
@@ -664,12 +662,7 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       if constexpr (sizeof(V) == 8)
         k_fwd_c64<<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
       else
-      {
-        if (F.fwd_rows == 16)
-          k_fwd<V, 16><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
-        else
-          k_fwd<V, 64><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
-      }
+        k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
   }
   for (int l = F.nlev - 1; l >= 0; l--) {
