@@ -405,7 +405,52 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
     dst[q] = from2<V>(src[gidx[q]]);
 }
 
+// Forward, 64 rows of one supernode per task:
+//   b1 = t[pivots] + children's updates;  rows < k:  z = D^{-1} (T b1);
+//   rows >= k:  u = (children's updates) - G b1.
 constexpr int kMaxK = 128;
+template <typename V>
+__global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+                                             const int64_t* cidx, const V* panels, const V* tin, V* zout,
+                                             V* u) {
+  __shared__ V b1[kMaxK];
+  __shared__ V part[4][kFwdRows];
+  const int2 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, tid = threadIdx.x;
+  const int64_t* cp = cptr + S.rowoff;
+  for (int j = tid; j < k; j += blockDim.x) {
+    V acc = tin[S.first + j];
+    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+    b1[j] = acc;
+  }
+  __syncthreads();
+  const int rr = tid & (kFwdRows - 1), cg = tid / kFwdRows;
+  const int r = t.y * kFwdRows + rr;
+  const V* P = panels + S.paneloff;
+  V acc = czero<V>(), acc2 = czero<V>();
+  if (r < m) {
+    const int jmax = min(r, k);
+    int j = cg;
+    for (; j + 4 < jmax; j += 8) {
+      acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+      acc2 = cmad(P[r + int64_t(j + 4) * S.ld], b1[j + 4], acc2);
+    }
+    if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+  }
+  part[cg][rr] = cadd(acc, acc2);
+  __syncthreads();
+  if (cg == 0 && r < m) {
+    const V tot = cadd(cadd(part[0][rr], part[1][rr]), cadd(part[2][rr], part[3][rr]));
+    if (r < k) {
+      zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
+    } else {
+      V b2 = czero<V>();
+      for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+      u[S.uoff + (r - k)] = csub(b2, tot);
+    }
+  }
+}
 
 // Backward, split over row chunks so that tall supernodes use many CTAs:
 //   partial[task][c] = sum over the task's rows r > j of P[r][j] vec[r],
