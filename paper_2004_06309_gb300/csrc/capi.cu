@@ -253,7 +253,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
-      const int frows = precision == 0 ? 32 : 256;     // forward task rows (k_fwd_c128 / k_fwd_c64)
+      const int frows = precision == 0 ? 64 : 256;     // forward task rows (k_fwd / k_fwd_c64)
       for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
       const int nch = (m + bwd_rows - 1) / bwd_rows;
       for (int cb = 0; cb * 32 < k; cb++) {

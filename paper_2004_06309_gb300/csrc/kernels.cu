@@ -408,6 +408,7 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
 // Forward, 64 rows of one supernode per task:
 //   b1 = t[pivots] + children's updates;  rows < k:  z = D^{-1} (T b1);
 //   rows >= k:  u = (children's updates) - G b1.
+constexpr int kFwdRows = 64;
 constexpr int kMaxK = 128;
 template <typename V>
 __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
@@ -495,59 +496,6 @@ __device__ __forceinline__ void bwd_finish(const int4 fin, const SnDev& S, const
   }
 }
 
-// complex128 forward, 32 rows per task, 8 column groups; every thread loads all of its
-// (at most 16) panel values into registers right after the supernode descriptor, so
-// that one HBM round trip (overlapping the right-hand-side gather) replaces a chain
-// of dependent loads -- the tree top is a long chain of single supernodes, where
-// per-CTA latency, not throughput, sets the time.
-__global__ void __launch_bounds__(256) k_fwd_c128(const int2* tasks, const SnDev* sn, const int64_t* cptr,
-                                                  const int64_t* cidx, const double2* panels, const double2* tin,
-                                                  double2* zout, double2* u) {
-  constexpr int ROWS = 32, CG = 8, NPF = kMaxK / CG;
-  __shared__ double2 b1[kMaxK];
-  __shared__ double2 part[CG][ROWS];
-  const int2 t = tasks[blockIdx.x];
-  const SnDev S = sn[t.x];
-  const int k = S.k, m = S.m, tid = threadIdx.x;
-  const int rr = tid % ROWS, cg = tid / ROWS;
-  const int r = t.y * ROWS + rr;
-  const double2* P = panels + S.paneloff;
-  const int jmax = (r < m) ? min(r, k) : 0;
-  double2 pv[NPF];
-#pragma unroll
-  for (int q = 0; q < NPF; q++) {
-    const int j = cg + q * CG;
-    pv[q] = (j < jmax) ? P[r + int64_t(j) * S.ld] : make_double2(0.0, 0.0);
-  }
-  const int64_t* cp = cptr + S.rowoff;
-  for (int j = tid; j < k; j += blockDim.x) {
-    double2 acc = tin[S.first + j];
-    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
-    b1[j] = acc;
-  }
-  __syncthreads();
-  double2 a0 = make_double2(0.0, 0.0), a1 = a0;
-#pragma unroll
-  for (int q = 0; q < NPF; q += 2) {
-    const int j = cg + q * CG;
-    if (j < jmax) a0 = cmad(pv[q], b1[j], a0);
-    if (j + CG < jmax) a1 = cmad(pv[q + 1], b1[j + CG], a1);
-  }
-  part[cg][rr] = cadd(a0, a1);
-  __syncthreads();
-  if (cg == 0 && r < m) {
-    double2 tot = part[0][rr];
-    for (int q = 1; q < CG; q++) tot = cadd(tot, part[q][rr]);
-    if (r < k) {
-      zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
-    } else {
-      double2 b2 = make_double2(0.0, 0.0);
-      for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
-      u[S.uoff + (r - k)] = csub(b2, tot);
-    }
-  }
-}
-
 // complex128 backward partial sums, transposed mapping for FP64 throughput: thread
 // (c, s) sums column j = 32 * block + c over slice s (of 8) of the chunk's rows,
 // reading its column sequentially (L1 reuse of each 128-byte line); the 8 slice
@@ -556,35 +504,27 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
                                                           const int32_t* rowlist, const double2* panels,
                                                           const double2* zin, double2* x, double2* partial,
                                                           int rows, const int4* fins, unsigned int* counters) {
-  constexpr int D = 8;                                  // register pipeline depth (rows)
   __shared__ double2 vec[kBwdRows];
   __shared__ double2 red[8][33];
   const int4 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, c = tid & 31, s = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
-  const int j = t.y * 32 + c;
-  const int slice = (rows + 7) / 8;
-  const int ra = max(r0 + s * slice, j + 1), rb = (j < k) ? min(r1, r0 + (s + 1) * slice) : ra;
-  const double2* col = panels + S.paneloff + int64_t(min(j, k - 1)) * S.ld;
-  double2 pv[D];
-#pragma unroll
-  for (int q = 0; q < D; q++) pv[q] = (ra + q < rb) ? col[ra + q] : make_double2(0.0, 0.0);
   const int32_t* rl = rowlist + S.rowoff;
   for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
   __syncthreads();
+  const int j = t.y * 32 + c;
+  const int slice = (rows + 7) / 8;
+  const int ra = max(r0 + s * slice, j + 1), rb = min(r1, r0 + (s + 1) * slice);
   double2 a0 = make_double2(0.0, 0.0), a1 = a0;
-  for (int rbase = ra; rbase < rb; rbase += D) {
-    double2 nx[D];
-#pragma unroll
-    for (int q = 0; q < D; q++) nx[q] = (rbase + D + q < rb) ? col[rbase + D + q] : make_double2(0.0, 0.0);
-#pragma unroll
-    for (int q = 0; q < D; q += 2) {
-      if (rbase + q < rb) a0 = cmad(pv[q], vec[rbase + q - r0], a0);
-      if (rbase + q + 1 < rb) a1 = cmad(pv[q + 1], vec[rbase + q + 1 - r0], a1);
+  if (j < k) {
+    const double2* col = panels + S.paneloff + int64_t(j) * S.ld;
+    int r = ra;
+    for (; r + 1 < rb; r += 2) {
+      a0 = cmad(col[r], vec[r - r0], a0);
+      a1 = cmad(col[r + 1], vec[r + 1 - r0], a1);
     }
-#pragma unroll
-    for (int q = 0; q < D; q++) pv[q] = nx[q];
+    if (r < rb) a0 = cmad(col[r], vec[r - r0], a0);
   }
   red[s][c] = cadd(a0, a1);
   __syncthreads();
@@ -722,7 +662,7 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       if constexpr (sizeof(V) == 8)
         k_fwd_c64<<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
       else
-        k_fwd_c128<<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+        k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
   }
   for (int l = F.nlev - 1; l >= 0; l--) {
