@@ -231,7 +231,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   std::vector<int2> fwd, wg, ea;
   std::vector<int4> bwd, bfin;
   int64_t max_bwd_level = 0;
-  std::vector<int4> cbt;
+  std::vector<int4> cbt, tct;
   std::vector<int64_t> scr_off(ns, 0);
   std::vector<std::vector<int32_t>> children(ns);
   for (int s = 0; s < ns; s++)
@@ -240,7 +240,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   for (int s = 0; s < ns; s++) max_slot = std::max(max_slot, int(children[s].size()));
   F.max_slot = max_slot;
   std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
-      cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1);
+      cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1), tc_ptr(nlev + 1);
   int64_t scratch = 0;
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
@@ -249,6 +249,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     bfin_ptr[l] = int64_t(bfin.size());
     wg_ptr[l] = int64_t(wg.size());
     cb_ptr[l] = int64_t(cbt.size());
+    tc_ptr[l] = int64_t(tct.size());
     int64_t lev_scr = 0;
     for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
       const int s = S.lev_sn[q];
@@ -262,9 +263,15 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
         for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, fin));
       }
       for (int rb = 0; rb * 32 < r; rb++) wg.push_back(make_int2(s, rb));
-      const int T = (r + 31) / 32;
-      for (int ti = 0; ti < T; ti++)
-        for (int tj = 0; tj <= ti; tj++) cbt.push_back(make_int4(s, ti, tj, 0));
+      if (precision == 0) {
+        const int T = (r + 31) / 32;
+        for (int ti = 0; ti < T; ti++)
+          for (int tj = 0; tj <= ti; tj++) cbt.push_back(make_int4(s, ti, tj, 0));
+      } else {
+        const int T = (r + 127) / 128;
+        for (int ti = 0; ti < T; ti++)
+          for (int tj = 0; tj <= ti; tj++) tct.push_back(make_int4(s, ti, tj, 0));
+      }
       scr_off[s] = lev_scr;
       lev_scr += int64_t(r) * k;
     }
@@ -288,6 +295,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   bfin_ptr[nlev] = int64_t(bfin.size());
   wg_ptr[nlev] = int64_t(wg.size());
   cb_ptr[nlev] = int64_t(cbt.size());
+  tc_ptr[nlev] = int64_t(tct.size());
   ea_ptr[int64_t(nlev) * max_slot] = int64_t(ea.size());
   F.scratch_elems = scratch;
   TRY(upload(c, &F.fwd_tasks, fwd));
@@ -296,6 +304,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   TRY(upload(c, &F.bwd_counters, std::vector<unsigned int>(std::max<size_t>(bfin.size(), 1), 0u)));
   TRY(upload(c, &F.wg_tasks, wg));
   TRY(upload(c, &F.cb_tasks, cbt));
+  TRY(upload(c, &F.tc_tasks, tct));
   TRY(upload(c, &F.ea_tasks, ea));
   TRY(upload(c, &F.scr_off, scr_off));
   TRY(upload(c, &F.lev_sn, S.lev_sn));
@@ -310,6 +319,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_bfin_ptr = hcopy(bfin_ptr);
   F.h_wg_ptr = hcopy(wg_ptr);
   F.h_cb_ptr = hcopy(cb_ptr);
+  F.h_tc_ptr = hcopy(tc_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
   F.h_ent_ptr = hcopy(S.ent_ptr);
   // batched sweeps for nrhs_block right-hand sides (pseudo-block FGMRES)
@@ -384,6 +394,8 @@ void free_host_ptrs(hz::FactorDev& F) {
   delete[] F.h_bfin_ptr;
   delete[] F.h_wg_ptr;
   delete[] F.h_cb_ptr;
+  delete[] F.h_tc_ptr;
+  F.h_tc_ptr = nullptr;
   delete[] F.h_ea_ptr;
   delete[] F.h_ent_ptr;
   delete[] F.h_mfwd_ptr;
@@ -402,7 +414,7 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
     dfree(c, fronts);
     return s;
   }
-  hz::DevStatus init{0u, 0u, 0.0};
+  hz::DevStatus init{0u, 0u, 0.0};   // zero_pivot, timeout, min_pivot
   const double big = 1e300;
   std::memcpy(&init.min_pivot, &big, sizeof(double));
   CU(cudaMemcpyAsync(c->status, &init, sizeof(init), cudaMemcpyHostToDevice, c->st));
@@ -415,6 +427,7 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
   dfree(c, fronts);
   dfree(c, scratch);
   min_pivot = std::min(min_pivot, out.min_pivot);
+  if (out.timeout) return fail(c, HZ_ERR_TIMEOUT, "a tensor-core completion wait ran out in the factorisation");
   if (out.zero_pivot) return fail(c, HZ_ERR_ZERO_PIVOT, "tiny pivot in a local LDL^T factor");
   return HZ_OK;
 }

@@ -47,6 +47,8 @@ struct FactorDev {
   int2* ea_tasks = nullptr;      // (child sn, col block)
   int2* wg_tasks = nullptr;      // (sn, row block of the off-diagonal part)
   int4* cb_tasks = nullptr;      // (sn, row tile, col tile, scratch-relative offset unused)
+  int4* tc_tasks = nullptr;      // complex64 path: (sn, 128-row tile, 128-col tile, 0), tensor-core Schur update
+  int64_t* h_tc_ptr = nullptr;   // nlev + 1 (host)
   int64_t* scr_off = nullptr;    // per supernode: offset of its W block in the level scratch
   int32_t* lev_sn = nullptr;
   int64_t* h_lev_ptr = nullptr;       // nlev + 1 (host)
@@ -90,7 +92,7 @@ struct FactorDev {
 // Status word written by device code (pivot health).
 struct DevStatus {
   unsigned int zero_pivot;
-  unsigned int nonfinite;
+  unsigned int timeout;          // a bounded wait on a tensor-core completion barrier ran out
   double min_pivot;   // stored as the bit pattern of a non-negative double (atomicMin on u64)
 };
 

@@ -95,6 +95,9 @@ template <typename V> __device__ __forceinline__ V warp_sum(V v) {
   return v;
 }
 
+// widest supernode (pivot columns) any kernel handles
+constexpr int kMaxK = 128;
+
 static inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 16) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -307,6 +310,175 @@ __global__ void __launch_bounds__(256) k_cb(const int4* tasks, const SnDev* sn, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05) Schur update of complex64 fronts, one 128 x 128 lower
+// tile of the contribution block per CTA (4 warps):
+//   F22[a][b] -= sum_i W[a][i] d_i^{-1} W[b][i]      (complex, i < k)
+// as two real products over K' = 2k:
+//   Re = [Wr | Wi] [Br | -Bi]^T,  Im = [Wr | Wi] [Bi | Br]^T,   B = W diag(d^{-1}),
+// each in 3xTF32 (hi*hi + hi*lo + lo*hi, hi = TF32 rounding, lo = the remainder),
+// accumulated in FP32 in tensor memory (Re: columns 0-127, Im: 128-255).
+// Operands are staged K-major in shared memory as 8-row x 16-byte core matrices
+// (no swizzle), 32 K-elements per stage.  Every wait on the MMA-completion
+// barrier is bounded: on timeout the CTA raises status->timeout, skips its
+// epilogue and still frees its tensor memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+// float offset of element (row r, k) in a 128 x 32 K-major tile of core matrices
+__device__ __forceinline__ int tc_off(int r, int kk) { return ((r >> 3) * 8 + (kk >> 2)) * 32 + (r & 7) * 4 + (kk & 3); }
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  // LBO = 128 B (next core matrix along K), SBO = 1024 B (next 8-row group), version 1, no swizzle
+  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
+  // D f32, A/B tf32, both K-major, N = 128, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+               :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; it++)
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(smem_addr(mbar)), "r"(phase));
+  return done != 0;
+}
+__device__ __forceinline__ void tc_ld32(uint32_t ta, float* out) {
+  uint32_t v[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                 "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                 "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                 "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+               : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 32; j++) out[j] = __uint_as_float(v[j]);
+}
+
+constexpr int kTcSmemFloats = 6 * 128 * 32;   // Ah, Al, B1h, B1l, B2h, B2l: 96 KB
+__global__ void __launch_bounds__(128) k_cb_tc(const int4* tasks, const SnDev* sn, const int64_t* scr_off,
+                                               float2* fronts, const float2* scratch, DevStatus* status) {
+  extern __shared__ __align__(1024) float tsm[];
+  float* Ah = tsm;
+  float* Al = Ah + 4096;
+  float* B1h = Al + 4096;
+  float* B1l = B1h + 4096;
+  float* B2h = B1l + 4096;
+  float* B2l = B2h + 4096;
+  __shared__ float2 dinv[kMaxK];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int4 t = tasks[blockIdx.x];
+  const SnDev S = sn[t.x];
+  const int k = S.k, m = S.m, r = m - k, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int a0 = t.y * 128, b0 = t.z * 128;
+  const float2* W = scratch + scr_off[t.x];          // r x k, column-major (ld r)
+  float2* F = fronts + S.frontoff;
+  for (int i = tid; i < k; i += blockDim.x) dinv[i] = F[i + int64_t(i) * m];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&tmem_base)), "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar)), "r"(1));
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int K2 = 2 * k;
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int kc = 0; kc < K2 && ok; kc += 32) {
+    // stage: thread = row of the A tile (a0 + tid) and of the B tile (b0 + tid)
+    const int ra = a0 + tid, rb = b0 + tid;
+    for (int q = 0; q < 32; q++) {
+      const int kap = kc + q;
+      float a = 0.f, b1 = 0.f, b2 = 0.f;
+      if (kap < K2) {
+        const int i = kap < k ? kap : kap - k;
+        if (ra < r) {
+          const float2 w = W[ra + int64_t(i) * r];
+          a = kap < k ? w.x : w.y;
+        }
+        if (rb < r) {
+          const float2 bw = cmul(W[rb + int64_t(i) * r], dinv[i]);
+          b1 = kap < k ? bw.x : -bw.y;
+          b2 = kap < k ? bw.y : bw.x;
+        }
+      }
+      const int o = tc_off(tid, q);
+      const float ah = tf32_rna(a), b1h = tf32_rna(b1), b2h = tf32_rna(b2);
+      Ah[o] = ah;
+      Al[o] = tf32_rna(a - ah);
+      B1h[o] = b1h;
+      B1l[o] = tf32_rna(b1 - b1h);
+      B2h[o] = b2h;
+      B2l[o] = tf32_rna(b2 - b2h);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      for (int kk = 0; kk < 4; kk++) {
+        const uint32_t off = kk * 256;                  // two core matrices (8 K-elements) per MMA
+        const uint32_t acc0 = (kc > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t dah = tc_desc(smem_addr(Ah) + off), dal = tc_desc(smem_addr(Al) + off);
+        tc_mma(tmem, dah, tc_desc(smem_addr(B1h) + off), acc0);
+        tc_mma(tmem, dah, tc_desc(smem_addr(B1l) + off), 1u);
+        tc_mma(tmem, dal, tc_desc(smem_addr(B1h) + off), 1u);
+        tc_mma(tmem + 128, dah, tc_desc(smem_addr(B2h) + off), acc0);
+        tc_mma(tmem + 128, dah, tc_desc(smem_addr(B2l) + off), 1u);
+        tc_mma(tmem + 128, dal, tc_desc(smem_addr(B2h) + off), 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_addr(&mbar)));
+    }
+    const bool mine = tc_wait(&mbar, phase);
+    ok = __syncthreads_and(mine) != 0;                 // block-uniform; the stage may be overwritten
+    if (ok) phase ^= 1u;
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&status->timeout, 1u);
+    tc_wait(&mbar, phase);                             // second bounded wait for MMAs still in flight
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int a = a0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      float re[32], im[32];
+      const uint32_t ta = tmem + (uint32_t(warp * 32) << 16) + c0;
+      tc_ld32(ta, re);
+      tc_ld32(ta + 128, im);
+      if (a < r) {
+        for (int j = 0; j < 32; j++) {
+          const int b = b0 + c0 + j;
+          if (b < r && a >= b) {
+            const int64_t pos = (k + a) + int64_t(k + b) * m;
+            float2 f = F[pos];
+            f.x -= re[j];
+            f.y -= im[j];
+            F[pos] = f;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256));
+}
+
 template <typename V>
 __global__ void k_front_zero(const int32_t* lev_sn, const SnDev* sn, V* fronts) {
   const SnDev S = sn[lev_sn[blockIdx.x]];
@@ -363,10 +535,19 @@ static void factor_level_t(const FactorDev& F, int lev, double w, V* fronts, V* 
     k_wg<V><<<unsigned(we - wb), 256, wg_smem(F.maxk, sizeof(V)), st>>>(F.wg_tasks + wb, F.sn, F.scr_off, fronts,
                                                                        scratch);
   }
-  const int64_t cbb = F.h_cb_ptr[lev], cbe = F.h_cb_ptr[lev + 1];
-  if (cbe > cbb) {
-    HZ_COUNT();
-    k_cb<V><<<unsigned(cbe - cbb), 256, 0, st>>>(F.cb_tasks + cbb, F.sn, F.scr_off, fronts, scratch);
+  if constexpr (sizeof(V) == 8) {
+    const int64_t tb = F.h_tc_ptr[lev], te = F.h_tc_ptr[lev + 1];
+    if (te > tb) {
+      HZ_COUNT();
+      k_cb_tc<<<unsigned(te - tb), 128, kTcSmemFloats * sizeof(float), st>>>(F.tc_tasks + tb, F.sn, F.scr_off,
+                                                                            fronts, scratch, status);
+    }
+  } else {
+    const int64_t cbb = F.h_cb_ptr[lev], cbe = F.h_cb_ptr[lev + 1];
+    if (cbe > cbb) {
+      HZ_COUNT();
+      k_cb<V><<<unsigned(cbe - cbb), 256, 0, st>>>(F.cb_tasks + cbb, F.sn, F.scr_off, fronts, scratch);
+    }
   }
   HZ_COUNT();
   k_panel_copy<V><<<unsigned(nb), 256, 0, st>>>(lsn, F.sn, fronts, (V*)F.panels);
@@ -381,6 +562,7 @@ static void set_attrs(int prec, int kmax) {
     cudaFuncSetAttribute(k_wg<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   } else {
     cudaFuncSetAttribute(k_diag<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_cb_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemFloats * int(sizeof(float)));
     cudaFuncSetAttribute(k_wg<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   }
   g_attr_done[prec] = true;
@@ -409,7 +591,6 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
 //   b1 = t[pivots] + children's updates;  rows < k:  z = D^{-1} (T b1);
 //   rows >= k:  u = (children's updates) - G b1.
 constexpr int kFwdRows = 64;
-constexpr int kMaxK = 128;
 template <typename V>
 __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                              const int64_t* cidx, const V* panels, const V* tin, V* zout,
