@@ -406,6 +406,8 @@ void free_host_ptrs(hz::FactorDev& F) {
 
 hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[3], double& min_pivot) {
   if (F.nsn == 0) return HZ_OK;
+  static const bool verbose = std::getenv("HZ_VERBOSE") != nullptr;
+  auto t0 = std::chrono::steady_clock::now();
   const size_t vs = F.precision == 0 ? 16 : 8;
   char *fronts = nullptr, *scratch = nullptr;
   TRY(dalloc(c, &fronts, F.front_elems * int64_t(vs)));
@@ -419,13 +421,29 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
   std::memcpy(&init.min_pivot, &big, sizeof(double));
   CU(cudaMemcpyAsync(c->status, &init, sizeof(init), cudaMemcpyHostToDevice, c->st));
   const double tiny = 1e-13 * (maxabs[0] + w * w * maxabs[1] + w * maxabs[2]);
+  if (verbose) {
+    cudaStreamSynchronize(c->st);
+    std::fprintf(stderr, "[hz] factor: workspace %.2f GB allocated in %.3f s\n",
+                 double(F.front_elems) * double(vs) / 1e9,
+                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    t0 = std::chrono::steady_clock::now();
+  }
   for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, w, fronts, scratch, c->status, tiny, c->st);
+  if (verbose) {
+    cudaStreamSynchronize(c->st);
+    std::fprintf(stderr, "[hz] factor: %d levels in %.3f s\n", F.nlev,
+                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    t0 = std::chrono::steady_clock::now();
+  }
   CU(cudaGetLastError());
   hz::DevStatus out{};
   CU(cudaMemcpyAsync(&out, c->status, sizeof(out), cudaMemcpyDeviceToHost, c->st));
   CU(cudaStreamSynchronize(c->st));
   dfree(c, fronts);
   dfree(c, scratch);
+  if (verbose)
+    std::fprintf(stderr, "[hz] factor: status read and workspace freed in %.3f s\n",
+                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
   min_pivot = std::min(min_pivot, out.min_pivot);
   if (out.timeout) return fail(c, HZ_ERR_TIMEOUT, "a tensor-core completion wait ran out in the factorisation");
   if (out.zero_pivot) return fail(c, HZ_ERR_ZERO_PIVOT, "tiny pivot in a local LDL^T factor");
