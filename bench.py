@@ -152,13 +152,207 @@ def scaled_rhs_per_s(sample, n_full, it_full):
     return work_ratio / sample["seconds"]
 
 
+# Serving workload: the request stream over 3 seeded Overthrust-shaped models and 5
+# frequencies, scaled down 2x in frequency (8x in dofs) so that cold-loading all 15
+# problems and serving the stream takes about a minute per precision.
+SERVE_SEEDS = (0, 1, 2)
+SERVE_FREQS = (1.0, 1.25, 1.5, 2.0, 2.5)
+
+
+def serve_problem(seed, f):
+    import synth
+    cells = (int(round(10 * f)), int(round(10 * f)), max(3, int(round(2.4 * f))))
+    nsub = 8 if f < 1.5 else 16
+    return synth.overthrust_problem(seed=seed, freq=f, cells=cells, nsub=nsub, overlap=2, restart=50, levels=2)
+
+
+def serve_requests(rng, nreq, rate, max_batch):
+    """Poisson arrivals (exponential gaps at `rate` per second); each request names a
+    problem uniformly, and 1..max_batch sources at uniform surface positions, 50 m deep."""
+    import numpy as np
+    gaps = rng.exponential(1.0 / rate, nreq)
+    out = []
+    for k in range(nreq):
+        pid = int(rng.integers(0, len(SERVE_SEEDS) * len(SERVE_FREQS)))
+        nb = int(rng.integers(1, max_batch + 1))
+        xy = rng.uniform(0.5, 19.5, (nb, 2))
+        pts = np.column_stack([xy, np.full(nb, 0.05)])
+        out.append((float(gaps[k]), pid, pts))
+    return out
+
+
+def serve_bench(args):
+    """Continuous-batching server under a Poisson request stream; p50/p99 request latency
+    and RHS/s, mixed precision against FP64."""
+    import threading
+
+    import numpy as np
+    import torch
+    from paper_2004_06309_gb300 import build, hz
+    torch.cuda.set_device(0)
+    build.build()
+    t0 = time.time()
+    probs = [serve_problem(sd, f) for sd in SERVE_SEEDS for f in SERVE_FREQS]
+    t_gen = time.time() - t0
+    budget = 150 * 10**9
+    res = {}
+    for pname in ({"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]):
+        srv = hz.Server(slots=16, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, hbm_budget=budget)
+        ids = [srv.add_problem(p) for p in probs]
+        # cold start: one single-source request per problem loads every factorisation
+        tc = time.time()
+        warm = [srv.submit(i, [[10.0, 10.0, 0.05]], 1e-6) for i in ids]
+        for r in warm:
+            srv.wait(r)
+        t_cold = time.time() - tc
+        dofs = [srv.ndofs(i) for i in ids]
+        # capacity: a closed burst of requests with the stream's batch mix
+        rng = np.random.default_rng(11)
+        burst = serve_requests(rng, max(args.warmup, 3) * 8, 1.0, args.serve_batch)
+        tb = time.time()
+        reqs = [srv.submit(pid, pts, 1e-6) for _, pid, pts in burst]
+        for r in reqs:
+            srv.wait(r)
+        cap = sum(len(p) for _, _, p in burst) / (time.time() - tb)
+        rate = 0.7 * cap / ((1 + args.serve_batch) / 2.0)        # ~70 % of the measured capacity
+        stream = serve_requests(np.random.default_rng(12), args.steps, rate, args.serve_batch)
+        s0 = srv.stats()
+        clocks = Clocks(0, os.path.join(ROOT, "gpurun_out", f"clocks_serve_{pname}.csv")) \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(0, f"/tmp/clocks_serve_{pname}.csv")
+        done = []
+        lock = threading.Lock()
+
+        def collect(r, n_src, n_dof):
+            X, inf, t = srv.wait(r)
+            with lock:
+                done.append((t["latency_s"], n_src, max(i for i, _, _ in inf), all(st == 0 for _, st, _ in inf),
+                             n_src * n_dof * 16))
+
+        threads = []
+        ts = time.time()
+        nxt = ts
+        for gap, pid, pts in stream:
+            nxt += gap
+            dt = nxt - time.time()
+            if dt > 0:
+                time.sleep(dt)
+            r = srv.submit(pid, pts, 1e-6)
+            th = threading.Thread(target=collect, args=(r, len(pts), dofs[pid]))
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        wall = time.time() - ts
+        ck = clocks.stop()
+        s1 = srv.stats()
+        lat = np.array([d[0] for d in done])
+        nrhs = sum(d[1] for d in done)
+        res[pname] = dict(rhs_per_s=nrhs / wall, p50=float(np.percentile(lat, 50, method="inverted_cdf")),
+                          p99=float(np.percentile(lat, 99, method="inverted_cdf")), requests=len(done), rhs=nrhs,
+                          all_ok=all(d[3] for d in done), max_iterations=max(d[2] for d in done),
+                          capacity_rhs_per_s=cap, rate_req_per_s=rate, cold_start_s=t_cold,
+                          factor_seconds=s1["factor_seconds"], factorisations=s1["factorisations"],
+                          evictions=s1["evictions"], peak_resident_gb=s1["peak_resident_bytes"] / 1e9,
+                          launches=s1["launches"] - s0["launches"], clocks=ck, wall_s=wall, dofs=dofs,
+                          h2d_bytes_per_request=sum(24 * d[1] for d in done) / len(done),
+                          d2h_bytes_per_request=sum(d[4] for d in done) / len(done))
+        srv.close()
+        torch.cuda.empty_cache()
+    main_p = "mixed" if "mixed" in res else "fp64"
+    R = res[main_p]
+    line = {
+        "metric": METRIC, "value": R["rhs_per_s"], "unit": "RHS/s", "n_gpus": 1, "steps": R["requests"],
+        "warmup": len(probs), "ms_per_step": 1e3 * R["wall_s"] / max(R["requests"], 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64 subdomain factors/solves + complex128 Krylov, SpMV, coarse" if main_p == "mixed"
+        else "complex128",
+        "data": "synthetic",
+        "config": {"workload": "serving: Poisson stream over 3 Overthrust-shaped models x 5 frequencies",
+                   "seeds": list(SERVE_SEEDS), "freqs_hz": list(SERVE_FREQS),
+                   "dofs": R["dofs"],
+                   "batch_sources": [1, args.serve_batch], "slots": 16, "hbm_budget_gb": budget / 1e9,
+                   "tol": 1e-6, "arrival": "Poisson at 70% of the measured closed-loop capacity",
+                   "l2": "factors and Krylov bases >> 129 MB", "parallelism": "replicas x1"},
+        "latency_ms": {"p50": 1e3 * R["p50"], "p99": 1e3 * R["p99"]},
+        "e2e": {"value": R["rhs_per_s"], "unit": "RHS/s", "h2d_bytes_per_step": R["h2d_bytes_per_request"],
+                "d2h_bytes_per_step": R["d2h_bytes_per_request"],
+                "note": "value is already end to end (host wall clock from submission of host source "
+                        "coordinates to collection of host solutions); a step is one request"},
+        "gpu_launches": R["launches"], "clocks": R["clocks"], "serving": R,
+        "generate_seconds": t_gen,
+    }
+    if "fp64" in res and main_p != "fp64":
+        line["fp64"] = res["fp64"]
+    print(json.dumps(line))
+
+
+def trends_bench(args):
+    """Shape of the paper's Table 1 and its remarks on synthetic models (no real model):
+    iterations of one- and two-level ORAS-FGMRES against frequency (mesh and subdomain
+    count growing with it), the effect of attenuation Q, and the cost of 10 right-hand
+    sides against one.  Mixed precision, tol 1e-6, one source at (2.5, 2.5, 0.58) km."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2004_06309_gb300 import build, hz
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def run(p, levels, nrhs=1, block=0):
+        G = hz.Solver(p, precision=hz.HZ_MIXED, stream=stream, block_size=block)
+        G.factor()
+        if nrhs > 1:
+            B = torch.from_numpy(np.asfortranarray(G.point_sources(synth.surface_source_grid()[:nrhs]))).cuda()
+        else:
+            B = torch.from_numpy(G.point_sources(p.sources)[:, 0].copy()).cuda()
+        G.solve(B)                                   # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        X, info = G.solve(B)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        n = G.n
+        G.close()
+        torch.cuda.empty_cache()
+        return dict(n=n, iterations=max(i[0] for i in info), seconds=dt, ok=all(i[1] == 0 for i in info))
+
+    freqs = [(1.25, (12, 12, 3), 8), (2.5, (25, 25, 6), 16), (5.0, (50, 50, 12), 64)]
+    table = []
+    for f, cells, nsub in freqs:
+        row = {"freq_hz": f, "nsub": nsub}
+        for lv in (1, 2):
+            p = synth.overthrust_problem(seed=0, freq=f, cells=cells, nsub=nsub, overlap=2, levels=lv)
+            r = run(p, lv)
+            row["n_dofs"] = r["n"]
+            row[f"{lv}level"] = {"iterations": r["iterations"], "seconds": r["seconds"], "ok": r["ok"]}
+        table.append(row)
+    qrows = []
+    for Q in (50.0, 100.0, 1000.0):
+        p = synth.overthrust_problem(seed=0, freq=2.5, cells=(25, 25, 6), nsub=16, overlap=2, levels=2, Q=Q)
+        r = run(p, 2)
+        qrows.append({"Q": Q, "iterations": r["iterations"], "ok": r["ok"]})
+    p = synth.overthrust_problem(seed=0, freq=5.0, cells=(50, 50, 12), nsub=64, overlap=2, levels=2)
+    one = run(p, 2)
+    ten = run(p, 2, nrhs=10, block=16)
+    line = {"experiment": "trends (Table 1 shape on synthetic Overthrust-shaped models)",
+            "iterations_vs_frequency": table, "attenuation_2p5hz": qrows,
+            "multi_rhs_5hz": {"one_rhs_s": one["seconds"], "ten_rhs_s": ten["seconds"],
+                              "ratio_10_to_1": ten["seconds"] / one["seconds"],
+                              "iterations": [one["iterations"], ten["iterations"]]},
+            "precision": "mixed", "tol": 1e-6}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
-    ap.add_argument("--workload", default="overthrust-5hz", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="overthrust-5hz", choices=list(WORKLOADS) + ["serving", "trends"])
+    ap.add_argument("--serve-batch", type=int, default=16, help="largest sources per request (serving)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0,
@@ -172,6 +366,11 @@ def main():
 
     if args.oracle_sample:
         print(json.dumps(run_oracle_sample(args.steps, args.warmup)))
+        return
+
+    if args.workload in ("serving", "trends") and args.impl == "hz":
+        if int(os.environ.get("RANK", "0")) == 0:
+            (serve_bench if args.workload == "serving" else trends_bench)(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

@@ -96,6 +96,11 @@ typedef struct {
                                section).  0/1: one at a time; 2..16 (padded to 4, 8 or
                                16).  Results per right-hand side are those of a solve
                                alone up to rounding.                                  */
+  int32_t spmv_lanes;       /* lanes per row of the complex CSR SpMV: 0 = autotuned at
+                               the first hz_factor (fastest of 2, 4, 8, 16 on this
+                               matrix); 2, 4, 8 or 16 = fixed.  The choice sets the
+                               summation order, so contexts that must agree bitwise
+                               fix it.                                                */
 } hz_options;
 
 typedef struct {
@@ -231,6 +236,115 @@ const char* hz_status_string(hz_status s);
 /* Message of the last error on this context ("" if none). */
 const char* hz_last_error(const hz_ctx* ctx);
 void hz_free(hz_ctx* ctx); /* NULL-safe; releases every device buffer of the context */
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of point-source solves over cached factors.
+ *
+ * The experiments section solves many sources per frequency by reusing one
+ * factorisation and batching right-hand sides (multi-RHS forward/back solves,
+ * pseudo-block GMRES).  A server keeps that reuse across requests: each
+ * registered problem (a mesh at one frequency) is analysed once, made resident
+ * (device setup + hz_factor) when a request needs it, and kept resident until the
+ * HBM budget forces out the least recently used idle problem.  Each source of a
+ * request takes one slot of its problem's pseudo-block FGMRES (block_size =
+ * slots); a slot freed by a converged source takes the next queued source at the
+ * next step, while the other slots continue.  Steps of different resident
+ * problems are issued on their own streams and overlap on the device.  Every
+ * source follows the same per-right-hand-side recurrence whatever else shares
+ * its steps, so a result is the same alone and in the mix.
+ * A server runs two native threads (loader, solver) on options.device.  All
+ * entry points are thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct hz_server hz_server;
+
+typedef struct {
+  uint64_t hbm_budget;      /* device bytes all resident problems may hold together,
+                               factorisation workspace included (0: free memory at
+                               creation minus 2 GiB)                                  */
+  int32_t slots;            /* right-hand sides per problem advanced together, 2..16
+                               (rounded up to 4, 8 or 16)                            */
+  int32_t precision;        /* HZ_FP64 or HZ_MIXED, for every problem                 */
+  int32_t device;           /* CUDA device                                            */
+} hz_server_options;
+
+typedef struct {
+  double submit_s;          /* seconds since hz_server_create: submission             */
+  double admit_s;           /* first source admitted to a slot                        */
+  double done_s;            /* last source finished                                   */
+  double latency_s;         /* done_s - submit_s                                      */
+  int32_t nsrc;
+  int32_t status;           /* worst per-source status                               */
+} hz_request_times;
+
+typedef struct {
+  int64_t requests_done, rhs_done;
+  double p50_latency_s, p99_latency_s;  /* nearest rank over finished requests       */
+  double rhs_per_s;         /* rhs_done / (last completion - first submission)        */
+  int64_t analyses;         /* host analyses (once per problem)                        */
+  int64_t factorisations;   /* device setups + hz_factor (again after an eviction)     */
+  int64_t evictions;
+  int64_t resident_bytes, peak_resident_bytes, budget_bytes;
+  int64_t steps;            /* slot-engine steps, one per busy problem per round       */
+  double factor_seconds;    /* wall time spent in analysis, setup and factorisation   */
+  int64_t launches;         /* kernel launches of the library (process-wide counter)
+                               since the server was created                         */
+} hz_server_stats;
+
+/* Starts a server (no problem is loaded yet).  HZ_ERR_ARG for slots outside
+   [2, 16] or a bad precision; HZ_ERR_CUDA if the device cannot be selected. */
+hz_status hz_server_create(const hz_server_options* opt, hz_server** out);
+
+/* Registers a problem: mesh (copied; the caller keeps its arrays), solver options
+   (nsub, overlap, levels, restart, max_iter, leaf_size, max_snode, elem_part
+   copied; precision and block_size come from the server; stream and hbm_budget
+   are the server's) and the frequency.  Nothing runs until a request names it.
+   *problem_id counts from 0 in registration order. */
+hz_status hz_server_add_problem(hz_server* s, const hz_mesh_desc* mesh, const hz_options* opt, double freq_hz,
+                                int32_t* problem_id);
+
+/* Queues a request: nsrc point sources (host xyz, 3 x nsrc, copied) on one problem,
+   each solved to ||b - A x|| / ||b|| <= tol from x0 = 0 (right-hand side as
+   hz_point_sources).  Returns at once with *request_id.  HZ_ERR_ARG for an unknown
+   problem, nsrc < 0 or tol <= 0.  A source outside the mesh finishes with
+   HZ_ERR_ARG in its hz_rhs_info. */
+hz_status hz_server_submit(hz_server* s, int32_t problem_id, const double* src_xyz, int32_t nsrc, double tol,
+                           uint64_t* request_id);
+
+/* Waits at most timeout_s seconds (<= 0: no limit) for a request to finish and
+   fills *times (NULL to skip).  HZ_OK once it has finished (whatever its sources'
+   statuses: see times->status, or hz_server_collect); HZ_ERR_TIMEOUT if it is
+   still queued or running at the limit; HZ_ERR_ARG for an unknown or already
+   collected id.  The request stays until collected. */
+hz_status hz_server_wait(hz_server* s, uint64_t request_id, double timeout_s, hz_request_times* times);
+
+/* Copies a finished request's solutions to x (host complex128, n x nsrc
+   column-major, n = hz_server_ndofs(problem); NULL to skip; untouched if the
+   problem never became resident), its per-source results to info (nsrc entries;
+   NULL to skip) and its times, and forgets the request.  Returns the worst
+   per-source status (HZ_ERR_OOM if the problem could not fit the budget even
+   alone); HZ_ERR_STATE if it has not finished; HZ_ERR_ARG for an unknown id. */
+hz_status hz_server_collect(hz_server* s, uint64_t request_id, void* x, hz_rhs_info* info, hz_request_times* times);
+
+/* Dofs of a registered problem once analysed (after its first request was
+   admitted), else -1. */
+int64_t hz_server_ndofs(hz_server* s, int32_t problem_id);
+
+hz_status hz_server_get_stats(hz_server* s, hz_server_stats* out);
+/* Message of the server's last problem error ("" if none). */
+const char* hz_server_last_error(hz_server* s);
+/* Stops both threads (sources still running are abandoned), frees every resident
+   problem and the server.  NULL-safe. */
+void hz_server_free(hz_server* s);
+
+/* Admission rule of the server, exposed for callers that schedule contexts
+   themselves: to add `need` bytes to `resident` under `budget`, pick residents
+   among those with evictable[i] != 0 in increasing last_use (stable on ties),
+   until resident - freed + need <= budget.  Writes their indices to out (up to
+   count entries) and returns how many; 0 when it already fits (or budget <= 0);
+   -1 when evicting every evictable one would not make room (out then holds
+   nothing useful) or on bad arguments. */
+int32_t hz_select_evictions(int32_t count, const int64_t* bytes, const double* last_use, const int32_t* evictable,
+                            int64_t resident, int64_t need, int64_t budget, int32_t* out);
 
 #ifdef __cplusplus
 }

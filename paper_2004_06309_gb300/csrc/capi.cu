@@ -13,6 +13,7 @@
 
 #include "../../include/hz.h"
 #include "dev.h"
+#include "engine.h"
 #include "host.h"
 
 using hz::cplx;
@@ -63,6 +64,18 @@ struct hz_ctx {
   double2 *Hb = nullptr, *snb = nullptr, *gb = nullptr, *yb = nullptr;
   double *csb = nullptr, *scalb = nullptr;
   int* brkb = nullptr;
+  // slot engine (continuous pseudo-block FGMRES): one right-hand side per slot
+  enum { SLOT_FREE = hz_engine::SLOT_FREE, SLOT_RUN = hz_engine::SLOT_RUN, SLOT_DONE = hz_engine::SLOT_DONE };
+  struct Slot {
+    int state = SLOT_FREE;
+    int64_t tag = -1;
+    double tol = 0.0, bnorm = 0.0;
+    int its = 0, j = 0;               // iterations so far; position in the current cycle
+    hz_rhs_info info{0, HZ_OK, 0.0};
+  };
+  std::vector<Slot> slots;
+  // pinned host scalars: [0, 8) single-RHS loop, then per-slot scalars, flags and |b|
+  enum { PIN_SLOT = 8, PIN_FLAGS = 8 + 8 * 16, PIN_BNORM = 8 + 8 * 16 + 16, PIN_TOTAL = 8 + 8 * 16 + 32 };
   std::vector<void*> allocs;
   std::vector<size_t> sizes;
   int64_t bytes = 0;
@@ -607,11 +620,11 @@ hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
 }
 
 // ---------------------------------------------------------------------------
-// Pseudo-block FGMRES: S right-hand sides, one Krylov space each, advanced in
-// lock-step cycles.  Every preconditioner and operator application works on the S
-// vectors at once (interleaved per row), so each factor panel is read once for S
-// right-hand sides; orthogonalisation, Givens updates and stopping decisions stay
-// per right-hand side, exactly as in fgmres_one.
+// Pseudo-block FGMRES: S slots, each holding one right-hand side with its own Krylov
+// space, Givens rotations, cycle position and stopping decisions (the recurrence of
+// fgmres_one).  Every preconditioner and operator application works on the S vectors
+// at once (interleaved per row), so each factor panel is read once for S right-hand
+// sides; a slot whose solve ends takes new work while the others continue.
 // ---------------------------------------------------------------------------
 void apply_prec_multi(hz_ctx* c, const double2* X, double2* Y) {
   const int S = c->S;
@@ -627,121 +640,224 @@ void apply_prec_multi(hz_ctx* c, const double2* X, double2* Y) {
   }
 }
 
-hz_status fgmres_block(hz_ctx* c, int nact, double tol, hz_rhs_info* info) {
+double2* slot_V(hz_ctx* c, int i) { return c->Vb + int64_t(i) * c->n * (c->restart + 1); }
+double2* slot_Z(hz_ctx* c, int i) { return c->Zb + int64_t(i) * c->n * c->restart; }
+double2* slot_col(hz_ctx* c, double2* base, int i) { return base + int64_t(i) * c->n; }
+double* slot_scal(hz_ctx* c, int i) { return c->scalb + int64_t(i) * 8; }
+
+// New cycle of slot i from the residual in Wc[i] (|r|^2 in nrm): g = beta e_1, v_0 = r / beta.
+void slot_cycle(hz_ctx* c, int i) {
+  const int m = c->restart;
+  hz::launch_init_cycle(c->nrm, c->gb + int64_t(i) * (m + 1), m, slot_scal(c, i) + 2, slot_scal(c, i) + 3, c->st);
+  hz::launch_scale(c->n, slot_col(c, c->Wc, i), slot_scal(c, i) + 2, slot_V(c, i), c->st);
+  c->slots[i].j = 0;
+}
+
+}  // namespace
+
+namespace hz_engine {
+
+// Starts the right-hand side already in Bc[i] with x0 = 0 (r = b).
+hz_status slot_start(hz_ctx* c, int i, double tol, int64_t tag) {
+  hz_ctx::Slot& s = c->slots[i];
+  s = hz_ctx::Slot{};
+  s.tag = tag;
+  s.tol = tol;
+  s.state = hz_ctx::SLOT_RUN;
+  CU(cudaMemsetAsync(slot_col(c, c->Xc, i), 0, size_t(c->n) * 16, c->st));
+  TRY(norm2(c, slot_col(c, c->Bc, i), s.bnorm));        // leaves |b|^2 in nrm
+  if (s.bnorm == 0.0) {
+    s.state = hz_ctx::SLOT_DONE;
+    return HZ_OK;
+  }
+  if (!std::isfinite(s.bnorm)) {
+    s.state = hz_ctx::SLOT_DONE;
+    s.info.status = HZ_ERR_BREAKDOWN;
+    s.info.rel_residual = NAN;
+    return HZ_OK;
+  }
+  c->h_pin[hz_ctx::PIN_BNORM + i] = s.bnorm;             // |b| for the Givens breakdown test
+  CU(cudaMemcpyAsync(slot_scal(c, i) + 4, c->h_pin + hz_ctx::PIN_BNORM + i, sizeof(double),
+                     cudaMemcpyHostToDevice, c->st));
+  hz::launch_axpby_copy(c->n, slot_col(c, c->Bc, i), slot_col(c, c->Wc, i), c->st);
+  slot_cycle(c, i);
+  return HZ_OK;
+}
+
+// Right-hand side of one point source (Eq. 2 load -phi_a(x_s)) written into Bc[i].
+hz_status slot_point_source(hz_ctx* c, int i, const double xyz[3]) {
+  int64_t e = -1;
+  double lam[4], phi[10];
+  if (!hz::locate_point(c->mesh, xyz, e, lam)) return fail(c, HZ_ERR_ARG, "source outside the mesh");
+  hz::eval_basis(c->order, lam, phi);
+  hz::PointRhs p{};
+  for (int a = 0; a < c->dofs.nb; a++) {
+    const int64_t g = c->dofs.elem[int64_t(c->dofs.nb) * e + a];
+    if (c->dofs.is_dir[g]) continue;
+    p.idx[p.cnt] = g;
+    p.val[p.cnt] = -phi[a];
+    p.cnt++;
+  }
+  CU(cudaMemsetAsync(slot_col(c, c->Bc, i), 0, size_t(c->n) * 16, c->st));
+  hz::launch_point_rhs(p, slot_col(c, c->Bc, i), c->st);
+  return HZ_OK;
+}
+
+// Enqueues one inner iteration of every running slot (no host wait): the batched
+// z_j = M^{-1} v_j and w = A z_j over all S slots, then per slot CGS2 against its own
+// basis, the Givens update at its own position j and v_{j+1}; the per-slot residual
+// estimates and breakdown flags are copied to pinned memory.
+void slots_issue(hz_ctx* c) {
   const int S = c->S, m = c->restart;
   const int64_t n = c->n;
   const int nb = hz::cgs_blocks();
   cudaStream_t st = c->st;
-  std::vector<double> bnorm(S, 0.0);
-  std::vector<int> its(S, 0), kcyc(S, 0);
-  std::vector<char> done(S, 1), act(S, 0);
-  auto V = [&](int i) { return c->Vb + int64_t(i) * n * (m + 1); };
-  auto Zc = [&](int i) { return c->Zb + int64_t(i) * n * m; };
-  auto col = [&](double2* base, int i) { return base + int64_t(i) * n; };
-  auto scal = [&](int i) { return c->scalb + int64_t(i) * 8; };
-  CU(cudaMemsetAsync(c->Xc, 0, size_t(S) * n * 16, st));
-  for (int i = 0; i < nact; i++) {
-    TRY(norm2(c, col(c->Bc, i), bnorm[i]));
-    info[i].iterations = 0;
-    info[i].status = HZ_OK;
-    info[i].rel_residual = 0.0;
-    if (bnorm[i] == 0.0) continue;
-    if (!std::isfinite(bnorm[i])) {
-      info[i].status = HZ_ERR_BREAKDOWN;
-      info[i].rel_residual = NAN;
+  if (c->spmv_lanes) hz::set_spmv_lanes(c->spmv_lanes);
+  hz::SlotCols vin, zout, wout;
+  for (int i = 0; i < 16; i++) vin.o[i] = zout.o[i] = wout.o[i] = -1;
+  for (int i = 0; i < S; i++) {
+    const hz_ctx::Slot& s = c->slots[i];
+    if (s.state != hz_ctx::SLOT_RUN) continue;
+    vin.o[i] = int64_t(i) * n * (m + 1) + int64_t(s.j) * n;
+    zout.o[i] = int64_t(i) * n * m + int64_t(s.j) * n;
+    wout.o[i] = int64_t(i) * n;
+  }
+  hz::launch_interleave(n, S, vin, c->Vb, c->Xi, st);
+  apply_prec_multi(c, c->Xi, c->Yi);
+  hz::launch_deinterleave(n, S, zout, c->Yi, c->Zb, st);
+  hz::launch_spmv_multi(n, S, c->d_rp, c->d_ci, c->d_A, c->Yi, nullptr, c->Wi, st);
+  hz::launch_deinterleave(n, S, wout, c->Wi, c->Wc, st);
+  for (int i = 0; i < S; i++) {
+    const hz_ctx::Slot& s = c->slots[i];
+    if (s.state != hz_ctx::SLOT_RUN) continue;
+    const int j = s.j;
+    double2* w = slot_col(c, c->Wc, i);
+    double2* V = slot_V(c, i);
+    hz::launch_cgs(n, j + 1, V, n, nullptr, w, j + 1, c->partial, st);
+    hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
+    hz::launch_cgs(n, j + 1, V, n, c->h1, w, j + 1, c->partial, st);
+    hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
+    hz::launch_cgs(n, j + 1, V, n, c->h2, w, 0, c->partial, st);
+    hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+    hz::launch_givens(j, m, c->Hb + int64_t(i) * (m + 1) * m, c->csb + int64_t(i) * m, c->snb + int64_t(i) * m,
+                      c->gb + int64_t(i) * (m + 1), c->h1, c->h2, c->nrm, slot_scal(c, i) + 4, slot_scal(c, i),
+                      c->brkb + i, slot_scal(c, i) + 1, st);
+    hz::launch_scale(n, w, slot_scal(c, i) + 1, V + int64_t(j + 1) * n, st);
+  }
+  cudaMemcpyAsync(c->h_pin + hz_ctx::PIN_SLOT, c->scalb, size_t(S) * 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(c->h_pin + hz_ctx::PIN_FLAGS, c->brkb, size_t(S) * sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+// End of slot i's cycle: x += Z y, true residual ||b - A x|| / ||b||; the slot either
+// finishes (converged, iteration limit, non-finite) or restarts from that residual.
+static hz_status slot_end_cycle(hz_ctx* c, int i) {
+  hz_ctx::Slot& s = c->slots[i];
+  const int m = c->restart;
+  const int64_t n = c->n;
+  double2* xi = slot_col(c, c->Xc, i);
+  hz::launch_update_x(n, s.j, c->Hb + int64_t(i) * (m + 1) * m, m + 1, c->gb + int64_t(i) * (m + 1),
+                      c->yb + int64_t(i) * m, slot_Z(c, i), n, xi, c->st);
+  hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, xi, slot_col(c, c->Bc, i), slot_col(c, c->Wc, i), c->st);
+  double rn = 0;
+  TRY(norm2(c, slot_col(c, c->Wc, i), rn));             // leaves |r|^2 in nrm for a restart
+  const double rel = rn / s.bnorm;
+  s.info.iterations = s.its;
+  s.info.rel_residual = rel;
+  if (!std::isfinite(rel)) {
+    s.info.status = HZ_ERR_BREAKDOWN;
+    s.state = hz_ctx::SLOT_DONE;
+  } else if (rel <= s.tol) {
+    s.state = hz_ctx::SLOT_DONE;
+  } else if (s.its >= c->max_iter) {
+    s.info.status = HZ_ERR_NOT_CONVERGED;
+    s.state = hz_ctx::SLOT_DONE;
+  } else {
+    slot_cycle(c, i);
+  }
+  return HZ_OK;
+}
+
+// Waits for the step issued by slots_issue and applies each running slot's stopping
+// decisions (the rule of fgmres_one, per slot).
+hz_status slots_complete(hz_ctx* c) {
+  CU(cudaStreamSynchronize(c->st));
+  CU(cudaGetLastError());
+  const double* hs = c->h_pin + hz_ctx::PIN_SLOT;
+  const int* hb = reinterpret_cast<const int*>(c->h_pin + hz_ctx::PIN_FLAGS);
+  if (c->spmv_lanes) hz::set_spmv_lanes(c->spmv_lanes);
+  for (int i = 0; i < c->S; i++) {
+    hz_ctx::Slot& s = c->slots[i];
+    if (s.state != hz_ctx::SLOT_RUN) continue;
+    s.its++;
+    s.j++;
+    const double est = hs[8 * i];
+    if (!std::isfinite(est)) {
+      s.state = hz_ctx::SLOT_DONE;
+      s.info.iterations = s.its;
+      s.info.status = HZ_ERR_BREAKDOWN;
+      s.info.rel_residual = NAN;
       continue;
     }
-    done[i] = 0;
-    c->h_pin[6] = bnorm[i];
-    CU(cudaMemcpyAsync(scal(i) + 4, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
-    hz::launch_axpby_copy(n, col(c->Bc, i), col(c->Wc, i), st);                // r = b
-    hz::launch_cgs(n, 0, V(i), n, nullptr, col(c->Wc, i), 0, c->partial, st);
-    hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
-    hz::launch_init_cycle(c->nrm, c->gb + int64_t(i) * (m + 1), m, scal(i) + 2, scal(i) + 3, st);
-    hz::launch_scale(n, col(c->Wc, i), scal(i) + 2, V(i), st);
-    CU(cudaStreamSynchronize(st));
+    if (hb[i] || est <= s.tol || s.its >= c->max_iter || s.j == c->restart) TRY(slot_end_cycle(c, i));
   }
-  double* hs = c->h_pin + 8;                      // S x 8 scalars
-  int* hb = reinterpret_cast<int*>(c->h_pin + 8 + 8 * 16);
-  for (;;) {
-    bool any = false;
-    for (int i = 0; i < S; i++) {
-      act[i] = !done[i];
-      kcyc[i] = 0;
-      any = any || act[i];
+  return HZ_OK;
+}
+
+int slot_count(const hz_ctx* c) { return c->S; }
+void slot_reset(hz_ctx* c, int i) { c->slots[i] = hz_ctx::Slot{}; }
+int slot_state(const hz_ctx* c, int i) { return c->slots[i].state; }
+int64_t slot_tag(const hz_ctx* c, int i) { return c->slots[i].tag; }
+bool slots_running(const hz_ctx* c) {
+  for (int i = 0; i < c->S; i++)
+    if (c->slots[i].state == hz_ctx::SLOT_RUN) return true;
+  return false;
+}
+
+// Copies a finished slot's solution (device or host destination) and frees the slot.
+hz_status slot_harvest(hz_ctx* c, int i, void* x, bool on_device, hz_rhs_info* info) {
+  hz_ctx::Slot& s = c->slots[i];
+  if (s.state != hz_ctx::SLOT_DONE) return fail(c, HZ_ERR_STATE, "slot has no finished solve");
+  CU(cudaMemcpyAsync(x, slot_col(c, c->Xc, i), size_t(c->n) * 16,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  if (info) *info = s.info;
+  s = hz_ctx::Slot{};
+  return HZ_OK;
+}
+
+}  // namespace hz_engine
+
+namespace {
+
+// Pseudo-block solve of nrhs right-hand sides through the S slots: a slot whose solve
+// ends takes the next right-hand side at once, so the slots stay full.
+hz_status solve_slots(hz_ctx* c, const double2* rhs, int nrhs, double tol, double2* x, bool on_device,
+                      hz_rhs_info* info, hz_status& worst) {
+  const int64_t n = c->n;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (auto& s : c->slots) s = hz_ctx::Slot{};
+  int next = 0, left = nrhs;
+  while (left > 0) {
+    for (int i = 0; i < c->S && next < nrhs; i++) {
+      if (c->slots[i].state != hz_ctx::SLOT_FREE) continue;
+      CU(cudaMemcpyAsync(slot_col(c, c->Bc, i), rhs + int64_t(next) * n, size_t(n) * 16, kin, c->st));
+      TRY(hz_engine::slot_start(c, i, tol, next));
+      next++;
     }
-    if (!any) break;
-    for (int j = 0; j < m; j++) {
-      bool running = false;
-      for (int i = 0; i < S; i++) running = running || act[i];
-      if (!running) break;
-      hz::launch_interleave(n, S, nact, V(0) + int64_t(j) * n, n * (m + 1), c->Xi, st);
-      apply_prec_multi(c, c->Xi, c->Yi);
-      hz::launch_deinterleave(n, S, nact, c->Yi, Zc(0) + int64_t(j) * n, n * m, st);
-      hz::launch_spmv_multi(n, S, c->d_rp, c->d_ci, c->d_A, c->Yi, nullptr, c->Wi, st);
-      hz::launch_deinterleave(n, S, nact, c->Wi, c->Wc, n, st);
-      for (int i = 0; i < S; i++) {
-        if (!act[i]) continue;
-        double2* w = col(c->Wc, i);
-        hz::launch_cgs(n, j + 1, V(i), n, nullptr, w, j + 1, c->partial, st);
-        hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
-        hz::launch_cgs(n, j + 1, V(i), n, c->h1, w, j + 1, c->partial, st);
-        hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
-        hz::launch_cgs(n, j + 1, V(i), n, c->h2, w, 0, c->partial, st);
-        hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
-        hz::launch_givens(j, m, c->Hb + int64_t(i) * (m + 1) * m, c->csb + int64_t(i) * m, c->snb + int64_t(i) * m,
-                          c->gb + int64_t(i) * (m + 1), c->h1, c->h2, c->nrm, scal(i) + 4, scal(i), c->brkb + i,
-                          scal(i) + 1, st);
-        hz::launch_scale(n, w, scal(i) + 1, V(i) + int64_t(j + 1) * n, st);
-      }
-      CU(cudaMemcpyAsync(hs, c->scalb, size_t(S) * 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CU(cudaMemcpyAsync(hb, c->brkb, size_t(S) * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-      for (int i = 0; i < S; i++) {
-        if (!act[i]) continue;
-        its[i]++;
-        kcyc[i] = j + 1;
-        const double est = hs[8 * i];
-        if (!std::isfinite(est)) {
-          act[i] = 0;
-          done[i] = 1;
-          info[i].iterations = its[i];
-          info[i].status = HZ_ERR_BREAKDOWN;
-          info[i].rel_residual = NAN;
-          kcyc[i] = 0;
-          continue;
-        }
-        if (hb[i] || est <= tol || its[i] >= c->max_iter) act[i] = 0;
-      }
+    if (hz_engine::slots_running(c)) {
+      hz_engine::slots_issue(c);
+      TRY(hz_engine::slots_complete(c));
     }
-    // end of cycle: x_i += Z_i y_i, true residual, restart the unconverged
-    for (int i = 0; i < S; i++) {
-      if (done[i] || kcyc[i] == 0) continue;
-      double2* xi = col(c->Xc, i);
-      hz::launch_update_x(n, kcyc[i], c->Hb + int64_t(i) * (m + 1) * m, m + 1, c->gb + int64_t(i) * (m + 1),
-                          c->yb + int64_t(i) * m, Zc(i), n, xi, st);
-      hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, xi, col(c->Bc, i), col(c->Wc, i), st);
-      double rn = 0;
-      TRY(norm2(c, col(c->Wc, i), rn));
-      const double rel = rn / bnorm[i];
-      info[i].iterations = its[i];
-      info[i].rel_residual = rel;
-      if (!std::isfinite(rel)) {
-        info[i].status = HZ_ERR_BREAKDOWN;
-        done[i] = 1;
-      } else if (rel <= tol) {
-        done[i] = 1;
-      } else if (its[i] >= c->max_iter) {
-        info[i].status = HZ_ERR_NOT_CONVERGED;
-        done[i] = 1;
-      } else {
-        hz::launch_init_cycle(c->nrm, c->gb + int64_t(i) * (m + 1), m, scal(i) + 2, scal(i) + 3, st);
-        hz::launch_scale(n, col(c->Wc, i), scal(i) + 2, V(i), st);
-      }
+    for (int i = 0; i < c->S; i++) {
+      if (c->slots[i].state != hz_ctx::SLOT_DONE) continue;
+      const int64_t k = c->slots[i].tag;
+      hz_rhs_info inf{};
+      TRY(hz_engine::slot_harvest(c, i, x + k * n, on_device, &inf));
+      if (info) info[k] = inf;
+      if (inf.status != HZ_OK && worst == HZ_OK) worst = hz_status(inf.status);
+      left--;
     }
-    CU(cudaGetLastError());
   }
-  CU(cudaStreamSynchronize(st));
   return HZ_OK;
 }
 
@@ -847,6 +963,9 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     return fail(c, HZ_ERR_ARG, "bad nsub / overlap / levels");
   if (op->restart < 1 || op->restart > 63) return fail(c, HZ_ERR_ARG, "restart must be in [1, 63]");
   if (op->precision != HZ_FP64 && op->precision != HZ_MIXED) return fail(c, HZ_ERR_ARG, "bad precision");
+  if (op->spmv_lanes != 0 && op->spmv_lanes != 2 && op->spmv_lanes != 4 && op->spmv_lanes != 8 &&
+      op->spmv_lanes != 16)
+    return fail(c, HZ_ERR_ARG, "spmv_lanes must be 0, 2, 4, 8 or 16");
   const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
   for (int64_t q = 0; q < ne * 4; q++)
     if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
@@ -964,42 +1083,19 @@ extern "C" hz_status hz_plan(const hz_mesh_desc* md, const hz_options* op, hz_st
   fill_stats(&tmp, P);
   tmp.stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // device bytes a context would hold after hz_factor (excluding transient fronts)
-  const int64_t vs = op->precision == HZ_FP64 ? 16 : 8;
-  int64_t b = 0;
-  b += P.A.pat.nnz() * (4 + 8 + 16 + 16 + 16) + (P.dofs.n + 1) * 8;
-  b += P.local.panel_elems * vs + (3 * P.local.voff.back() + P.local.u_elems) * vs;
-  b += P.coarse.panel_elems * 16;
-  b += int64_t(2 * op->restart + 8) * P.dofs.n * 16;
-  tmp.stats.device_bytes = b;
+  int64_t persistent = 0, transient = 0;
+  hz_engine::plan_bytes(P, *op, persistent, transient);
+  tmp.stats.device_bytes = persistent;
   *out = tmp.stats;
   return HZ_OK;
 }
 
-extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op, hz_ctx** outp) {
-  if (!outp) return HZ_ERR_ARG;
-  *outp = nullptr;
-  hz_ctx* c = new hz_ctx();
-  if (op) c->opt = *op;
-  auto t0 = std::chrono::steady_clock::now();
-  {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-      std::fprintf(stderr, "hz_setup_mesh: no CUDA device: %s\n", cudaGetErrorString(e));
-      delete c;
-      return HZ_ERR_CUDA;
-    }
-    c->device = dev;
-  }
-  hz::HostProblem P;
-  hz_status s = analyse(c, md, op, P);
-  if (s != HZ_OK) {
-    std::fprintf(stderr, "hz_setup_mesh: %s\n", c->err.c_str());
-    delete c;
-    return s;
-  }
+// Device side of a context from an analysed problem: operator, interpolation, factor
+// stores and Krylov workspaces.  The problem is left intact when copy_mesh is set
+// (a cached analysis reused by the serving layer), else its mesh is moved out.
+static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_options* op, bool copy_mesh) {
   c->st = reinterpret_cast<cudaStream_t>(op->stream);
-  c->order = md->order;
+  c->order = order;
   c->levels = op->levels;
   c->restart = op->restart;
   c->precision = op->precision;
@@ -1010,15 +1106,10 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
   c->nnzH = P.E.pat.nnz();
   c->zeta_nnz = P.Z.nnz();
   fill_stats(c, P);
-  auto bail = [&](hz_status st) {
-    std::fprintf(stderr, "hz_setup_mesh: %s\n", c->err.c_str());
-    hz_free(c);
-    return st;
-  };
 #define SETUP_TRY(expr)                      \
   do {                                       \
     hz_status s_ = (expr);                   \
-    if (s_ != HZ_OK) return bail(s_);        \
+    if (s_ != HZ_OK) return s_;              \
   } while (0)
   SETUP_TRY(upload(c, &c->d_rp, P.A.pat.ptr));
   SETUP_TRY(upload(c, &c->d_ci, P.A.pat.col));
@@ -1033,7 +1124,7 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     c->S = bs <= 1 ? 0 : (bs <= 4 ? 4 : (bs <= 8 ? 8 : 16));
     if (bs > 16) {
       c->err = "block_size must be at most 16";
-      return bail(HZ_ERR_ARG);
+      return HZ_ERR_ARG;
     }
   }
   SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max,
@@ -1096,22 +1187,55 @@ extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op,
     SETUP_TRY(dalloc(c, &c->csb, int64_t(S) * m));
     SETUP_TRY(dalloc(c, &c->scalb, int64_t(S) * 8));
     SETUP_TRY(dalloc(c, &c->brkb, int64_t(S)));
+    c->slots.assign(S, hz_ctx::Slot{});
   }
   // pinned scalars: 8 for the single-RHS loop, then 16 x 8 per-RHS scalars and 16 flags
-  if (cudaMallocHost((void**)&c->h_pin, (8 + 8 * 16 + 16) * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&c->h_pin, hz_ctx::PIN_TOTAL * sizeof(double)) != cudaSuccess) {
     c->err = "cudaMallocHost failed";
-    return bail(HZ_ERR_CUDA);
+    return HZ_ERR_CUDA;
   }
   if (cudaStreamSynchronize(c->st) != cudaSuccess) {
     c->err = "stream sync after upload failed";
-    return bail(HZ_ERR_CUDA);
+    return HZ_ERR_CUDA;
   }
-  c->mesh = std::move(P.mesh);
-  c->dofs = std::move(P.dofs);
+  if (copy_mesh) {
+    c->mesh = P.mesh;
+    c->dofs = P.dofs;
+  } else {
+    c->mesh = std::move(P.mesh);
+    c->dofs = std::move(P.dofs);
+  }
+  return HZ_OK;
+#undef SETUP_TRY
+}
+
+extern "C" hz_status hz_setup_mesh(const hz_mesh_desc* md, const hz_options* op, hz_ctx** outp) {
+  if (!outp) return HZ_ERR_ARG;
+  *outp = nullptr;
+  hz_ctx* c = new hz_ctx();
+  if (op) c->opt = *op;
+  auto t0 = std::chrono::steady_clock::now();
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      std::fprintf(stderr, "hz_setup_mesh: no CUDA device: %s\n", cudaGetErrorString(e));
+      delete c;
+      return HZ_ERR_CUDA;
+    }
+    c->device = dev;
+  }
+  hz::HostProblem P;
+  hz_status s = analyse(c, md, op, P);
+  if (s == HZ_OK) s = populate(c, P, md->order, op, false);
+  if (s != HZ_OK) {
+    std::fprintf(stderr, "hz_setup_mesh: %s\n", c->err.c_str());
+    hz_free(c);
+    return s;
+  }
   c->stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *outp = c;
   return HZ_OK;
-#undef SETUP_TRY
 }
 
 extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
@@ -1121,7 +1245,13 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
   c->factored = false;
   const double w = 2.0 * M_PI * freq_hz;
   hz::launch_fill_values(c->nnz, c->d_K, c->d_M, c->d_B, w, c->d_A, c->st);
-  if (c->spmv_lanes == 0) TRY(tune_spmv(c));
+  if (c->spmv_lanes == 0) {
+    const int fixed = c->opt.spmv_lanes;
+    if (fixed == 2 || fixed == 4 || fixed == 8 || fixed == 16)
+      c->spmv_lanes = fixed;
+    else
+      TRY(tune_spmv(c));
+  }
   hz::set_spmv_lanes(c->spmv_lanes);
   double minp = 1e300;
   TRY(factor_one(c, c->loc, w, c->loc_max, minp));
@@ -1162,20 +1292,7 @@ extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double t
   const int64_t n = c->n;
   hz_status worst = HZ_OK;
   if (c->S && nrhs > 1) {
-    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    std::vector<hz_rhs_info> inf(c->S);
-    for (int32_t j0 = 0; j0 < nrhs; j0 += c->S) {
-      const int nact = std::min<int>(c->S, nrhs - j0);
-      CU(cudaMemsetAsync(c->Bc, 0, size_t(c->S) * n * 16, c->st));
-      CU(cudaMemcpyAsync(c->Bc, (const double2*)rhs + int64_t(j0) * n, size_t(nact) * n * 16, kin, c->st));
-      TRY(fgmres_block(c, nact, tol, inf.data()));
-      CU(cudaMemcpyAsync((double2*)x + int64_t(j0) * n, c->Xc, size_t(nact) * n * 16, kout, c->st));
-      for (int i = 0; i < nact; i++) {
-        if (info) info[j0 + i] = inf[i];
-        if (inf[i].status != HZ_OK && worst == HZ_OK) worst = hz_status(inf[i].status);
-      }
-    }
+    TRY(solve_slots(c, (const double2*)rhs, nrhs, tol, (double2*)x, on_device != 0, info, worst));
     CU(cudaStreamSynchronize(c->st));
     return worst;
   }
@@ -1356,3 +1473,66 @@ extern "C" hz_status hz_cgs2(hz_ctx* c, const void* V, int64_t ldv, int32_t ncol
   *wnorm = std::sqrt(c->h_pin[5]);
   return HZ_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Internal interface for the serving layer (engine.h).
+// ---------------------------------------------------------------------------
+namespace hz_engine {
+
+hz_status analyse_problem(const hz_mesh_desc* md, const hz_options* op, hz::HostProblem& P, std::string& err) {
+  hz_ctx tmp;
+  if (op) tmp.opt = *op;
+  hz_status s = analyse(&tmp, md, op, P);
+  if (s != HZ_OK) err = tmp.err;
+  return s;
+}
+
+void plan_bytes(const hz::HostProblem& P, const hz_options& op, int64_t& persistent, int64_t& transient) {
+  const int64_t vs = op.precision == HZ_FP64 ? 16 : 8;
+  const int64_t n = P.dofs.n, m = op.restart;
+  const int bs = op.block_size;
+  const int64_t S = bs <= 1 ? 0 : (bs <= 4 ? 4 : (bs <= 8 ? 8 : 16));
+  int64_t b = 0;
+  b += P.A.pat.nnz() * (4 + 8 + 16 + 16 + 16) + (n + 1) * 8;                  // A pattern, K, M', B', A
+  b += P.local.panel_elems * vs + (3 * P.local.voff.back() + P.local.u_elems) * vs;
+  b += int64_t(P.local.rowlist.size()) * 4 + int64_t(P.local.cidx.size()) * 8 + int64_t(P.local.epos.size()) * 40;
+  b += P.coarse.panel_elems * 16;
+  if (!P.coarse.voff.empty())
+    b += (3 * P.coarse.voff.back() + P.coarse.u_elems) * 16 + int64_t(P.coarse.epos.size()) * 40;
+  b += (P.Z.nnz() + P.Zt.nnz()) * 12;
+  b += (2 * m + 8) * n * 16;                                                   // one-RHS Krylov
+  if (S) b += S * n * (2 * m + 9) * 16 + S * (P.local.voff.back() + P.local.u_elems) * 3 * vs;
+  persistent = b + b / 20 + (64 << 20);                                        // 5 % + 64 MB headroom
+  const int64_t tl = P.local.front_elems * vs, tc = P.coarse.front_elems * 16;
+  transient = std::max(tl, tc) + std::max(tl, tc) / 10;
+}
+
+hz_status create(const hz::HostProblem& P, int order, const hz_options* op, hz_ctx** out, std::string& err) {
+  *out = nullptr;
+  if (!op || op->block_size < 2) {
+    err = "serving contexts need block_size >= 2";
+    return HZ_ERR_ARG;
+  }
+  hz_ctx* c = new hz_ctx();
+  c->opt = *op;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    delete c;
+    return HZ_ERR_CUDA;
+  }
+  hz_status s = populate(c, const_cast<hz::HostProblem&>(P), order, op, true);
+  if (s != HZ_OK) {
+    err = c->err;
+    hz_free(c);
+    return s;
+  }
+  c->stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return HZ_OK;
+}
+
+int64_t device_bytes(const hz_ctx* c) { return c ? c->bytes : 0; }
+
+}  // namespace hz_engine

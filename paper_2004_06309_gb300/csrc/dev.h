@@ -90,6 +90,18 @@ struct FactorDev {
 };
 
 // Status word written by device code (pivot health).
+// Column offsets of the S slots of a pseudo-block solve (negative: empty slot).
+struct SlotCols {
+  int64_t o[16];
+};
+
+// One point source's right-hand side: at most 10 basis functions (P2 tetrahedron).
+struct PointRhs {
+  int64_t idx[10];
+  double val[10];
+  int cnt;
+};
+
 struct DevStatus {
   unsigned int zero_pivot;
   unsigned int timeout;          // a bounded wait on a tensor-core completion barrier ran out
@@ -112,10 +124,9 @@ void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream
 
 void launch_local_multi(const FactorDev& F, int S, const double2* src, const double2* y, double2* dst,
                         cudaStream_t st);
-void launch_interleave(int64_t n, int S, int active, const double2* cols, int64_t stride, double2* inter,
-                       cudaStream_t st);
-void launch_deinterleave(int64_t n, int S, int active, const double2* inter, double2* cols, int64_t stride,
-                         cudaStream_t st);
+void launch_interleave(int64_t n, int S, const SlotCols& off, const double2* base, double2* inter, cudaStream_t st);
+void launch_deinterleave(int64_t n, int S, const SlotCols& off, const double2* inter, double2* base, cudaStream_t st);
+void launch_point_rhs(const PointRhs& p, double2* out, cudaStream_t st);
 void launch_spmv_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                        const double2* sub, double2* y, cudaStream_t st);
 void launch_spmv_real_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double* val,

@@ -1101,29 +1101,41 @@ void launch_local_multi(const FactorDev& F, int S, const double2* src, const dou
 }
 
 // interleaved <-> per-right-hand-side column layouts
-__global__ void k_interleave(int64_t n, int S, int active, const double2* cols, int64_t stride, double2* inter) {
+// Interleaving of per-slot columns: slot i reads (or writes) base + off.o[i] + r; a
+// negative offset marks an empty slot, read as zero and never written.
+__global__ void k_interleave(int64_t n, int S, SlotCols off, const double2* base, double2* inter) {
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = e / S;
     const int i = int(e % S);
-    inter[e] = (i < active) ? cols[i * stride + r] : make_double2(0.0, 0.0);
+    const int64_t o = off.o[i];
+    inter[e] = (o >= 0) ? base[o + r] : make_double2(0.0, 0.0);
   }
 }
-__global__ void k_deinterleave(int64_t n, int S, int active, const double2* inter, double2* cols, int64_t stride) {
+__global__ void k_deinterleave(int64_t n, int S, SlotCols off, const double2* inter, double2* base) {
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * S; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = e / S;
     const int i = int(e % S);
-    if (i < active) cols[i * stride + r] = inter[e];
+    const int64_t o = off.o[i];
+    if (o >= 0) base[o + r] = inter[e];
   }
 }
-void launch_interleave(int64_t n, int S, int active, const double2* cols, int64_t stride, double2* inter,
-                       cudaStream_t st) {
+void launch_interleave(int64_t n, int S, const SlotCols& off, const double2* base, double2* inter, cudaStream_t st) {
   HZ_COUNT();
-  k_interleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, active, cols, stride, inter);
+  k_interleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, off, base, inter);
 }
-void launch_deinterleave(int64_t n, int S, int active, const double2* inter, double2* cols, int64_t stride,
-                         cudaStream_t st) {
+void launch_deinterleave(int64_t n, int S, const SlotCols& off, const double2* inter, double2* base, cudaStream_t st) {
   HZ_COUNT();
-  k_deinterleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, active, inter, cols, stride);
+  k_deinterleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, off, inter, base);
+}
+
+// Point-source right-hand side written into a zeroed column: out[idx[q]] += val[q].
+__global__ void k_point_rhs(PointRhs p, double2* out) {
+  if (threadIdx.x == 0)
+    for (int q = 0; q < p.cnt; q++) out[p.idx[q]].x += p.val[q];
+}
+void launch_point_rhs(const PointRhs& p, double2* out, cudaStream_t st) {
+  HZ_COUNT();
+  k_point_rhs<<<1, 32, 0, st>>>(p, out);
 }
 
 // Y = A X (or SUB - A X) for S interleaved vectors; lanes of a warp split the right-hand sides.

@@ -46,7 +46,7 @@ class Options(C.Structure):
         ("restart", C.c_int32), ("precision", C.c_int32), ("max_iter", C.c_int32),
         ("leaf_size", C.c_int32), ("max_snode", C.c_int32),
         ("hbm_budget", C.c_uint64), ("elem_part", C.c_void_p), ("stream", C.c_void_p),
-        ("block_size", C.c_int32),
+        ("block_size", C.c_int32), ("spmv_lanes", C.c_int32),
     ]
 
 
@@ -76,6 +76,32 @@ class Profile(C.Structure):
                 ("launches", C.c_int64 * 8)]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget", C.c_uint64), ("slots", C.c_int32), ("precision", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class RequestTimes(C.Structure):
+    _fields_ = [("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("latency_s", C.c_double), ("nsrc", C.c_int32), ("status", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("requests_done", C.c_int64), ("rhs_done", C.c_int64), ("p50_latency_s", C.c_double),
+        ("p99_latency_s", C.c_double), ("rhs_per_s", C.c_double), ("analyses", C.c_int64),
+        ("factorisations", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_int64),
+        ("peak_resident_bytes", C.c_int64), ("budget_bytes", C.c_int64), ("steps", C.c_int64),
+        ("factor_seconds", C.c_double), ("launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # Every exported symbol and its signature: (restype, argtypes).
 SIGNATURES = {
     "hz_setup_mesh": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(Options), C.POINTER(C.c_void_p)]),
@@ -96,6 +122,20 @@ SIGNATURES = {
     "hz_status_string": (C.c_char_p, [C.c_int]),
     "hz_last_error": (C.c_char_p, [C.c_void_p]),
     "hz_free": (None, [C.c_void_p]),
+    "hz_server_create": (C.c_int, [C.POINTER(ServerOptions), C.POINTER(C.c_void_p)]),
+    "hz_server_add_problem": (C.c_int, [C.c_void_p, C.POINTER(MeshDesc), C.POINTER(Options), C.c_double,
+                                        C.POINTER(C.c_int32)]),
+    "hz_server_submit": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_double,
+                                   C.POINTER(C.c_uint64)]),
+    "hz_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(RequestTimes)]),
+    "hz_server_collect": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(RhsInfo),
+                                    C.POINTER(RequestTimes)]),
+    "hz_server_ndofs": (C.c_int64, [C.c_void_p, C.c_int32]),
+    "hz_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "hz_server_last_error": (C.c_char_p, [C.c_void_p]),
+    "hz_server_free": (None, [C.c_void_p]),
+    "hz_select_evictions": (C.c_int32, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                                        C.c_int64, C.c_void_p]),
 }
 
 
@@ -164,7 +204,7 @@ class _MeshArrays:
 
 
 def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=2000, leaf_size=0,
-                 max_snode=0, hbm_budget=0, elem_part=None, stream=0, block_size=0):
+                 max_snode=0, hbm_budget=0, elem_part=None, stream=0, block_size=0, spmv_lanes=0):
     o = Options()
     o.nsub, o.overlap, o.levels, o.restart = int(nsub), int(overlap), int(levels), int(restart)
     o.precision, o.max_iter = int(precision), int(max_iter)
@@ -174,6 +214,7 @@ def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=200
     o.elem_part = _ptr(part)
     o.stream = int(stream) if stream else None
     o.block_size = int(block_size)
+    o.spmv_lanes = int(spmv_lanes)
     return o, part
 
 
@@ -305,3 +346,91 @@ class Solver:
         z = self.torch.empty_like(v)
         self._check(lib().hz_apply_M(self.h, C.c_void_p(v.data_ptr()), C.c_void_p(z.data_ptr())), "hz_apply_M")
         return z
+
+
+def select_evictions(bytes_, last_use, evictable, resident, need, budget):
+    """The server's admission rule (hz_select_evictions): indices to evict, or None."""
+    b = _c(bytes_, np.int64)
+    lu = _c(last_use, np.float64)
+    ev = _c(evictable, np.int32)
+    out = np.zeros(max(len(b), 1), np.int32)
+    k = lib().hz_select_evictions(len(b), _ptr(b), _ptr(lu), _ptr(ev), int(resident), int(need), int(budget),
+                                  _ptr(out))
+    return None if k < 0 else [int(i) for i in out[:k]]
+
+
+class Server:
+    """Continuous-batching solve server over cached per-(mesh, frequency) factors.
+
+    ``add_problem`` registers a ``synth`` problem (its mesh, options and frequency);
+    ``submit`` queues point sources and returns a request id at once; ``wait`` returns
+    ``(X (n, nsrc), [(iterations, status, rel_residual)], times)``.  Both native threads
+    (loader, solver) run inside libhz.so."""
+
+    def __init__(self, slots=8, precision=HZ_MIXED, hbm_budget=0, device=0):
+        o = ServerOptions()
+        o.hbm_budget, o.slots, o.precision, o.device = int(hbm_budget), int(slots), int(precision), int(device)
+        h = C.c_void_p()
+        s = lib().hz_server_create(C.byref(o), C.byref(h))
+        if s != HZ_OK:
+            raise HzError(s, "hz_server_create failed: " + lib().hz_status_string(s).decode())
+        self.h = h
+        self.problems = []
+
+    def add_problem(self, problem, freq=None, use_partition=True, **kw):
+        ma = _problem_args(problem)
+        o, part = make_options(problem.nsub, problem.overlap, problem.levels, problem.restart,
+                               elem_part=problem.elem_part if use_partition else None, **kw)
+        pid = C.c_int32()
+        freq = problem.freq if freq is None else freq
+        s = lib().hz_server_add_problem(self.h, C.byref(ma.desc), C.byref(o), float(freq), C.byref(pid))
+        if s != HZ_OK:
+            raise HzError(s, "hz_server_add_problem failed")
+        self.problems.append(problem)
+        return pid.value
+
+    def submit(self, pid, pts, tol=1e-6):
+        pts = _c(np.atleast_2d(pts), np.float64).reshape(-1, 3)
+        rid = C.c_uint64()
+        s = lib().hz_server_submit(self.h, int(pid), _ptr(pts), len(pts), float(tol), C.byref(rid))
+        if s != HZ_OK:
+            raise HzError(s, "hz_server_submit failed")
+        return rid.value, len(pts), int(pid)
+
+    def wait(self, req, timeout=0.0):
+        """Blocks until the request finishes; returns (X (n, nsrc), info, times)."""
+        rid, nsrc, pid = req
+        times = RequestTimes()
+        s = lib().hz_server_wait(self.h, rid, float(timeout), C.byref(times))
+        if s != HZ_OK:
+            raise HzError(s, "hz_server_wait: " + lib().hz_status_string(s).decode())
+        n = self.ndofs(pid)
+        X = np.zeros((nsrc, max(n, 0)), np.complex128)
+        info = (RhsInfo * max(nsrc, 1))()
+        lib().hz_server_collect(self.h, rid, _ptr(X) if n > 0 else None, info, C.byref(times))
+        inf = [(info[j].iterations, info[j].status, info[j].rel_residual) for j in range(nsrc)]
+        return X.T, inf, times.as_dict()
+
+    def ndofs(self, pid):
+        return int(lib().hz_server_ndofs(self.h, int(pid)))
+
+    def stats(self):
+        st = ServerStats()
+        s = lib().hz_server_get_stats(self.h, C.byref(st))
+        if s != HZ_OK:
+            raise HzError(s, "hz_server_get_stats failed")
+        return st.as_dict()
+
+    def last_error(self):
+        return lib().hz_server_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hz_server_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

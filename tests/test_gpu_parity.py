@@ -206,13 +206,13 @@ def test_graph_path_matches_eager_path(hzmod):
     p = synth.small_overthrust(levels=2, cells=(4, 4, 2), freq=0.5, nsub=8)
     S = OracleSolver(p)
     b = S.rhs()[:, 0]
-    G0 = hzmod.Solver(p)
+    G0 = hzmod.Solver(p, spmv_lanes=4)          # same SpMV summation order in both contexts
     G0.factor()
     x0, i0 = G0.solve(b)
     G0.close()
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        G1 = hzmod.Solver(p, stream=s)
+        G1 = hzmod.Solver(p, stream=s, spmv_lanes=4)
         G1.factor()
         x1, i1 = G1.solve(b)
         x2, i2 = G1.solve(b)           # second solve replays the captured graphs
