@@ -19,8 +19,9 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
-from . import fem
+from . import dd, fem, krylov
 
 
 def interpolation(problem, dm):
@@ -61,3 +62,83 @@ def coarse_operator(Z, A):
     E = (Z.T @ A @ Z).tocsr()
     E.sort_indices()
     return E
+
+
+# ---------------------------------------------------------------------------
+# The paper's coarse solve: E y = r_H by GMRES preconditioned with one-level
+# ORAS on Gamma_H, with the same spatial partition as the fine level.
+#
+# Readings (the paper gives the method in one sentence):
+# * coarse partition: a coarse element belongs to the part that holds most of
+#   its fine children (ties: the lowest part id);
+# * coarse overlap and partition of unity: the fine recipe applied to Gamma_H
+#   (delta layers of coarse elements, chi = 1 - l/delta), restricted to the free
+#   coarse dofs;
+# * local coarse operators: E_i = Z_i^T A_i^h Z_i, the Galerkin projection of the
+#   fine Robin problem on the fine elements inside Gamma_H,i (absorbing faces on
+#   its artificial interfaces, global conditions elsewhere), so that E_i uses the
+#   same fine coefficients as E = Z^T A Z;
+# * inner GMRES: x0 = 0, right preconditioning, CGS2 and the Givens rotations of
+#   the outer solve, one cycle of at most m_H iterations ending when the estimate
+#   |g_{j+1}| / ||r_H|| <= tol_H (no restart, no true-residual check).  The coarse
+#   correction is then not a fixed linear map, hence the flexible outer GMRES.
+# ---------------------------------------------------------------------------
+def coarse_partition(problem):
+    """Part of every coarse element: the majority part of its fine children."""
+    neH = problem.coarse.tets.shape[0]
+    counts = np.zeros((neH, problem.nsub), np.int64)
+    np.add.at(counts, (problem.fine_parent, problem.elem_part), 1)
+    return np.argmax(counts, axis=1)
+
+
+class _Region:
+    def __init__(self, elems):
+        self.elems = elems
+
+
+class CoarseORAS:
+    """One-level ORAS on the coarse mesh (Eq. 4 with Gamma_H, E_i, D_H,i) and the
+    GMRES solve of E it preconditions."""
+
+    def __init__(self, problem, dm, Z, cdm, keep):
+        self.p = problem
+        self.dm = dm
+        self.Z = Z.tocsc()
+        cm = problem.coarse
+        self.part = coarse_partition(problem)
+        subs = dd.grow_subdomains(cm, self.part, problem.nsub, problem.overlap, cdm)
+        newid = np.full(cdm.n, -1, np.int64)
+        newid[keep] = np.arange(len(keep))
+        self.dofs, self.D, self.regions = [], [], []
+        for s in subs:
+            k = newid[s.dofs]
+            m = k >= 0
+            self.dofs.append(k[m])
+            self.D.append(s.D[m])
+            self.regions.append(np.nonzero(np.isin(problem.fine_parent, s.elems))[0])
+        self.nH = len(keep)
+
+    def factor(self, freq):
+        w = 2.0 * np.pi * freq
+        self.E_loc, self.lu = [], []
+        for dofs, reg in zip(self.dofs, self.regions):
+            K, Mp, Bp = dd.local_parts(self.p.mesh, self.p.c, self.p.order, self.dm, _Region(reg))
+            Ah = (K.astype(np.complex128) - (w * w) * Mp - (1j * w) * Bp).tocsr()
+            Zi = self.Z[:, dofs]
+            Ei = (Zi.T @ Ah @ Zi).tocsc()
+            Ei.sort_indices()
+            self.E_loc.append(Ei)
+            self.lu.append(spla.splu(Ei))
+
+    def apply(self, r):
+        """M_{1,H}^{-1} r = sum_i R_H,i^T D_H,i E_i^{-1} R_H,i r."""
+        z = np.zeros(self.nH, np.complex128)
+        for dofs, D, lu in zip(self.dofs, self.D, self.lu):
+            z[dofs] += D * lu.solve(r[dofs])
+        return z
+
+    def solve(self, E, r, tol, m):
+        """y ~ E^{-1} r by the inner GMRES; returns (y, inner iterations)."""
+        y, its, est, ok = krylov.fgmres(lambda v: E @ v, self.apply, r, tol=tol, m=m, maxit=m,
+                                        verify=False)
+        return y, its

@@ -34,8 +34,12 @@ def givens(a, b):
     return aa / rho, (a / aa) * np.conj(b) / rho
 
 
-def fgmres(apply_A, apply_M, b, tol=1e-6, m=30, maxit=1000, history=None):
-    """Solve A x = b.  Returns (x, iterations, true relative residual, converged)."""
+def fgmres(apply_A, apply_M, b, tol=1e-6, m=30, maxit=1000, history=None, verify=True):
+    """Solve A x = b.  Returns (x, iterations, true relative residual, converged).
+
+    ``verify=False`` (an inner solve) ends at the first cycle end -- the Givens
+    estimate crossing tol, a happy breakdown or ``maxit`` -- without forming the
+    true residual, and returns the estimate in its place."""
     b = np.asarray(b, np.complex128)
     n = b.shape[0]
     bnorm = np.linalg.norm(b)
@@ -90,6 +94,8 @@ def fgmres(apply_A, apply_M, b, tol=1e-6, m=30, maxit=1000, history=None):
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1: k] @ y[i + 1: k]) / H[i, i]
         x = x + Zs[:, :k] @ y
+        if not verify:
+            return x, its, est, est <= tol
         r = b - apply_A(x)
         rel = np.linalg.norm(r) / bnorm
         if rel <= tol:

@@ -18,9 +18,17 @@ from . import coarse, dd, fem, krylov
 
 
 class OracleSolver:
-    def __init__(self, problem, robin=True):
+    """``coarse_solver="direct"`` solves E by a sparse direct solver; ``"oras"`` by the
+    paper's inner GMRES with one-level ORAS on the coarse mesh (tolerance
+    ``coarse_tol``, at most ``coarse_m`` iterations)."""
+
+    def __init__(self, problem, robin=True, coarse_solver="direct", coarse_tol=1e-2, coarse_m=30):
         self.p = problem
         self.robin = robin
+        self.coarse_solver = coarse_solver
+        self.coarse_tol = coarse_tol
+        self.coarse_m = coarse_m
+        self.coarse_its = []
         self.A, self.dm, self.ddofs = fem.global_system(problem)
         self.n = self.dm.n
         self.subs = dd.grow_subdomains(problem.mesh, problem.elem_part, problem.nsub,
@@ -28,6 +36,8 @@ class OracleSolver:
         self.Z = None
         if problem.levels == 2:
             self.Z, self.cdm, self.ckeep = coarse.interpolation(problem, self.dm)
+            if coarse_solver == "oras":
+                self.cor = coarse.CoarseORAS(problem, self.dm, self.Z, self.cdm, self.ckeep)
         self.freq = None
 
     def factor(self, freq=None):
@@ -39,7 +49,10 @@ class OracleSolver:
         self.lu = [spla.splu(s.A.tocsc()) for s in self.subs]
         if self.Z is not None:
             self.E = coarse.coarse_operator(self.Z, self.A)
-            self.Elu = spla.splu(self.E.tocsc())
+            if self.coarse_solver == "oras":
+                self.cor.factor(freq)
+            else:
+                self.Elu = spla.splu(self.E.tocsc())
         self.freq = freq
 
     # --- operators -------------------------------------------------------
@@ -54,7 +67,12 @@ class OracleSolver:
         return z
 
     def coarse_correction(self, v):
-        return self.Z @ self.Elu.solve(self.Z.T @ v)
+        rH = self.Z.T @ v
+        if self.coarse_solver == "oras":
+            yH, its = self.cor.solve(self.E, rH, self.coarse_tol, self.coarse_m)
+            self.coarse_its.append(its)
+            return self.Z @ yH
+        return self.Z @ self.Elu.solve(rH)
 
     def apply_M(self, v):
         if self.Z is None:
