@@ -361,6 +361,10 @@ def main():
                     help="right-hand sides per step (sources from the 16 x 8 surface grid at 50 m depth)")
     ap.add_argument("--leaf", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--maxsn", type=int, default=0, help="widest supernode (0: library default)")
+    ap.add_argument("--coarse", default="direct", choices=["direct", "oras"],
+                    help="coarse solve: direct LDL^T of E, or inner GMRES with coarse one-level ORAS")
+    ap.add_argument("--coarse-tol", type=float, default=0.0, help="inner coarse tolerance (0: library default)")
+    ap.add_argument("--coarse-maxit", type=int, default=0, help="inner coarse iterations at most (0: default)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -434,7 +438,9 @@ def main():
     torch.cuda.set_stream(stream)
     for pname in precs:
         G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream,
-                      leaf_size=args.leaf, max_snode=args.maxsn, block_size=args.block)
+                      leaf_size=args.leaf, max_snode=args.maxsn, block_size=args.block,
+                      coarse_solver=hz.HZ_COARSE_ORAS if args.coarse == "oras" else hz.HZ_COARSE_DIRECT,
+                      coarse_tol=args.coarse_tol, coarse_maxit=args.coarse_maxit)
         tf = time.time()
         G.factor()
         torch.cuda.synchronize()
@@ -526,6 +532,7 @@ def main():
         "config": {"workload": args.workload, "n_dofs": n, "nsub": prob.nsub, "overlap": prob.overlap,
                    "levels": 2 if prob.levels == 2 else 1, "restart": prob.restart, "tol": 1e-6,
                    "rhs_per_step": args.nrhs, "block_size": args.block, "freq_hz": prob.freq,
+                   "coarse_solver": args.coarse,
                    "l2": "inputs larger than L2 (factors >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "iterations": R["iterations"][-1], "rel_residual": R["rel"],
@@ -539,7 +546,7 @@ def main():
         "phases_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
         "stats": {k: R["stats"][k] for k in ("nnz", "n_coarse", "sum_ni", "nnz_factor", "nnz_factor_coarse",
                                              "nsupernodes", "nlevels", "front_bytes", "device_bytes",
-                                             "setup_seconds")},
+                                             "setup_seconds", "coarse_solves", "coarse_iterations")},
         "generate_seconds": t_gen,
     }
     if "fp64" in results and main_p != "fp64":

@@ -52,6 +52,7 @@ typedef enum {
 
 enum { HZ_TAG_DIRICHLET = 0, HZ_TAG_ABC = 1 };
 enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+enum { HZ_COARSE_DIRECT = 0, HZ_COARSE_ORAS = 1 };
 
 /* Mesh (Eq. 1-2).  All arrays are host pointers, read during hz_setup_mesh only. */
 typedef struct {
@@ -101,6 +102,20 @@ typedef struct {
                                matrix); 2, 4, 8 or 16 = fixed.  The choice sets the
                                summation order, so contexts that must agree bitwise
                                fix it.                                                */
+  int32_t coarse_solver;    /* two levels: how E y_H = r_H is solved.
+                               HZ_COARSE_DIRECT: sparse LDL^T of E in FP64 (a direct
+                               solve); HZ_COARSE_ORAS: the method section's scheme --
+                               GMRES on E right-preconditioned by one-level ORAS on the
+                               coarse mesh with the fine partition carried over (local
+                               E_i factored in the precision of the subdomain factors),
+                               one cycle of at most coarse_maxit iterations ending when
+                               the residual estimate reaches coarse_tol.  The coarse
+                               correction is then inexact and not linear, which the
+                               flexible outer GMRES allows.                          */
+  int32_t coarse_maxit;     /* HZ_COARSE_ORAS: at most this many inner iterations,
+                               1..63 (0: 30)                                          */
+  double coarse_tol;        /* HZ_COARSE_ORAS: inner relative residual estimate
+                               (0: 1e-2)                                              */
 } hz_options;
 
 typedef struct {
@@ -128,6 +143,8 @@ typedef struct {
   double factor_seconds;    /* wall time of the last hz_factor                        */
   double min_pivot;         /* min |d_j| over all local factors (last hz_factor)     */
   int64_t launches;         /* kernel launches issued by the library in this process */
+  int64_t coarse_solves;    /* iterative coarse solve: inner solves since hz_factor    */
+  int64_t coarse_iterations;/* ... and their inner GMRES iterations in total           */
 } hz_stats;
 
 /* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */

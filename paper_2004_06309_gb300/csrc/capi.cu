@@ -40,6 +40,18 @@ struct hz_ctx {
   double *d_Zv = nullptr, *d_Ztv = nullptr;
   hz::FactorDev loc, crs;
   double loc_max[3] = {0, 0, 0}, crs_max[3] = {0, 0, 0};
+  // iterative coarse solve: E in CSR, local coarse factors, inner GMRES workspace
+  int coarse_oras = 0, cmaxit = 30;
+  double ctol = 1e-2;
+  hz::FactorDev cloc;
+  double cloc_max[3] = {0, 0, 0};
+  int64_t* d_Erp = nullptr;
+  int32_t* d_Eci = nullptr;
+  double* d_EK = nullptr;
+  double2 *d_EM = nullptr, *d_EB = nullptr, *d_E = nullptr;
+  double2 *VH = nullptr, *ZH = nullptr, *wH = nullptr, *HH = nullptr, *snH = nullptr, *gH = nullptr, *yHs = nullptr;
+  double *csH = nullptr, *scalH = nullptr;
+  int* brkH = nullptr;
   // Krylov workspace
   double2 *V = nullptr, *Zs = nullptr, *w = nullptr, *b = nullptr, *x = nullptr, *y = nullptr, *t = nullptr;
   double2 *rH = nullptr, *yH = nullptr;
@@ -75,7 +87,13 @@ struct hz_ctx {
   };
   std::vector<Slot> slots;
   // pinned host scalars: [0, 8) single-RHS loop, then per-slot scalars, flags and |b|
-  enum { PIN_SLOT = 8, PIN_FLAGS = 8 + 8 * 16, PIN_BNORM = 8 + 8 * 16 + 16, PIN_TOTAL = 8 + 8 * 16 + 32 };
+  enum {
+    PIN_SLOT = 8,
+    PIN_FLAGS = 8 + 8 * 16,
+    PIN_BNORM = 8 + 8 * 16 + 16,
+    PIN_CRS = 8 + 8 * 16 + 32,        // inner coarse solve: |r_H|^2, estimate, breakdown flag
+    PIN_TOTAL = 8 + 8 * 16 + 36
+  };
   std::vector<void*> allocs;
   std::vector<size_t> sizes;
   int64_t bytes = 0;
@@ -463,14 +481,76 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
   return HZ_OK;
 }
 
+// y ~ E^{-1} r (iterative coarse solve): one cycle of GMRES(coarse_maxit) on E
+// right-preconditioned by one-level ORAS on the coarse mesh (Eq. 4 with the coarse
+// subdomains), CGS2 and the Givens rotations of the outer solve, x0 = 0, ending when
+// the estimate |g_{j+1}| / ||r|| reaches coarse_tol, on a happy breakdown or after
+// coarse_maxit iterations.  Host-synchronous: one pinned read per inner iteration.
+// r is not modified; a zero r gives y = 0.
+void coarse_inner(hz_ctx* c, const double2* r, double2* y) {
+  const int64_t nH = c->nH;
+  const int mH = c->cmaxit;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  double* pin = c->h_pin + hz_ctx::PIN_CRS;
+  hz::launch_cgs(nH, 0, c->VH, nH, nullptr, const_cast<double2*>(r), 0, c->partial, st);
+  hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+  cudaMemsetAsync(y, 0, size_t(nH) * 16, st);
+  cudaMemcpyAsync(pin, &c->nrm[64].x, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (!(pin[0] > 0.0) || !std::isfinite(pin[0])) {
+    c->stats.coarse_solves++;
+    return;
+  }
+  hz::launch_init_cycle(c->nrm, c->gH, mH, c->scalH + 2, c->scalH + 3, st);
+  hz::launch_scale(nH, r, c->scalH + 2, c->VH, st);
+  int k = 0;
+  for (int j = 0; j < mH; j++) {
+    double2* vj = c->VH + int64_t(j) * nH;
+    double2* zj = c->ZH + int64_t(j) * nH;
+    hz::launch_gather(c->cloc, vj, st);                                           // R_H,i v
+    hz::launch_solve(c->cloc, st);                                                // E_i^{-1}
+    hz::launch_prolong(c->cloc, nullptr, zj, st);                                 // sum R^T D x_i
+    hz::launch_spmv(nH, c->d_Erp, c->d_Eci, c->d_E, zj, nullptr, c->wH, st);      // E z_j
+    hz::launch_cgs(nH, j + 1, c->VH, nH, nullptr, c->wH, j + 1, c->partial, st);
+    hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
+    hz::launch_cgs(nH, j + 1, c->VH, nH, c->h1, c->wH, j + 1, c->partial, st);
+    hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
+    hz::launch_cgs(nH, j + 1, c->VH, nH, c->h2, c->wH, 0, c->partial, st);
+    hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+    hz::launch_givens(j, mH, c->HH, c->csH, c->snH, c->gH, c->h1, c->h2, c->nrm, c->scalH + 3, c->scalH, c->brkH,
+                      c->scalH + 1, st);
+    hz::launch_scale(nH, c->wH, c->scalH + 1, c->VH + int64_t(j + 1) * nH, st);
+    cudaMemcpyAsync(pin + 1, c->scalH, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(pin + 2, c->brkH, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    k = j + 1;
+    int brk = 0;
+    std::memcpy(&brk, pin + 2, sizeof(int));
+    if (brk || !(pin[1] > c->ctol)) break;
+  }
+  hz::launch_update_x(nH, k, c->HH, mH + 1, c->gH, c->yHs, c->ZH, nH, y, st);
+  c->stats.coarse_solves++;
+  c->stats.coarse_iterations += k;
+}
+
+// y_H = E^{-1} r_H on the coarse factor (direct) or by the inner GMRES (iterative).
+void coarse_solve(hz_ctx* c, const double2* r, double2* y) {
+  if (c->coarse_oras) {
+    coarse_inner(c, r, y);
+    return;
+  }
+  hz::launch_gather(c->crs, r, c->st);
+  hz::launch_solve(c->crs, c->st);
+  hz::launch_prolong(c->crs, nullptr, y, c->st);
+}
+
 // z = M^{-1} v  (Eq. 3 with two levels, Eq. 4 with one)
 void apply_prec(hz_ctx* c, const double2* v, double2* z) {
   cudaStream_t st = c->st;
   if (c->levels == 2) {
     hz::launch_spmv_real(c->nH, c->d_Ztrp, c->d_Ztci, c->d_Ztv, v, c->rH, st);   // r_H = Z^T v
-    hz::launch_gather(c->crs, c->rH, st);
-    hz::launch_solve(c->crs, st);                                                // E^{-1}
-    hz::launch_prolong(c->crs, nullptr, c->yH, st);
+    coarse_solve(c, c->rH, c->yH);                                               // E^{-1}
     hz::launch_spmv_real(c->n, c->d_Zrp, c->d_Zci, c->d_Zv, c->yH, c->y, st);     // y = Z y_H
     hz::launch_spmv(c->n, c->d_rp, c->d_ci, c->d_A, c->y, v, c->t, st);          // t = v - A y
     hz::launch_gather(c->loc, c->t, st);                                         // R_i t
@@ -631,7 +711,20 @@ void apply_prec_multi(hz_ctx* c, const double2* X, double2* Y) {
   cudaStream_t st = c->st;
   if (c->levels == 2) {
     hz::launch_spmv_real_multi(c->nH, S, c->d_Ztrp, c->d_Ztci, c->d_Ztv, X, c->rHi, st);   // Z^T v
-    hz::launch_local_multi(c->crs, S, c->rHi, nullptr, c->yHi, st);                       // E^{-1}
+    if (c->coarse_oras) {                                                                 // E^{-1}
+      // one inner solve per running slot (each right-hand side has its own coarse problem)
+      cudaMemsetAsync(c->yHi, 0, size_t(S) * c->nH * 16, st);
+      for (int i = 0; i < S; i++) {
+        if (c->slots[i].state != hz_ctx::SLOT_RUN) continue;
+        hz::SlotCols one;
+        for (int q = 0; q < 16; q++) one.o[q] = q == i ? 0 : -1;
+        hz::launch_deinterleave(c->nH, S, one, c->rHi, c->rH, st);
+        coarse_inner(c, c->rH, c->yH);
+        hz::launch_interleave_put(c->nH, S, i, c->yH, c->yHi, st);
+      }
+    } else {
+      hz::launch_local_multi(c->crs, S, c->rHi, nullptr, c->yHi, st);
+    }
     hz::launch_spmv_real_multi(c->n, S, c->d_Zrp, c->d_Zci, c->d_Zv, c->yHi, c->yi, st);  // y = Z y_H
     hz::launch_spmv_multi(c->n, S, c->d_rp, c->d_ci, c->d_A, c->yi, X, c->Ti, st);         // t = v - A y
     hz::launch_local_multi(c->loc, S, c->Ti, c->yi, Y, st);                               // y + M_1^{-1} t
@@ -940,6 +1033,7 @@ void hz_free(hz_ctx* c) {
   if (c->h_pin) cudaFreeHost(c->h_pin);
   free_host_ptrs(c->loc);
   free_host_ptrs(c->crs);
+  free_host_ptrs(c->cloc);
   delete c;
 }
 
@@ -966,6 +1060,10 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
   if (op->spmv_lanes != 0 && op->spmv_lanes != 2 && op->spmv_lanes != 4 && op->spmv_lanes != 8 &&
       op->spmv_lanes != 16)
     return fail(c, HZ_ERR_ARG, "spmv_lanes must be 0, 2, 4, 8 or 16");
+  if (op->coarse_solver != HZ_COARSE_DIRECT && op->coarse_solver != HZ_COARSE_ORAS)
+    return fail(c, HZ_ERR_ARG, "bad coarse_solver");
+  if (op->coarse_maxit < 0 || op->coarse_maxit > 63 || !(op->coarse_tol >= 0.0))
+    return fail(c, HZ_ERR_ARG, "coarse_maxit must be in [0, 63] and coarse_tol >= 0");
   const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
   for (int64_t q = 0; q < ne * 4; q++)
     if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
@@ -1032,7 +1130,26 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     hz::symbolic_batch(mats, leaf, maxsn, P.local);
   }
   phase("local symbolic", tp);
-  if (op->levels == 2) {
+  if (op->levels == 2 && op->coarse_solver == HZ_COARSE_ORAS) {
+    hz::build_coarse(P, true);
+    phase("coarse space", tp);
+    hz::build_coarse_subdomains(P, part, op->nsub, op->overlap);
+    phase("coarse subdomains + E_i", tp);
+    std::vector<hz::MatrixInput> mats(op->nsub);
+    std::vector<std::vector<double>> coords(op->nsub);
+    for (int i = 0; i < op->nsub; i++) {
+      const hz::Subdomain& S = P.csubs[i];
+      coords[i].resize(S.dofs.size() * 3);
+      for (size_t k = 0; k < S.dofs.size(); k++)
+        for (int a = 0; a < 3; a++) coords[i][3 * k + a] = P.cdofs.coord[3 * S.dofs[k] + a];
+      mats[i].A = &S.A;
+      mats[i].coord = coords[i].data();
+      mats[i].gidx = P.cgidx[i].data();
+      mats[i].weight = S.D.data();
+    }
+    hz::symbolic_batch(mats, leaf, maxsn, P.clocal);
+    phase("coarse local symbolic", tp);
+  } else if (op->levels == 2) {
     hz::build_coarse(P);
     std::vector<double> coords(P.nH * 3);
     std::vector<int64_t> gid(P.nH);
@@ -1060,12 +1177,13 @@ static void fill_stats(hz_ctx* c, const hz::HostProblem& P) {
   for (const auto& S : P.subs) nl += S.A.pat.nnz();
   s.nnz_local = nl;
   s.nnz_factor = P.local.panel_elems;
-  s.nnz_factor_coarse = P.coarse.panel_elems;
+  const bool it = !P.clocal.voff.empty();           // iterative coarse solve
+  s.nnz_factor_coarse = it ? P.clocal.panel_elems : P.coarse.panel_elems;
   s.nsupernodes = int64_t(P.local.sn_k.size());
   s.nlevels = P.local.nlev;
-  s.nlevels_coarse = P.coarse.nlev;
+  s.nlevels_coarse = it ? P.clocal.nlev : P.coarse.nlev;
   const int64_t vs = c->opt.precision == HZ_FP64 ? 16 : 8;
-  s.front_bytes = std::max(P.local.front_elems * vs, P.coarse.front_elems * 16);
+  s.front_bytes = std::max({P.local.front_elems * vs, P.coarse.front_elems * 16, P.clocal.front_elems * vs});
   s.factor_flops = P.local.flops;
 }
 
@@ -1136,7 +1254,32 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
     SETUP_TRY(upload(c, &c->d_Ztrp, P.Zt.ptr));
     SETUP_TRY(upload(c, &c->d_Ztci, P.Zt.col));
     SETUP_TRY(upload(c, &c->d_Ztv, P.Ztv));
-    SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S));
+    if (op->coarse_solver == HZ_COARSE_ORAS) {
+      c->coarse_oras = 1;
+      c->cmaxit = op->coarse_maxit > 0 ? op->coarse_maxit : 30;
+      c->ctol = op->coarse_tol > 0.0 ? op->coarse_tol : 1e-2;
+      SETUP_TRY(upload_factor(c, P.clocal, op->precision == HZ_MIXED ? 1 : 0, c->nH, c->cloc, c->cloc_max,
+                              op->precision == HZ_MIXED ? 512 : 256, 0));
+      SETUP_TRY(upload(c, &c->d_Erp, P.E.pat.ptr));
+      SETUP_TRY(upload(c, &c->d_Eci, P.E.pat.col));
+      SETUP_TRY(upload(c, &c->d_EK, P.E.K));
+      SETUP_TRY(upload(c, &c->d_EM, to_d2(P.E.M)));
+      SETUP_TRY(upload(c, &c->d_EB, to_d2(P.E.B)));
+      SETUP_TRY(dalloc(c, &c->d_E, c->nnzH));
+      const int mH = c->cmaxit;
+      SETUP_TRY(dalloc(c, &c->VH, c->nH * (mH + 1)));
+      SETUP_TRY(dalloc(c, &c->ZH, c->nH * mH));
+      SETUP_TRY(dalloc(c, &c->wH, c->nH));
+      SETUP_TRY(dalloc(c, &c->HH, int64_t(mH + 1) * mH));
+      SETUP_TRY(dalloc(c, &c->snH, mH));
+      SETUP_TRY(dalloc(c, &c->gH, mH + 1));
+      SETUP_TRY(dalloc(c, &c->yHs, mH));
+      SETUP_TRY(dalloc(c, &c->csH, mH));
+      SETUP_TRY(dalloc(c, &c->scalH, 8));
+      SETUP_TRY(dalloc(c, &c->brkH, 1));
+    } else {
+      SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S));
+    }
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));
   }
@@ -1161,7 +1304,8 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
   SETUP_TRY(dalloc(c, &c->scal, 8));
   c->gexec.assign(m, nullptr);
   c->gcount.assign(m, 0);
-  c->graphs = std::getenv("HZ_NO_GRAPHS") == nullptr;
+  // the iterative coarse solve waits on the host inside each preconditioner application
+  c->graphs = std::getenv("HZ_NO_GRAPHS") == nullptr && !c->coarse_oras;
   SETUP_TRY(dalloc(c, &c->brk, 1));
   SETUP_TRY(dalloc(c, &c->status, 1));
   if (c->S) {
@@ -1255,7 +1399,13 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
   hz::set_spmv_lanes(c->spmv_lanes);
   double minp = 1e300;
   TRY(factor_one(c, c->loc, w, c->loc_max, minp));
-  if (c->levels == 2) TRY(factor_one(c, c->crs, w, c->crs_max, minp));
+  if (c->levels == 2 && c->coarse_oras) {
+    hz::launch_fill_values(c->nnzH, c->d_EK, c->d_EM, c->d_EB, w, c->d_E, c->st);
+    TRY(factor_one(c, c->cloc, w, c->cloc_max, minp));
+    c->stats.coarse_solves = c->stats.coarse_iterations = 0;
+  } else if (c->levels == 2) {
+    TRY(factor_one(c, c->crs, w, c->crs_max, minp));
+  }
   CU(cudaStreamSynchronize(c->st));
   c->stats.min_pivot = minp;
   c->stats.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1364,9 +1514,7 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
       case HZ_PH_COARSE:
         if (c->levels == 2) {
           hz::launch_spmv_real(c->nH, c->d_Ztrp, c->d_Ztci, c->d_Ztv, c->b, c->rH, st);
-          hz::launch_gather(c->crs, c->rH, st);
-          hz::launch_solve(c->crs, st);
-          hz::launch_prolong(c->crs, nullptr, c->yH, st);
+          coarse_solve(c, c->rH, c->yH);
           hz::launch_spmv_real(n, c->d_Zrp, c->d_Zci, c->d_Zv, c->yH, c->y, st);
         }
         break;
@@ -1402,9 +1550,11 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
+  double inner_its = 0;          // iterative coarse solve: mean inner iterations per run
   for (int ph = 0; ph < HZ_PH_COUNT; ph++) {
     run(ph);   // warm-up
     const long long l0 = hz::launch_count();
+    const int64_t c0 = c->stats.coarse_iterations;
     CU(cudaEventRecord(e0, st));
     for (int r = 0; r < reps; r++) run(ph);
     CU(cudaEventRecord(e1, st));
@@ -1413,6 +1563,7 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
     CU(cudaEventElapsedTime(&ms, e0, e1));
     out->ms[ph] = double(ms) / reps;
     out->launches[ph] = (hz::launch_count() - l0) / reps;
+    if (ph == HZ_PH_COARSE) inner_its = double(c->stats.coarse_iterations - c0) / reps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1423,9 +1574,20 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   out->flops[HZ_PH_SPMV] = 8 * nnz;
   if (c->levels == 2) {
     const double nz = double(c->zeta_nnz), nH = double(c->nH);
-    out->bytes[HZ_PH_COARSE] = 2 * nz * 12 + (dn + 1) * 8 + (nH + 1) * 8 + 2 * dn * nt + 2 * nH * nt +
-                               c->crs.gather_bytes + c->crs.solve_bytes + c->crs.prolong_bytes;
-    out->flops[HZ_PH_COARSE] = 2 * 4 * nz + c->crs.solve_flops;
+    out->bytes[HZ_PH_COARSE] = 2 * nz * 12 + (dn + 1) * 8 + (nH + 1) * 8 + 2 * dn * nt + 2 * nH * nt;
+    out->flops[HZ_PH_COARSE] = 2 * 4 * nz;
+    if (c->coarse_oras) {
+      // per inner iteration: local coarse sweeps, E z, CGS2 at the mean position
+      const double nzE = double(c->nnzH), jm = 0.5 * (inner_its + 1.0);
+      const double bi = c->cloc.gather_bytes + c->cloc.solve_bytes + c->cloc.prolong_bytes +
+                        nzE * (nt + 4) + (nH + 1) * 8 + 2 * nH * nt + (3 * (jm + 1) + 5) * nH * nt;
+      const double fi = c->cloc.solve_flops + 8 * nzE + (32 * (jm + 1) + 12) * nH;
+      out->bytes[HZ_PH_COARSE] += inner_its * bi;
+      out->flops[HZ_PH_COARSE] += inner_its * fi;
+    } else {
+      out->bytes[HZ_PH_COARSE] += c->crs.gather_bytes + c->crs.solve_bytes + c->crs.prolong_bytes;
+      out->flops[HZ_PH_COARSE] += c->crs.solve_flops;
+    }
   }
   out->bytes[HZ_PH_RESTRICT] = c->loc.gather_bytes;
   out->bytes[HZ_PH_LOCAL_SOLVE] = c->loc.solve_bytes;
@@ -1499,11 +1661,17 @@ void plan_bytes(const hz::HostProblem& P, const hz_options& op, int64_t& persist
   b += P.coarse.panel_elems * 16;
   if (!P.coarse.voff.empty())
     b += (3 * P.coarse.voff.back() + P.coarse.u_elems) * 16 + int64_t(P.coarse.epos.size()) * 40;
+  if (!P.clocal.voff.empty()) {
+    const int64_t mH = op.coarse_maxit > 0 ? op.coarse_maxit : 30;
+    b += P.clocal.panel_elems * vs + (3 * P.clocal.voff.back() + P.clocal.u_elems) * vs +
+         int64_t(P.clocal.epos.size()) * 40;
+    b += P.E.pat.nnz() * (4 + 8 + 16 + 16 + 16) + (P.nH + 1) * 8 + (2 * mH + 2) * P.nH * 16;
+  }
   b += (P.Z.nnz() + P.Zt.nnz()) * 12;
   b += (2 * m + 8) * n * 16;                                                   // one-RHS Krylov
   if (S) b += S * n * (2 * m + 9) * 16 + S * (P.local.voff.back() + P.local.u_elems) * 3 * vs;
   persistent = b + b / 20 + (64 << 20);                                        // 5 % + 64 MB headroom
-  const int64_t tl = P.local.front_elems * vs, tc = P.coarse.front_elems * 16;
+  const int64_t tl = std::max(P.local.front_elems, P.clocal.front_elems) * vs, tc = P.coarse.front_elems * 16;
   transient = std::max(tl, tc) + std::max(tl, tc) / 10;
 }
 

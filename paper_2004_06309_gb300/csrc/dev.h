@@ -127,6 +127,7 @@ void launch_local_multi(const FactorDev& F, int S, const double2* src, const dou
 void launch_interleave(int64_t n, int S, const SlotCols& off, const double2* base, double2* inter, cudaStream_t st);
 void launch_deinterleave(int64_t n, int S, const SlotCols& off, const double2* inter, double2* base, cudaStream_t st);
 void launch_point_rhs(const PointRhs& p, double2* out, cudaStream_t st);
+void launch_interleave_put(int64_t n, int S, int i, const double2* col, double2* inter, cudaStream_t st);
 void launch_spmv_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                        const double2* sub, double2* y, cudaStream_t st);
 void launch_spmv_real_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double* val,

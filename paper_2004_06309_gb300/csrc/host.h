@@ -93,7 +93,14 @@ struct HostProblem {
   Csr Z, Zt;                          // n x nH and nH x n
   std::vector<double> Zv, Ztv;
   Parts E;                            // coarse operator pieces
-  SymbolicSet coarse;
+  SymbolicSet coarse;                 // direct coarse solve: LDL^T of E
+  // iterative coarse solve: one-level ORAS on the coarse mesh (same partition)
+  std::vector<double> cEK;            // per coarse element Galerkin pieces (transient)
+  std::vector<cplx> cEM, cEB;
+  std::vector<int32_t> cpart;         // coarse element -> part
+  std::vector<Subdomain> csubs;       // Gamma_H,i with E_i pieces (dofs: full coarse ids)
+  std::vector<std::vector<int64_t>> cgidx;   // free coarse id of each local dof (0: Dirichlet)
+  SymbolicSet clocal;                 // LDL^T of all E_i
 };
 
 // setup.cpp
@@ -102,7 +109,8 @@ void assemble_global(const Mesh& m, const Dofs& d, Parts& A);
 void rcb_partition(const Mesh& m, int nparts, std::vector<int32_t>& part);
 void build_subdomains(const Mesh& m, const Dofs& d, const std::vector<int32_t>& part, int nsub,
                       int overlap, std::vector<Subdomain>& subs);
-void build_coarse(HostProblem& P);
+void build_coarse(HostProblem& P, bool keep_pieces = false);
+void build_coarse_subdomains(HostProblem& P, const std::vector<int32_t>& part, int nsub, int overlap);
 bool locate_point(const Mesh& m, const double* p, int64_t& elem, double lam[4]);
 void eval_basis(int order, const double lam[4], double* out);
 

@@ -1128,6 +1128,16 @@ void launch_deinterleave(int64_t n, int S, const SlotCols& off, const double2* i
   k_deinterleave<<<grid_for(n * S, 256), 256, 0, st>>>(n, S, off, inter, base);
 }
 
+// Column i of S interleaved vectors set from a plain vector (other columns untouched).
+__global__ void k_interleave_put(int64_t n, int S, int i, const double2* col, double2* inter) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x)
+    inter[r * S + i] = col[r];
+}
+void launch_interleave_put(int64_t n, int S, int i, const double2* col, double2* inter, cudaStream_t st) {
+  HZ_COUNT();
+  k_interleave_put<<<grid_for(n, 256), 256, 0, st>>>(n, S, i, col, inter);
+}
+
 // Point-source right-hand side written into a zeroed column: out[idx[q]] += val[q].
 __global__ void k_point_rhs(PointRhs p, double2* out) {
   if (threadIdx.x == 0)

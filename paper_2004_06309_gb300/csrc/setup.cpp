@@ -434,19 +434,74 @@ void rcb_partition(const Mesh& m, int nparts, std::vector<int32_t>& part) {
 }
 
 // ---------------------------------------------------------------------------
-void build_subdomains(const Mesh& m, const Dofs& d, const std::vector<int32_t>& part, int nsub,
-                      int overlap, std::vector<Subdomain>& subs) {
+// Vertex -> element incidence (CSR).
+static void vertex_elements(const Mesh& m, std::vector<int64_t>& vptr, std::vector<int64_t>& vel) {
   const int64_t nv = m.nv, ne = m.ne;
-  // vertex -> elements
-  std::vector<int64_t> vptr(nv + 1, 0), vel(size_t(ne) * 4);
+  vptr.assign(nv + 1, 0);
+  vel.resize(size_t(ne) * 4);
   for (int64_t e = 0; e < ne; e++)
     for (int k = 0; k < 4; k++) vptr[m.tets[4 * e + k] + 1]++;
   for (int64_t v = 0; v < nv; v++) vptr[v + 1] += vptr[v];
-  {
-    std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
-    for (int64_t e = 0; e < ne; e++)
-      for (int k = 0; k < 4; k++) vel[fill[m.tets[4 * e + k]]++] = e;
+  std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
+  for (int64_t e = 0; e < ne; e++)
+    for (int k = 0; k < 4; k++) vel[fill[m.tets[4 * e + k]]++] = e;
+}
+
+// Elements of part i grown by `overlap` layers, each layer adding every element that
+// shares a vertex with the current set; layer[v] = the layer at which vertex v entered
+// (0 for the part itself).  in_e / layer are scratch (all clear on entry; the caller
+// clears the entries of elems / verts afterwards).
+static void grow_part(const Mesh& m, const std::vector<int64_t>& vptr, const std::vector<int64_t>& vel,
+                      const std::vector<int32_t>& part, int i, int overlap, std::vector<int32_t>& layer,
+                      std::vector<uint8_t>& in_e, std::vector<int64_t>& elems, std::vector<int64_t>& verts) {
+  std::vector<int64_t> frontier;
+  for (int64_t e = 0; e < m.ne; e++)
+    if (part[e] == i) { elems.push_back(e); in_e[e] = 1; }
+  for (int64_t e : elems)
+    for (int k = 0; k < 4; k++) {
+      const int32_t v = m.tets[4 * e + k];
+      if (layer[v] < 0) { layer[v] = 0; verts.push_back(v); frontier.push_back(v); }
+    }
+  for (int l = 1; l <= overlap; l++) {
+    std::vector<int64_t> newe;
+    for (int64_t v : frontier)
+      for (int64_t k = vptr[v]; k < vptr[v + 1]; k++) {
+        const int64_t e = vel[k];
+        if (!in_e[e]) { in_e[e] = 1; newe.push_back(e); }
+      }
+    frontier.clear();
+    for (int64_t e : newe) {
+      elems.push_back(e);
+      for (int k = 0; k < 4; k++) {
+        const int32_t v = m.tets[4 * e + k];
+        if (layer[v] < 0) { layer[v] = l; verts.push_back(v); frontier.push_back(v); }
+      }
+    }
   }
+  std::sort(elems.begin(), elems.end());
+}
+
+// Partition-of-unity weight chi = 1 - l / overlap of each dof (edge dofs: mean of the
+// two end vertices).
+static void pu_weights(const Dofs& d, int64_t nv, const std::vector<int32_t>& layer, int overlap,
+                       const std::vector<int64_t>& dofs, std::vector<double>& chi) {
+  auto chiv = [&](int64_t v) { return overlap == 0 ? 1.0 : 1.0 - double(layer[v]) / double(overlap); };
+  chi.resize(dofs.size());
+  for (size_t k = 0; k < dofs.size(); k++) {
+    const int64_t g = dofs[k];
+    if (g < nv) chi[k] = chiv(g);
+    else {
+      const int64_t key = d.edge_key[g - nv];
+      chi[k] = 0.5 * (chiv(key / nv) + chiv(key % nv));
+    }
+  }
+}
+
+void build_subdomains(const Mesh& m, const Dofs& d, const std::vector<int32_t>& part, int nsub,
+                      int overlap, std::vector<Subdomain>& subs) {
+  const int64_t nv = m.nv, ne = m.ne;
+  std::vector<int64_t> vptr, vel;
+  vertex_elements(m, vptr, vel);
   // global boundary faces: sorted keys with tags
   std::vector<std::pair<int64_t, int8_t>> bkeys(m.tag.size());
   for (size_t f = 0; f < m.tag.size(); f++)
@@ -465,31 +520,8 @@ void build_subdomains(const Mesh& m, const Dofs& d, const std::vector<int32_t>& 
 #pragma omp for schedule(dynamic, 1)
     for (int i = 0; i < nsub; i++) {
       Subdomain& S = subs[i];
-      std::vector<int64_t> elems, verts, frontier;
-      for (int64_t e = 0; e < ne; e++)
-        if (part[e] == i) { elems.push_back(e); in_e[e] = 1; }
-      for (int64_t e : elems)
-        for (int k = 0; k < 4; k++) {
-          const int32_t v = m.tets[4 * e + k];
-          if (layer[v] < 0) { layer[v] = 0; verts.push_back(v); frontier.push_back(v); }
-        }
-      for (int l = 1; l <= overlap; l++) {
-        std::vector<int64_t> newe;
-        for (int64_t v : frontier)
-          for (int64_t k = vptr[v]; k < vptr[v + 1]; k++) {
-            const int64_t e = vel[k];
-            if (!in_e[e]) { in_e[e] = 1; newe.push_back(e); }
-          }
-        frontier.clear();
-        for (int64_t e : newe) {
-          elems.push_back(e);
-          for (int k = 0; k < 4; k++) {
-            const int32_t v = m.tets[4 * e + k];
-            if (layer[v] < 0) { layer[v] = l; verts.push_back(v); frontier.push_back(v); }
-          }
-        }
-      }
-      std::sort(elems.begin(), elems.end());
+      std::vector<int64_t> elems, verts;
+      grow_part(m, vptr, vel, part, i, overlap, layer, in_e, elems, verts);
       // dofs
       std::vector<int64_t> dofs;
       dofs.reserve(elems.size() * 2);
@@ -498,16 +530,8 @@ void build_subdomains(const Mesh& m, const Dofs& d, const std::vector<int32_t>& 
       std::sort(dofs.begin(), dofs.end());
       dofs.erase(std::unique(dofs.begin(), dofs.end()), dofs.end());
       const int64_t ni = int64_t(dofs.size());
-      std::vector<double> chi(ni);
-      auto chiv = [&](int64_t v) { return overlap == 0 ? 1.0 : 1.0 - double(layer[v]) / double(overlap); };
-      for (int64_t k = 0; k < ni; k++) {
-        const int64_t g = dofs[k];
-        if (g < nv) chi[k] = chiv(g);
-        else {
-          const int64_t key = d.edge_key[g - nv];
-          chi[k] = 0.5 * (chiv(key / nv) + chiv(key % nv));
-        }
-      }
+      std::vector<double> chi;
+      pu_weights(d, nv, layer, overlap, dofs, chi);
       for (int64_t k = 0; k < ni; k++) loc[dofs[k]] = k;
       // local operator on the element pattern of Gamma_i
       std::vector<int64_t> ld(elems.size() * d.nb);
@@ -589,7 +613,25 @@ static inline void bary_from(const double g[4][3], const double* x0, const doubl
   l[0] = 1.0 - s;
 }
 
-void build_coarse(HostProblem& P) {
+// Interpolation weights of the coarse basis of element E at fine node `node` (zeroed
+// on fine Dirichlet nodes and for removed coarse Dirichlet dofs; rounding noise below
+// 1e-12 dropped: the exact weights are dyadic rationals).  g: gradients of E.
+static void coarse_zrow(const HostProblem& P, int64_t E, const double g[4][3], int64_t node, double* out) {
+  const Mesh& cm = P.cmesh;
+  const Dofs& d = P.dofs;
+  const Dofs& cd = P.cdofs;
+  const int nb = d.nb;
+  double l[4], phi[10];
+  bary_from(g, cm.xyz.data() + 3 * int64_t(cm.tets[4 * E]), d.coord.data() + 3 * node, l);
+  eval_basis(d.order, l, phi);
+  for (int b = 0; b < nb; b++) {
+    double v = phi[b];
+    if (std::fabs(v) < 1e-12 || d.is_dir[node] || P.cfree[cd.elem[nb * E + b]] < 0) v = 0.0;
+    out[b] = v;
+  }
+}
+
+void build_coarse(HostProblem& P, bool keep_pieces) {
   const Mesh& m = P.mesh;
   const Mesh& cm = P.cmesh;
   const Dofs& d = P.dofs;
@@ -602,19 +644,7 @@ void build_coarse(HostProblem& P) {
   P.nH = nH;
   const int nb = d.nb;
   const int64_t ncE = cm.ne;
-  // Interpolation weights of the coarse basis of element E at fine node g (zeroed
-  // on fine Dirichlet nodes and for removed coarse Dirichlet dofs; rounding noise
-  // below 1e-12 dropped: the exact weights are dyadic rationals).
-  auto zrow = [&](int64_t E, const double g[4][3], int64_t node, double* out) {
-    double l[4], phi[10];
-    bary_from(g, cm.xyz.data() + 3 * int64_t(cm.tets[4 * E]), d.coord.data() + 3 * node, l);
-    eval_basis(d.order, l, phi);
-    for (int b = 0; b < nb; b++) {
-      double v = phi[b];
-      if (std::fabs(v) < 1e-12 || d.is_dir[node] || P.cfree[cd.elem[nb * E + b]] < 0) v = 0.0;
-      out[b] = v;
-    }
-  };
+  auto zrow = [&](int64_t E, const double g[4][3], int64_t node, double* out) { coarse_zrow(P, E, g, node, out); };
   // Z rows: for every fine node, the lowest fine element containing it
   std::vector<int64_t> first_elem(d.n, -1);
   for (int64_t e = m.ne - 1; e >= 0; e--)
@@ -767,6 +797,181 @@ void build_coarse(HostProblem& P) {
       }
     }
   }
+  if (keep_pieces) {
+    P.cEK.swap(EK);
+    P.cEM.swap(EM);
+    P.cEB.swap(EB);
+  }
+}
+
+// Coarse level of the iterative coarse solve: one-level ORAS on the coarse mesh with
+// the fine partition carried over (a coarse element joins the part holding most of its
+// fine children; ties: lowest part), the fine overlap and partition-of-unity recipe
+// applied to the coarse mesh, and local operators E_i = sum of the Galerkin pieces of
+// the coarse elements of Gamma_H,i plus, on its artificial interfaces, the Galerkin
+// projection of the fine absorbing term (fine faces on the coarse face, coefficient of
+// the fine element inside).  Coarse Dirichlet dofs are identity rows with weight 0.
+void build_coarse_subdomains(HostProblem& P, const std::vector<int32_t>& part, int nsub, int overlap) {
+  const Mesh& m = P.mesh;
+  const Mesh& cm = P.cmesh;
+  const Dofs& d = P.dofs;
+  const Dofs& cd = P.cdofs;
+  const int nb = d.nb;
+  const size_t nb2 = size_t(nb) * nb;
+  const int64_t ncE = cm.ne, nvH = cm.nv;
+  std::vector<int64_t> cptr(ncE + 1, 0), kids(m.ne);
+  for (int64_t e = 0; e < m.ne; e++) cptr[P.parent[e] + 1]++;
+  for (int64_t E = 0; E < ncE; E++) cptr[E + 1] += cptr[E];
+  {
+    std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int64_t e = 0; e < m.ne; e++) kids[fill[P.parent[e]]++] = e;
+  }
+  P.cpart.assign(ncE, 0);
+  for (int64_t E = 0; E < ncE; E++) {
+    int32_t best = -1, bestc = 0;
+    for (int64_t q = cptr[E]; q < cptr[E + 1]; q++) {
+      const int32_t pq = part[kids[q]];
+      int32_t c = 0;
+      for (int64_t r = cptr[E]; r < cptr[E + 1]; r++) c += part[kids[r]] == pq;
+      if (c > bestc || (c == bestc && pq < best)) { best = pq; bestc = c; }
+    }
+    P.cpart[E] = best < 0 ? 0 : best;
+  }
+  std::vector<int64_t> vptr, vel;
+  vertex_elements(cm, vptr, vel);
+  std::vector<std::pair<int64_t, int8_t>> bkeys(cm.tag.size());
+  for (size_t f = 0; f < cm.tag.size(); f++)
+    bkeys[f] = {face_key(cm.faces[3 * f], cm.faces[3 * f + 1], cm.faces[3 * f + 2], nvH), cm.tag[f]};
+  std::sort(bkeys.begin(), bkeys.end());
+  const RefTables& R = ref();
+  P.csubs.assign(nsub, Subdomain());
+  std::vector<std::vector<double>> chis(nsub);
+#pragma omp parallel
+  {
+    std::vector<int32_t> layer(nvH, -1);
+    std::vector<uint8_t> in_e(ncE, 0);
+    std::vector<int64_t> loc(cd.n, -1);
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < nsub; i++) {
+      Subdomain& S = P.csubs[i];
+      std::vector<int64_t> elems, verts;
+      grow_part(cm, vptr, vel, P.cpart, i, overlap, layer, in_e, elems, verts);
+      std::vector<int64_t> dofs;
+      for (int64_t E : elems)
+        for (int a = 0; a < nb; a++) dofs.push_back(cd.elem[nb * E + a]);
+      std::sort(dofs.begin(), dofs.end());
+      dofs.erase(std::unique(dofs.begin(), dofs.end()), dofs.end());
+      const int64_t ni = int64_t(dofs.size());
+      std::vector<double> chi;
+      pu_weights(cd, nvH, layer, overlap, dofs, chi);
+      for (int64_t k = 0; k < ni; k++) loc[dofs[k]] = k;
+      std::vector<int64_t> ld(elems.size() * nb);
+      for (size_t q = 0; q < elems.size(); q++)
+        for (int a = 0; a < nb; a++) ld[q * nb + a] = loc[cd.elem[nb * elems[q] + a]];
+      element_pattern(cd, elems, ni, ld, S.A.pat);
+      const int64_t nnz = S.A.pat.nnz();
+      S.A.K.assign(nnz, 0.0);
+      S.A.M.assign(nnz, 0.0);
+      S.A.B.assign(nnz, 0.0);
+      for (size_t q = 0; q < elems.size(); q++) {
+        const size_t o = size_t(elems[q]) * nb2;
+        for (int a = 0; a < nb; a++)
+          for (int b = 0; b < nb; b++) {
+            const int64_t k = S.A.pat.find(ld[q * nb + a], ld[q * nb + b]);
+            S.A.K[k] += P.cEK[o + a * nb + b];
+            S.A.M[k] += P.cEM[o + a * nb + b];
+            S.A.B[k] += P.cEB[o + a * nb + b];
+          }
+      }
+      // coarse faces of Gamma_H,i seen once and not on the global boundary
+      std::vector<std::pair<int64_t, int64_t>> fk(elems.size() * 4);
+      for (size_t q = 0; q < elems.size(); q++)
+        for (int k = 0; k < 4; k++) {
+          const int32_t* t = cm.tets.data() + 4 * elems[q];
+          fk[4 * q + k] = {face_key(t[kTetFace[k][0]], t[kTetFace[k][1]], t[kTetFace[k][2]], nvH), int64_t(4 * q + k)};
+        }
+      std::sort(fk.begin(), fk.end());
+      for (size_t a = 0; a < fk.size();) {
+        size_t b = a + 1;
+        while (b < fk.size() && fk[b].first == fk[a].first) b++;
+        if (b - a == 1) {
+          auto it = std::lower_bound(bkeys.begin(), bkeys.end(), std::make_pair(fk[a].first, int8_t(-128)));
+          const bool on_bdry = it != bkeys.end() && it->first == fk[a].first;
+          if (!on_bdry) {
+            const size_t q = size_t(fk[a].second / 4);
+            const int kf = int(fk[a].second % 4);
+            const int64_t E = elems[q];
+            double gr[4][3];
+            tet_grads(cm.xyz.data(), cm.tets.data() + 4 * E, gr);
+            const double* x0 = cm.xyz.data() + 3 * int64_t(cm.tets[4 * E]);
+            cplx piece[100];
+            for (size_t z = 0; z < nb2; z++) piece[z] = 0.0;
+            for (int64_t c = cptr[E]; c < cptr[E + 1]; c++) {
+              const int64_t e = kids[c];
+              const int32_t* t = m.tets.data() + 4 * e;
+              for (int fq = 0; fq < 4; fq++) {
+                const int32_t f3[3] = {t[kTetFace[fq][0]], t[kTetFace[fq][1]], t[kTetFace[fq][2]]};
+                bool on = true;
+                for (int v = 0; v < 3 && on; v++) {
+                  double l[4];
+                  bary_from(gr, x0, m.xyz.data() + 3 * int64_t(f3[v]), l);
+                  on = std::fabs(l[kf]) < 1e-9;
+                }
+                if (!on) continue;
+                int64_t fd[6];
+                d.face_dofs(f3, fd);
+                double Zf[60];
+                for (int z = 0; z < d.nbf; z++) coarse_zrow(P, E, gr, fd[z], Zf + z * nb);
+                const double area = tri_area(m.xyz.data(), f3);
+                const cplx w = 1.0 / m.c[e];
+                for (int aa = 0; aa < nb; aa++)
+                  for (int bb = 0; bb < nb; bb++) {
+                    double sacc = 0;
+                    for (int pp = 0; pp < d.nbf; pp++)
+                      for (int rr = 0; rr < d.nbf; rr++)
+                        sacc += Zf[pp * nb + aa] * area * R.F[d.order - 1][pp][rr] * Zf[rr * nb + bb];
+                    piece[aa * nb + bb] += w * sacc;
+                  }
+              }
+            }
+            for (int aa = 0; aa < nb; aa++)
+              for (int bb = 0; bb < nb; bb++) {
+                const int64_t k = S.A.pat.find(ld[q * nb + aa], ld[q * nb + bb]);
+                S.A.B[k] += piece[aa * nb + bb];
+              }
+          }
+        }
+        a = b;
+      }
+      std::vector<uint8_t> ldir(ni);
+      for (int64_t k = 0; k < ni; k++) ldir[k] = cd.is_dir[dofs[k]];
+      fold_dirichlet(S.A, ldir.data());
+      for (int64_t E : elems) in_e[E] = 0;
+      for (int64_t v : verts) layer[v] = -1;
+      for (int64_t k = 0; k < ni; k++) loc[dofs[k]] = -1;
+      S.elems.swap(elems);
+      S.dofs.swap(dofs);
+      chis[i].swap(chi);
+    }
+  }
+  std::vector<double> chi_sum(cd.n, 0.0);
+  for (int i = 0; i < nsub; i++)
+    for (size_t k = 0; k < P.csubs[i].dofs.size(); k++) chi_sum[P.csubs[i].dofs[k]] += chis[i][k];
+  P.cgidx.assign(nsub, {});
+  for (int i = 0; i < nsub; i++) {
+    Subdomain& S = P.csubs[i];
+    S.D.resize(S.dofs.size());
+    P.cgidx[i].resize(S.dofs.size());
+    for (size_t k = 0; k < S.dofs.size(); k++) {
+      const int64_t g = S.dofs[k];
+      const bool free = P.cfree[g] >= 0;
+      S.D[k] = free ? chis[i][k] / chi_sum[g] : 0.0;
+      P.cgidx[i][k] = free ? P.cfree[g] : 0;
+    }
+  }
+  std::vector<double>().swap(P.cEK);
+  std::vector<cplx>().swap(P.cEM);
+  std::vector<cplx>().swap(P.cEB);
 }
 
 bool locate_point(const Mesh& m, const double* p, int64_t& elem, double lam[4]) {
