@@ -5,8 +5,9 @@ FP64, with p50/p99 latency per right-hand side.
 
 Workload (default): the 5 Hz Overthrust-shaped synthetic model -- 20 x 20 x 4.65
 km, layered 2-6 km/s with two thrust-fold surfaces and 5% random texture, Q =
-100; nested P2 tetrahedral meshes (fine 100 x 100 x 24 cells x 6 tets, 1.98M
-dofs; coarse mesh twice as coarse); 64 subdomains, overlap 2, two-level ORAS,
+100; nested P2 tetrahedral meshes at 5 fine / 2.5 coarse nodes per wavelength
+(coarse 63 x 63 x 9 cells x 6 tets, fine its uniform refinement: 2.37M dofs);
+64 subdomains, overlap 2, two-level ORAS,
 FGMRES(50), one source at (2.5, 2.5, 0.58) km.  A step is one hz_solve of that
 right-hand side to 1e-6 (the per-frequency factorisation is done once before the
 timed region and reported separately).
@@ -30,19 +31,24 @@ sys.path.insert(0, ROOT)
 METRIC = "RHS solved/s to rel. residual 1e-6, mixed vs FP64 ORAS-GMRES; p50/p99 latency"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal, from the platform figures
 WORKLOADS = {
-    "overthrust-5hz": dict(kind="overthrust", cells=(50, 50, 12), freq=5.0, nsub=64, overlap=2,
+    "overthrust-5hz": dict(kind="overthrust", cells=None, freq=5.0, nsub=64, overlap=2,
                            restart=50),
-    "overthrust-medium": dict(kind="overthrust", cells=(24, 24, 6), freq=2.5, nsub=16, overlap=2,
+    "overthrust-medium": dict(kind="overthrust", cells=None, freq=2.5, nsub=16, overlap=2,
                               restart=50),
-    "overthrust-small": dict(kind="overthrust", cells=(12, 12, 3), freq=1.2, nsub=8, overlap=2,
+    "overthrust-small": dict(kind="overthrust", cells=None, freq=1.25, nsub=8, overlap=2,
                              restart=50),
     "tiny": dict(kind="tiny"),
 }
 # Inner iterations the 5 Hz workload takes to 1e-6 (measured on the GPU path, FP64 and mixed
 # alike); the reference arm runs in a separate process and scales its sample by it.
-FULL_WORKLOAD_ITERATIONS = 72
+FULL_WORKLOAD_ITERATIONS = 74
 # Oracle sample for the CPU baseline / reference arm: same generator, 1/64 of the dofs.
-ORACLE_SAMPLE = dict(kind="overthrust", cells=(12, 12, 3), freq=1.25, nsub=8, overlap=2, restart=50)
+ORACLE_SAMPLE = dict(kind="overthrust", cells=None, freq=1.25, nsub=8, overlap=2, restart=50)
+
+
+def synth_cells(spec):
+    import synth
+    return spec["cells"] or synth.overthrust_cells(spec["freq"])
 
 
 def make_problem(spec):
@@ -161,9 +167,8 @@ SERVE_FREQS = (1.0, 1.25, 1.5, 2.0, 2.5)
 
 def serve_problem(seed, f):
     import synth
-    cells = (int(round(10 * f)), int(round(10 * f)), max(3, int(round(2.4 * f))))
     nsub = 8 if f < 1.5 else 16
-    return synth.overthrust_problem(seed=seed, freq=f, cells=cells, nsub=nsub, overlap=2, restart=50, levels=2)
+    return synth.overthrust_problem(seed=seed, freq=f, nsub=nsub, overlap=2, restart=50, levels=2)
 
 
 def serve_requests(rng, nreq, rate, max_batch):
@@ -318,10 +323,13 @@ def trends_bench(args):
         torch.cuda.empty_cache()
         return dict(n=n, iterations=max(i[0] for i in info), seconds=dt, ok=all(i[1] == 0 for i in info))
 
-    freqs = [(1.25, (12, 12, 3), 8), (2.5, (25, 25, 6), 16), (5.0, (50, 50, 12), 64)]
+    # the paper's resolution (coarse edges of 1/2.5 of the wavelength) at three frequencies,
+    # then the 5 Hz workload's own mesh (half that resolution)
+    rows = [(0.625, 2.5, 8), (1.25, 2.5, 16), (2.5, 2.5, 64), (5.0, 1.25, 64)]
     table = []
-    for f, cells, nsub in freqs:
-        row = {"freq_hz": f, "nsub": nsub}
+    for f, epw, nsub in rows:
+        cells = synth.overthrust_cells(f, epw)
+        row = {"freq_hz": f, "coarse_elems_per_wavelength": epw, "cells": list(cells), "nsub": nsub}
         for lv in (1, 2):
             p = synth.overthrust_problem(seed=0, freq=f, cells=cells, nsub=nsub, overlap=2, levels=lv)
             r = run(p, lv)
@@ -330,14 +338,15 @@ def trends_bench(args):
         table.append(row)
     qrows = []
     for Q in (50.0, 100.0, 1000.0):
-        p = synth.overthrust_problem(seed=0, freq=2.5, cells=(25, 25, 6), nsub=16, overlap=2, levels=2, Q=Q)
+        p = synth.overthrust_problem(seed=0, freq=1.25, cells=synth.overthrust_cells(1.25, 2.5), nsub=16,
+                                     overlap=2, levels=2, Q=Q)
         r = run(p, 2)
         qrows.append({"Q": Q, "iterations": r["iterations"], "ok": r["ok"]})
-    p = synth.overthrust_problem(seed=0, freq=5.0, cells=(50, 50, 12), nsub=64, overlap=2, levels=2)
+    p = synth.overthrust_problem(seed=0, freq=5.0, nsub=64, overlap=2, levels=2)
     one = run(p, 2)
     ten = run(p, 2, nrhs=10, block=16)
     line = {"experiment": "trends (Table 1 shape on synthetic Overthrust-shaped models)",
-            "iterations_vs_frequency": table, "attenuation_2p5hz": qrows,
+            "iterations_vs_frequency": table, "attenuation_1p25hz_paper_resolution": qrows,
             "multi_rhs_5hz": {"one_rhs_s": one["seconds"], "ten_rhs_s": ten["seconds"],
                               "ratio_10_to_1": ten["seconds"] / one["seconds"],
                               "iterations": [one["iterations"], ten["iterations"]]},
@@ -386,10 +395,11 @@ def main():
             return
         samp = oracle_subprocess(args.steps, args.warmup)
         full_it = FULL_WORKLOAD_ITERATIONS
-        p_full_n = 1_985_000 if args.workload == "overthrust-5hz" else samp["n"]
+        nx, ny, nz = synth_cells(WORKLOADS["overthrust-5hz"])
+        p_full_n = (4 * nx + 1) * (4 * ny + 1) * (4 * nz + 1) if args.workload == "overthrust-5hz" else samp["n"]
         val = scaled_rhs_per_s(samp, p_full_n, full_it) if args.workload == "overthrust-5hz" else 1.0 / samp["seconds"]
         sample_txt = (f"FP64 oracle solve (factorisation excluded) of the same Overthrust-shaped generator at "
-                      f"cells {ORACLE_SAMPLE['cells']} ({samp['n']} dofs, {ORACLE_SAMPLE['nsub']} subdomains, "
+                      f"cells {synth_cells(ORACLE_SAMPLE)} ({samp['n']} dofs, {ORACLE_SAMPLE['nsub']} subdomains, "
                       f"{samp['iterations']} iterations), scaled by dofs x iterations")
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "RHS/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * samp["seconds"],
@@ -544,6 +554,8 @@ def main():
         "clocks": R["clocks"],
         "roofline": roof,
         "phases_ms": {k: round(v["ms"], 4) for k, v in prof.items()},
+        "phases_gbytes": {k: round(v["bytes"] / 1e9, 4) for k, v in prof.items()},
+        "phases_gflops": {k: round(v["flops"] / 1e9, 4) for k, v in prof.items()},
         "stats": {k: R["stats"][k] for k in ("nnz", "n_coarse", "sum_ni", "nnz_factor", "nnz_factor_coarse",
                                              "nsupernodes", "nlevels", "front_bytes", "device_bytes",
                                              "setup_seconds", "coarse_solves", "coarse_iterations")},
@@ -556,6 +568,7 @@ def main():
                         "factor_seconds": F["t_factor"],
                         "e2e_value": world * K * args.nrhs / F["e2e_s"],
                         "phases_ms": {k: round(v["ms"], 4) for k, v in F["profile"].items()},
+                        "phases_gflops": {k: round(v["flops"] / 1e9, 4) for k, v in F["profile"].items()},
                         "clocks": F["clocks"]}
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -565,7 +578,7 @@ def main():
             line["cpu_baseline"] = {
                 "value": val, "unit": "RHS/s", "cores": samp["cores"], "kind": "oracle",
                 "sample": (f"serial FP64 oracle solve (factorisation excluded) of the same generator at cells "
-                           f"{ORACLE_SAMPLE['cells']}: {samp['n']} dofs, {ORACLE_SAMPLE['nsub']} subdomains, "
+                           f"{synth_cells(ORACLE_SAMPLE)}: {samp['n']} dofs, {ORACLE_SAMPLE['nsub']} subdomains, "
                            f"{samp['iterations']} iterations in {samp['seconds']:.2f} s; scaled to this workload "
                            f"by dofs x iterations")}
         except Exception as e:  # the GPU line still stands

@@ -273,6 +273,20 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
       cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1), tc_ptr(nlev + 1);
   int64_t scratch = 0;
+  // complex128 sweeps: levels with fewer tasks than two per SM get narrow tasks
+  // (16-row forward tasks, 64-row backward chunks) so that they reach every SM
+  std::vector<int> fwd_rt(nlev, precision == 0 ? 64 : 256), lev_bwd_rows(nlev, bwd_rows);
+  if (precision == 0)
+    for (int l = 0; l < nlev; l++) {
+      int64_t nf = 0, nbk = 0;
+      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+        const int s = S.lev_sn[q];
+        nf += (S.sn_m[s] + 63) / 64;
+        nbk += int64_t((S.sn_k[s] + 31) / 32) * ((S.sn_m[s] + bwd_rows - 1) / bwd_rows);
+      }
+      if (nf < 2 * 152) fwd_rt[l] = 16;
+      if (nbk < 2 * 152) lev_bwd_rows[l] = std::min(bwd_rows, 64);
+    }
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
     fwd_ptr[l] = int64_t(fwd.size());
@@ -285,9 +299,9 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
-      const int frows = precision == 0 ? 64 : 256;     // forward task rows (k_fwd / k_fwd_c64)
+      const int frows = fwd_rt[l];                     // forward task rows (k_fwd / k_fwd_c64)
       for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
-      const int nch = (m + bwd_rows - 1) / bwd_rows;
+      const int nch = (m + lev_bwd_rows[l] - 1) / lev_bwd_rows[l];
       for (int cb = 0; cb * 32 < k; cb++) {
         const int fin = int(bfin.size());          // global index: its counter and its record
         bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
@@ -321,6 +335,20 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     }
   }
   lev_ptr[nlev] = S.lev_ptr[nlev];
+  if (const char* vb = std::getenv("HZ_VERBOSE"); vb && std::atoi(vb) >= 2) {
+    // per tree level: supernodes, panel entries and sweep tasks (for reading launch lists)
+    for (int l = 0; l < nlev; l++) {
+      int64_t pe = 0;
+      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+        const int s = S.lev_sn[q];
+        pe += int64_t(S.sn_k[s]) * (2 * S.sn_m[s] - S.sn_k[s] + 1) / 2;
+      }
+      std::fprintf(stderr, "[hz] level %3d: %6d supernodes %12lld panel entries %6lld fwd %6lld bwd tasks\n", l,
+                   S.lev_ptr[l + 1] - S.lev_ptr[l], (long long)pe,
+                   (long long)((l + 1 < nlev ? fwd_ptr[l + 1] : int64_t(fwd.size())) - fwd_ptr[l]),
+                   (long long)((l + 1 < nlev ? bwd_ptr[l + 1] : int64_t(bwd.size())) - bwd_ptr[l]));
+    }
+  }
   fwd_ptr[nlev] = int64_t(fwd.size());
   bwd_ptr[nlev] = int64_t(bwd.size());
   bfin_ptr[nlev] = int64_t(bfin.size());
@@ -353,6 +381,12 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_tc_ptr = hcopy(tc_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
   F.h_ent_ptr = hcopy(S.ent_ptr);
+  if (precision == 0) {
+    F.h_fwd_rt = new int[nlev];
+    F.h_bwd_rows = new int[nlev];
+    std::copy(fwd_rt.begin(), fwd_rt.end(), F.h_fwd_rt);
+    std::copy(lev_bwd_rows.begin(), lev_bwd_rows.end(), F.h_bwd_rows);
+  }
   // batched sweeps for nrhs_block right-hand sides (pseudo-block FGMRES)
   if (nrhs_block > 1) {
     F.mS = nrhs_block;
@@ -430,6 +464,10 @@ void free_host_ptrs(hz::FactorDev& F) {
   delete[] F.h_ea_ptr;
   delete[] F.h_ent_ptr;
   delete[] F.h_mfwd_ptr;
+  delete[] F.h_fwd_rt;
+  delete[] F.h_bwd_rows;
+  F.h_fwd_rt = nullptr;
+  F.h_bwd_rows = nullptr;
   delete[] F.h_mbwd_ptr;
   F.h_mfwd_ptr = F.h_mbwd_ptr = nullptr;
   F.h_bfin_ptr = F.h_lev_ptr = F.h_fwd_ptr = F.h_bwd_ptr = F.h_wg_ptr = F.h_cb_ptr = F.h_ea_ptr = F.h_ent_ptr = nullptr;

@@ -590,13 +590,17 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
 // Forward, 64 rows of one supernode per task:
 //   b1 = t[pivots] + children's updates;  rows < k:  z = D^{-1} (T b1);
 //   rows >= k:  u = (children's updates) - G b1.
-constexpr int kFwdRows = 64;
-template <typename V>
+// Forward, RT rows of one supernode per task; 256 threads = RT rows x (256 / RT)
+// column groups.  64-row tasks where a tree level has many supernodes; 16-row tasks
+// where it has few (the top of a single tree), so that such a level still spreads
+// over every SM (its FP64 arithmetic, not its bytes, is the bound there).
+template <typename V, int RT>
 __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                              const int64_t* cidx, const V* panels, const V* tin, V* zout,
                                              V* u) {
+  constexpr int CG = 256 / RT;
   __shared__ V b1[kMaxK];
-  __shared__ V part[4][kFwdRows];
+  __shared__ V part[CG][RT];
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
@@ -607,23 +611,25 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
     b1[j] = acc;
   }
   __syncthreads();
-  const int rr = tid & (kFwdRows - 1), cg = tid / kFwdRows;
-  const int r = t.y * kFwdRows + rr;
+  const int rr = tid % RT, cg = tid / RT;
+  const int r = t.y * RT + rr;
   const V* P = panels + S.paneloff;
   V acc = czero<V>(), acc2 = czero<V>();
   if (r < m) {
     const int jmax = min(r, k);
     int j = cg;
-    for (; j + 4 < jmax; j += 8) {
+    for (; j + CG < jmax; j += 2 * CG) {
       acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
-      acc2 = cmad(P[r + int64_t(j + 4) * S.ld], b1[j + 4], acc2);
+      acc2 = cmad(P[r + int64_t(j + CG) * S.ld], b1[j + CG], acc2);
     }
     if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
   }
   part[cg][rr] = cadd(acc, acc2);
   __syncthreads();
   if (cg == 0 && r < m) {
-    const V tot = cadd(cadd(part[0][rr], part[1][rr]), cadd(part[2][rr], part[3][rr]));
+    V tot = part[0][rr];
+#pragma unroll
+    for (int q = 1; q < CG; q++) tot = cadd(tot, part[q][rr]);
     if (r < k) {
       zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
     } else {
@@ -842,8 +848,10 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       HZ_COUNT();
       if constexpr (sizeof(V) == 8)
         k_fwd_c64<<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+      else if (F.h_fwd_rt && F.h_fwd_rt[l] == 16)
+        k_fwd<V, 16><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
       else
-        k_fwd<V><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+        k_fwd<V, 64><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
   }
   for (int l = F.nlev - 1; l >= 0; l--) {
@@ -855,7 +863,8 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
                                                            F.bwd_rows, F.bfin_tasks, F.bwd_counters);
       else
         k_bwd_partial_c128<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                            F.bwd_rows, F.bfin_tasks, F.bwd_counters);
+                                                            F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows,
+                                                            F.bfin_tasks, F.bwd_counters);
     }
   }
 }

@@ -294,18 +294,39 @@ def _graded_z(model, nzH):
     return np.interp(np.linspace(0.0, tau[-1], nzH + 1), tau, zz)
 
 
-def overthrust_problem(seed=0, freq=5.0, cells=(50, 50, 12), order=2, nsub=64, overlap=2,
+def overthrust_cells(freq, coarse_elems_per_wavelength=1.25):
+    """Coarse cell counts (nx, ny, nz) for frequency ``freq``, with
+    ``coarse_elems_per_wavelength`` coarse element edges per local wavelength (the
+    fine mesh, its uniform refinement, has twice as many).
+
+    The experiments section meshes with element edges of 1/5 of the local wavelength
+    on the fine mesh and 1/2.5 on the coarse one (``coarse_elems_per_wavelength =
+    2.5``; its 22M-dof Cartesian grid at 5 Hz fits that reading).  The default 1.25
+    is half that resolution: the one at which the 5 Hz workload has about 2M dofs.
+    A tensor grid cannot follow the local wavelength laterally, so x and y resolve
+    the slowest velocity (2 km/s); in depth the spacing is graded at equal travel
+    time through the mean profile, so nz follows the vertical travel time.  The
+    default gives (63, 63, 9) at 5 Hz (2.37M fine P2 dofs), the paper's resolution
+    the same cells at 2.5 Hz."""
+    lam = 2.0 / freq
+    nxy = int(np.ceil(OVT_X * coarse_elems_per_wavelength / lam - 1e-9))
+    tau = (OVT_Z / 8.0) * float(np.sum(1.0 / np.linspace(2.0, 6.0, 8)))
+    nz = max(2, int(np.ceil(coarse_elems_per_wavelength * tau * freq - 1e-9)))
+    return (nxy, nxy, nz)
+
+
+def overthrust_problem(seed=0, freq=5.0, cells=None, order=2, nsub=64, overlap=2,
                        levels=2, restart=50, tol=1e-6, Q=100.0, sources=None,
                        part_jitter=0.0):
     """Overthrust-shaped 20 x 20 x 4.65 km model meshed for frequency ``freq``.
 
-    ``cells`` are the COARSE cell counts (nx, ny, nz); the fine mesh halves
-    every interval, so at the default 50 x 50 x 12 the fine P2 space holds
-    201 x 201 x 49 = 1.98M dofs (the 5 Hz configuration: about 4 P2 elements
-    per wavelength at 4 km/s laterally, graded in depth with the mean
-    velocity).  ``part_jitter`` > 0 draws uneven part weights in
-    [1 - j, 1 + j].
+    ``cells`` are the COARSE cell counts (nx, ny, nz), by default
+    ``overthrust_cells(freq)``; the fine mesh halves every interval, so at 5 Hz the
+    fine P2 space holds 253 x 253 x 37 = 2.37M dofs.  ``part_jitter`` > 0 draws
+    uneven part weights in [1 - j, 1 + j].
     """
+    if cells is None:
+        cells = overthrust_cells(freq)
     model = OverthrustModel(seed=seed, Q=Q)
     nxH, nyH, nzH = cells
     xH = np.linspace(0.0, OVT_X, nxH + 1)
