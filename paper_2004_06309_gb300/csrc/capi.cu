@@ -1606,6 +1606,26 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CU(cudaGetLastError());
+  if (const char* vb = std::getenv("HZ_VERBOSE"); vb && std::atoi(vb) >= 2) {
+    // diagnostics: live time of every tree level of the local sweeps (one run)
+    hz::FactorDev& F = c->loc;
+    std::vector<cudaEvent_t> ev(size_t(2 * F.nlev + 1));
+    for (auto& e : ev) cudaEventCreate(&e);
+    F.level_events = ev.data();
+    hz::launch_solve(F, st);
+    F.level_events = nullptr;
+    cudaStreamSynchronize(st);
+    for (int q = 0; q < 2 * F.nlev; q++) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev[size_t(q)], ev[size_t(q) + 1]);
+      const bool fw = q < F.nlev;
+      const int l = fw ? q : 2 * F.nlev - 1 - q;
+      const int64_t nt = fw ? F.h_fwd_ptr[l + 1] - F.h_fwd_ptr[l] : F.h_bwd_ptr[l + 1] - F.h_bwd_ptr[l];
+      std::fprintf(stderr, "[hz] local %s level %3d: %6lld tasks %9.1f us\n", fw ? "fwd" : "bwd", l, (long long)nt,
+                   1e3 * ms);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
   // algorithmic bytes and flops
   const double nnz = double(c->nnz), dn = double(n);
   out->bytes[HZ_PH_SPMV] = nnz * (nt + 4) + (dn + 1) * 8 + 2 * dn * nt;

@@ -59,6 +59,7 @@ struct FactorDev {
   int64_t* h_cb_ptr = nullptr;
   int64_t* h_ea_ptr = nullptr;        // nlev * maxslot + 1, grouped (level, slot)
   int64_t* h_ent_ptr = nullptr;       // nlev + 1: entries of each level's fronts
+  cudaEvent_t* level_events = nullptr;  // optional (diagnostics): 2 * nlev + 1 events around sweep levels
   int* h_fwd_rt = nullptr;            // nlev: complex128 forward task rows (16 or 64)
   int* h_bwd_rows = nullptr;          // nlev: complex128 backward chunk rows
   int32_t max_slot = 0;

@@ -842,6 +842,7 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
   V* x = (V*)F.x_loc;
   V* u = (V*)F.u_ws;
   V* part = (V*)F.bwd_partial;
+  if (F.level_events) cudaEventRecord(F.level_events[0], st);
   for (int l = 0; l < F.nlev; l++) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
@@ -853,6 +854,7 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       else
         k_fwd<V, 64><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
+    if (F.level_events) cudaEventRecord(F.level_events[1 + l], st);
   }
   for (int l = F.nlev - 1; l >= 0; l--) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
@@ -866,6 +868,7 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
                                                             F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows,
                                                             F.bfin_tasks, F.bwd_counters);
     }
+    if (F.level_events) cudaEventRecord(F.level_events[1 + F.nlev + (F.nlev - 1 - l)], st);
   }
 }
 
