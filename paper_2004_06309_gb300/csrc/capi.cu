@@ -273,20 +273,24 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
       cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1), tc_ptr(nlev + 1);
   int64_t scratch = 0;
-  // complex128 sweeps: levels with fewer tasks than two per SM get narrow tasks
-  // (16-row forward tasks, 64-row backward chunks) so that they reach every SM
-  std::vector<int> fwd_rt(nlev, precision == 0 ? 64 : 256), lev_bwd_rows(nlev, bwd_rows);
-  if (precision == 0)
-    for (int l = 0; l < nlev; l++) {
-      int64_t nf = 0, nbk = 0;
-      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
-        const int s = S.lev_sn[q];
-        nf += (S.sn_m[s] + 63) / 64;
-        nbk += int64_t((S.sn_k[s] + 31) / 32) * ((S.sn_m[s] + bwd_rows - 1) / bwd_rows);
-      }
-      if (nf < 2 * 152) fwd_rt[l] = 16;
-      if (nbk < 2 * 152) lev_bwd_rows[l] = std::min(bwd_rows, 64);
+  // Sparse tree levels get narrow tasks.  complex128 (FP64 arithmetic bound): fewer
+  // tasks than two per SM -> 16-row forward tasks, 64-row backward chunks, so that such a
+  // level reaches every SM.  complex64: fewer tasks than one resident wave (8 CTAs per
+  // SM) -> 64-row forward tasks and 128-row backward chunks, which shorten each task's
+  // serial walk over its columns and rows (the time of a latency-bound level).
+  const int wide = precision == 0 ? 64 : 256;
+  std::vector<int> fwd_rt(nlev, wide), lev_bwd_rows(nlev, bwd_rows);
+  for (int l = 0; l < nlev; l++) {
+    int64_t nf = 0, nbk = 0;
+    for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+      const int s = S.lev_sn[q];
+      nf += (S.sn_m[s] + wide - 1) / wide;
+      nbk += int64_t((S.sn_k[s] + 31) / 32) * ((S.sn_m[s] + bwd_rows - 1) / bwd_rows);
     }
+    const int64_t sparse = precision == 0 ? 2 * 152 : 8 * 152;
+    if (nf < sparse) fwd_rt[l] = precision == 0 ? 16 : 64;
+    if (nbk < sparse) lev_bwd_rows[l] = std::min(bwd_rows, precision == 0 ? 64 : 128);
+  }
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
     fwd_ptr[l] = int64_t(fwd.size());
@@ -381,12 +385,10 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_tc_ptr = hcopy(tc_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
   F.h_ent_ptr = hcopy(S.ent_ptr);
-  if (precision == 0) {
-    F.h_fwd_rt = new int[nlev];
-    F.h_bwd_rows = new int[nlev];
-    std::copy(fwd_rt.begin(), fwd_rt.end(), F.h_fwd_rt);
-    std::copy(lev_bwd_rows.begin(), lev_bwd_rows.end(), F.h_bwd_rows);
-  }
+  F.h_fwd_rt = new int[nlev];
+  F.h_bwd_rows = new int[nlev];
+  std::copy(fwd_rt.begin(), fwd_rt.end(), F.h_fwd_rt);
+  std::copy(lev_bwd_rows.begin(), lev_bwd_rows.end(), F.h_bwd_rows);
   // batched sweeps for nrhs_block right-hand sides (pseudo-block FGMRES)
   if (nrhs_block > 1) {
     F.mS = nrhs_block;
@@ -1607,24 +1609,28 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   cudaEventDestroy(e1);
   CU(cudaGetLastError());
   if (const char* vb = std::getenv("HZ_VERBOSE"); vb && std::atoi(vb) >= 2) {
-    // diagnostics: live time of every tree level of the local sweeps (one run)
-    hz::FactorDev& F = c->loc;
-    std::vector<cudaEvent_t> ev(size_t(2 * F.nlev + 1));
-    for (auto& e : ev) cudaEventCreate(&e);
-    F.level_events = ev.data();
-    hz::launch_solve(F, st);
-    F.level_events = nullptr;
-    cudaStreamSynchronize(st);
-    for (int q = 0; q < 2 * F.nlev; q++) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, ev[size_t(q)], ev[size_t(q) + 1]);
-      const bool fw = q < F.nlev;
-      const int l = fw ? q : 2 * F.nlev - 1 - q;
-      const int64_t nt = fw ? F.h_fwd_ptr[l + 1] - F.h_fwd_ptr[l] : F.h_bwd_ptr[l + 1] - F.h_bwd_ptr[l];
-      std::fprintf(stderr, "[hz] local %s level %3d: %6lld tasks %9.1f us\n", fw ? "fwd" : "bwd", l, (long long)nt,
-                   1e3 * ms);
+    // diagnostics: live time of every tree level of the local and coarse sweeps (one run)
+    for (hz::FactorDev* Fp : {&c->loc, &c->crs}) {
+      hz::FactorDev& F = *Fp;
+      if (F.nsn == 0) continue;
+      const char* name = Fp == &c->loc ? "local" : "coarse";
+      std::vector<cudaEvent_t> ev(size_t(2 * F.nlev + 1));
+      for (auto& e : ev) cudaEventCreate(&e);
+      F.level_events = ev.data();
+      hz::launch_solve(F, st);
+      F.level_events = nullptr;
+      cudaStreamSynchronize(st);
+      for (int q = 0; q < 2 * F.nlev; q++) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[size_t(q)], ev[size_t(q) + 1]);
+        const bool fw = q < F.nlev;
+        const int l = fw ? q : 2 * F.nlev - 1 - q;
+        const int64_t nt = fw ? F.h_fwd_ptr[l + 1] - F.h_fwd_ptr[l] : F.h_bwd_ptr[l + 1] - F.h_bwd_ptr[l];
+        std::fprintf(stderr, "[hz] %s %s level %3d: %6lld tasks %9.1f us\n", name, fw ? "fwd" : "bwd", l,
+                     (long long)nt, 1e3 * ms);
+      }
+      for (auto& e : ev) cudaEventDestroy(e);
     }
-    for (auto& e : ev) cudaEventDestroy(e);
   }
   // algorithmic bytes and flops
   const double nnz = double(c->nnz), dn = double(n);

@@ -723,19 +723,24 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
   bwd_finish<double2>(fins[t.w], S, zin, partial, x, counters + t.w);
 }
 
-// complex64 forward, 256 rows of one supernode per task: thread t owns the row pair
-// (2p, 2p+1), p = t % 128, for the pivot columns of parity t / 128, with 16-byte
-// loads; the right-hand side b1 is gathered once per 256 rows.
-constexpr int kFwdRowsC64 = 256;
+// complex64 forward, 512 / CG rows of one supernode per task: thread t owns the row
+// pair (2p, 2p+1), p = t % (256 / CG), for the pivot columns j = t / (256 / CG) mod CG,
+// with 16-byte loads; the right-hand side b1 is gathered once per task.  CG = 2 (256
+// rows) where a tree level has many supernodes; CG = 8 (64 rows, each warp one column
+// group) on sparse levels, where a task's serial walk over its columns, not bandwidth,
+// sets the time.
+template <int CG>
 __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                                  const int64_t* cidx, const float2* panels, const float2* tin,
                                                  float2* zout, float2* u) {
+  constexpr int NP = 256 / CG;                       // row pairs per task
+  constexpr int ROWS = 2 * NP;
   __shared__ float2 b1[kMaxK];
-  __shared__ float2 part[2][kFwdRowsC64];
+  __shared__ float2 part[CG][ROWS];
   const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
-  const int pr = tid & 127, cg = tid >> 7;
+  const int pr = tid % NP, cg = tid / NP;
   const int64_t* cp = cptr + S.rowoff;
   for (int jj = tid; jj < k; jj += blockDim.x) {
     float2 acc = tin[S.first + jj];
@@ -743,21 +748,21 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
     b1[jj] = acc;
   }
   __syncthreads();
-  const int r = t.y * kFwdRowsC64 + 2 * pr;          // rows r, r + 1 (r even, ld % 4 == 0)
+  const int r = t.y * ROWS + 2 * pr;                 // rows r, r + 1 (r even, ld % 4 == 0)
   float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
   if (r < m) {
     const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
     const int64_t ld4 = S.ld / 2;
     const int j0 = min(r, k), j1 = min(r + 1, k);
     int j = cg;
-    for (; j + 2 < j1; j += 4) {                       // two independent chains
+    for (; j + CG < j1; j += 2 * CG) {                 // two independent chains
       const float4 p = P4[int64_t(j) * ld4];
-      const float4 q = P4[int64_t(j + 2) * ld4];
-      const float2 bj = b1[j], bq = b1[j + 2];
+      const float4 q = P4[int64_t(j + CG) * ld4];
+      const float2 bj = b1[j], bq = b1[j + CG];
       a1 = cmad(make_float2(p.z, p.w), bj, a1);
       c1 = cmad(make_float2(q.z, q.w), bq, c1);
       if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
-      if (j + 2 < j0) c0 = cmad(make_float2(q.x, q.y), bq, c0);
+      if (j + CG < j0) c0 = cmad(make_float2(q.x, q.y), bq, c0);
     }
     if (j < j1) {
       const float4 p = P4[int64_t(j) * ld4];
@@ -769,9 +774,11 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
   part[cg][2 * pr] = cadd(a0, c0);
   part[cg][2 * pr + 1] = cadd(a1, c1);
   __syncthreads();
-  const int rr = t.y * kFwdRowsC64 + tid;
-  if (rr < m) {
-    const float2 tot = cadd(part[0][tid], part[1][tid]);
+  const int rr = t.y * ROWS + tid;
+  if (tid < ROWS && rr < m) {
+    float2 tot = part[0][tid];
+#pragma unroll
+    for (int q = 1; q < CG; q++) tot = cadd(tot, part[q][tid]);
     const float2* P = panels + S.paneloff;
     if (rr < k) {
       zout[S.first + rr] = cmul(P[rr + int64_t(rr) * S.ld], cadd(b1[rr], tot));
@@ -847,9 +854,12 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
-      if constexpr (sizeof(V) == 8)
-        k_fwd_c64<<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
-      else if (F.h_fwd_rt && F.h_fwd_rt[l] == 16)
+      if constexpr (sizeof(V) == 8) {
+        if (F.h_fwd_rt && F.h_fwd_rt[l] == 64)
+          k_fwd_c64<8><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+        else
+          k_fwd_c64<2><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+      } else if (F.h_fwd_rt && F.h_fwd_rt[l] == 16)
         k_fwd<V, 16><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
       else
         k_fwd<V, 64><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
@@ -862,7 +872,8 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       HZ_COUNT();
       if constexpr (sizeof(V) == 8)
         k_bwd_partial_c64<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                           F.bwd_rows, F.bfin_tasks, F.bwd_counters);
+                                                           F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows,
+                                                           F.bfin_tasks, F.bwd_counters);
       else
         k_bwd_partial_c128<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
                                                             F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows,
