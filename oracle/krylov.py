@@ -103,3 +103,160 @@ def fgmres(apply_A, apply_M, b, tol=1e-6, m=30, maxit=1000, history=None, verify
         if its >= maxit:
             return x, its, rel, False
         beta = np.linalg.norm(r)
+
+
+# ---------------------------------------------------------------------------
+# GCRO-DR: GMRES with deflated restarting and subspace recycling (Parks, de Sturler,
+# Mackey, Johnson, Maiti 2006), the Krylov-recycling method the paper names as its
+# next step for many right-hand sides.  Right preconditioning with a fixed M: the
+# iteration runs on A M^{-1} in the preconditioned space, and a recycled space is
+# kept in both spaces, Uh (preconditioned) and Ux = M^{-1} Uh, with C = A Ux,
+# C^H C = I.  Per cycle:
+#   * r is made orthogonal to C (x += Ux C^H r, r -= C C^H r);
+#   * Arnoldi on (I - C C^H) A M^{-1}: each new vector is orthogonalised against
+#     [C, V] by CGS2; the C coefficients form B, the V ones the Hessenberg H;
+#   * the least-squares problem min || [0; beta e1] - [[D, B], [0, H]] [y1; y2] ||
+#     splits: y2 by Givens on H (as in fgmres), y1 = -D^{-1} B y2, so that
+#     x += Z y2 - Ux (B y2) (D scales Uh to unit columns);
+#   * at the cycle end, if the true residual misses tol, k harmonic Ritz vectors
+#     (smallest |theta|) of the cycle's space become the new recycled space:
+#       first cycle:  (H_m + |h_{m+1,m}|^2 H_m^{-H} e_m e_m^H) z = theta z,
+#       later:        G^H G z = theta G^H (Vh^H Wh) z,  G = [[D, B], [0, H]],
+#                     Vh = [C, V_{p+1}],  Wh = [Uh D, V_p];
+#     with P their eigenvectors: [Q, R] = qr(G P), C = Vh Q, Uh = Wh P R^{-1},
+#     Ux = Wx P R^{-1} (Wx = [Ux D, Z_p]).
+# A recycled space passed in (from the previous right-hand side at the same A and
+# M) is used from the first cycle on; cycles hold m vectors in all (k recycled,
+# m - k new).  Convergence and iteration counting follow fgmres.
+# ---------------------------------------------------------------------------
+def _arnoldi_cycle(apply_A, apply_M, r, beta, C, p, bnorm, tol, its, maxit, history):
+    n = r.shape[0]
+    kk = 0 if C is None else C.shape[1]
+    V = np.zeros((n, p + 1), np.complex128)
+    Zs = np.zeros((n, p), np.complex128)
+    H = np.zeros((p + 1, p), np.complex128)
+    B = np.zeros((kk, p), np.complex128)
+    R = np.zeros((p + 1, p), np.complex128)          # Givens-rotated copy of H
+    cs = np.zeros(p)
+    sn = np.zeros(p, np.complex128)
+    g = np.zeros(p + 1, np.complex128)
+    g[0] = beta
+    V[:, 0] = r / beta
+    k = 0
+    for j in range(p):
+        Zs[:, j] = apply_M(V[:, j])
+        w = apply_A(Zs[:, j])
+        w0 = np.linalg.norm(w)
+        Q = V[:, : j + 1] if kk == 0 else np.hstack([C, V[:, : j + 1]])
+        h1 = Q.conj().T @ w
+        w = w - Q @ h1
+        h2 = Q.conj().T @ w
+        w = w - Q @ h2
+        h = h1 + h2
+        hn = np.linalg.norm(w)
+        B[:, j] = h[:kk]
+        H[: j + 1, j] = h[kk:]
+        H[j + 1, j] = hn
+        col = H[: j + 2, j].copy()
+        for i in range(j):
+            t = cs[i] * col[i] + sn[i] * col[i + 1]
+            col[i + 1] = -np.conj(sn[i]) * col[i] + cs[i] * col[i + 1]
+            col[i] = t
+        cs[j], sn[j] = givens(col[j], col[j + 1])
+        col[j] = cs[j] * col[j] + sn[j] * col[j + 1]
+        col[j + 1] = 0.0
+        R[: j + 2, j] = col
+        g[j + 1] = -np.conj(sn[j]) * g[j]
+        g[j] = cs[j] * g[j]
+        its += 1
+        k = j + 1
+        est = abs(g[j + 1]) / bnorm
+        if history is not None:
+            history.append(est)
+        if hn > 0.0:
+            V[:, j + 1] = w / hn          # kept even at the last step: it spans A Z with V
+        if hn <= 1e-14 * w0 or est <= tol or its >= maxit:
+            break
+    y = np.zeros(k, np.complex128)
+    for i in range(k - 1, -1, -1):
+        y[i] = (g[i] - R[i, i + 1: k] @ y[i + 1: k]) / R[i, i]
+    return V[:, : k + 1], Zs[:, :k], H[: k + 1, :k], B[:, :k], y, its
+
+
+def _smallest_harmonic(Mat_a, Mat_b, k):
+    """Eigenvectors of Mat_a z = theta Mat_b z for the k smallest |theta|."""
+    import scipy.linalg as sla
+    th, Z = sla.eig(Mat_a, Mat_b)
+    th = np.where(np.isfinite(th), th, np.inf)
+    order = np.argsort(np.abs(th), kind="stable")
+    return Z[:, order[:k]]
+
+
+def gcrodr(apply_A, apply_M, b, tol=1e-6, m=50, k=10, recycle=None, maxit=1000, history=None):
+    """Solve A x = b.  Returns (x, iterations, true relative residual, converged, recycle)
+    where recycle = (Ux, Uh, C) for the next right-hand side at the same A and M."""
+    b = np.asarray(b, np.complex128)
+    n = b.shape[0]
+    bnorm = np.linalg.norm(b)
+    x = np.zeros(n, np.complex128)
+    if bnorm == 0.0:
+        return x, 0, 0.0, True, recycle
+    Ux = Uh = C = None
+    if recycle is not None:
+        Ux, Uh, C = recycle
+    r = b.copy()
+    its = 0
+    while True:
+        if C is not None:                                   # r orthogonal to C
+            c = C.conj().T @ r
+            x = x + Ux @ c
+            r = r - C @ c
+        beta = np.linalg.norm(r)
+        p = m if C is None else m - C.shape[1]
+        V, Zs, H, B, y, its = _arnoldi_cycle(apply_A, apply_M, r, beta, C, p, bnorm, tol, its, maxit,
+                                             history)
+        kc = y.shape[0]
+        x = x + Zs @ y
+        if C is not None:
+            x = x - Ux @ (B @ y)
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bnorm
+        # new recycled space from this cycle (kept for the next right-hand side as well)
+        if C is None:
+            Ux, Uh, C = _first_recycle(V, Zs, H, kc, k)
+        else:
+            kk = C.shape[1]
+            dn = 1.0 / np.linalg.norm(Uh, axis=0)
+            D = np.diag(dn)
+            G = np.zeros((kk + kc + 1, kk + kc), np.complex128)
+            G[:kk, :kk] = D
+            G[:kk, kk:] = B
+            G[kk:, kk:] = H
+            Vh = np.hstack([C, V])
+            Wh = np.hstack([Uh * dn, V[:, :kc]])
+            Wx = np.hstack([Ux * dn, Zs])
+            P = _smallest_harmonic(G.conj().T @ G, G.conj().T @ (Vh.conj().T @ Wh), min(k, kk + kc))
+            Q, Rq = np.linalg.qr(G @ P)
+            Rinv = np.linalg.inv(Rq)
+            C = Vh @ Q
+            Uh = Wh @ P @ Rinv
+            Ux = Wx @ P @ Rinv
+        if rel <= tol or its >= maxit:
+            return x, its, rel, rel <= tol, (Ux, Uh, C)
+
+
+def _first_recycle(V, Zs, H, kc, k):
+    """Recycled space from a plain GMRES cycle: harmonic Ritz vectors of H_m."""
+    Hm = H[:kc, :kc]
+    hl = H[kc, kc - 1]
+    em = np.zeros(kc, np.complex128)
+    em[-1] = 1.0
+    f = np.linalg.solve(Hm.conj().T, em)
+    Mh = Hm + (abs(hl) ** 2) * np.outer(f, em)
+    P = _smallest_harmonic(Mh, np.eye(kc), min(k, kc))
+    Q, Rq = np.linalg.qr(H @ P)
+    Rinv = np.linalg.inv(Rq)
+    C = V @ Q
+    Uh = V[:, :kc] @ P @ Rinv
+    Ux = Zs @ P @ Rinv
+    return Ux, Uh, C

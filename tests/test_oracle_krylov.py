@@ -60,3 +60,97 @@ def test_exact_preconditioner_is_one_iteration():
     Ainv = np.linalg.inv(A)
     x, it, rel, ok = krylov.fgmres(lambda v: A @ v, lambda v: Ainv @ v, b, tol=1e-8, m=10)
     assert ok and it == 1
+
+
+# --- GCRO-DR (Krylov recycling) ---------------------------------------------
+
+def _dense(n, seed, spread=1.0):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 3 + spread * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    return A
+
+
+def test_gcrodr_without_recycling_is_fgmres():
+    rng = np.random.default_rng(2)
+    n = 80
+    A = _dense(n, 3)
+    M = np.diag(1.0 / np.diag(A))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x1, i1, r1, ok1 = krylov.fgmres(lambda v: A @ v, lambda v: M @ v, b, tol=1e-10, m=12)
+    x2, i2, r2, ok2, rec = krylov.gcrodr(lambda v: A @ v, lambda v: M @ v, b, tol=1e-10, m=12, k=0)
+    assert ok1 and ok2 and i1 == i2
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
+
+
+def test_recycled_space_invariants():
+    """C = A Ux with orthonormal C, and Ux = M^{-1} Uh, after a solve and after a second
+    one that reuses and updates the space (a wrong G, B or index breaks these)."""
+    rng = np.random.default_rng(4)
+    n = 90
+    A = _dense(n, 5, spread=2.0)
+    Minv = np.linalg.inv(np.diag(np.diag(A)) + 0.3 * np.eye(n))
+    rec = None
+    for _ in range(2):
+        b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        x, it, rel, ok, rec = krylov.gcrodr(lambda v: A @ v, lambda v: Minv @ v, b, tol=1e-9, m=14, k=5,
+                                            recycle=rec)
+        assert ok and np.linalg.norm(b - A @ x) <= 1e-9 * np.linalg.norm(b)
+        Ux, Uh, C = rec
+        assert np.abs(C.conj().T @ C - np.eye(C.shape[1])).max() <= 1e-12
+        assert np.abs(A @ Ux - C).max() <= 1e-12 * np.abs(C).max()
+        assert np.abs(Minv @ Uh - Ux).max() <= 1e-12 * np.abs(Ux).max()
+
+
+def test_harmonic_ritz_space_is_invariant_when_the_cycle_spans_everything():
+    """With m >= n the first cycle's Krylov space is the whole space, the harmonic Ritz
+    pairs are exact eigenpairs, and the recycled space is the span of the k eigenvectors
+    of A M^{-1} with the smallest |eigenvalue| (checked against numpy's eigensolver)."""
+    rng = np.random.default_rng(6)
+    n = 10
+    lam = np.array([0.05, 0.1, 0.2, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0]) * (1 + 0.1j)
+    X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = X @ np.diag(lam) @ np.linalg.inv(X)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, it, rel, ok, rec = krylov.gcrodr(lambda v: A @ v, lambda v: v, b, tol=1e-12, m=n, k=3)
+    Ux, Uh, C = rec
+    ev, EV = np.linalg.eig(A)
+    small = EV[:, np.argsort(np.abs(ev))[:3]]
+    Qs, _ = np.linalg.qr(small)
+    Qu, _ = np.linalg.qr(Uh)
+    # the two 3-dimensional subspaces coincide: singular values of Qs^H Qu are all 1
+    sv = np.linalg.svd(Qs.conj().T @ Qu, compute_uv=False)
+    assert np.all(np.abs(sv - 1.0) <= 1e-8), sv
+
+
+def test_deflated_restarting_beats_plain_restarting_on_small_outliers():
+    """A few eigenvalues near zero stall restarted GMRES; GCRO-DR(m, k) deflates them
+    across restarts and needs fewer iterations (the method's reason to exist)."""
+    rng = np.random.default_rng(7)
+    n = 200
+    lam = np.concatenate([[1e-3, 2e-3, 4e-3, 8e-3], rng.uniform(1.0, 2.0, n - 4)]).astype(np.complex128)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    A = Q @ np.diag(lam) @ Q.conj().T
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    xf, itf, rf, okf = krylov.fgmres(lambda v: A @ v, lambda v: v, b, tol=1e-8, m=10, maxit=3000)
+    xg, itg, rg, okg, _ = krylov.gcrodr(lambda v: A @ v, lambda v: v, b, tol=1e-8, m=10, k=4, maxit=3000)
+    assert okg and rg <= 1e-8
+    assert itg < itf, (itg, itf)
+
+
+def test_recycling_helps_the_next_right_hand_side():
+    import synth
+    from oracle.solver import OracleSolver
+    p = synth.tiny_problem()
+    S = OracleSolver(p)
+    S.factor()
+    ext = p.mesh.xyz.max(axis=0)
+    B = S.rhs(np.array([[0.2, 0.3, 0.3], [0.7, 0.2, 0.5], [0.3, 0.8, 0.6]]) * ext)
+    rec = None
+    its_rec, its_plain = [], []
+    for j in range(B.shape[1]):
+        x, it, rel, ok, rec = krylov.gcrodr(S.apply_A, S.apply_M, B[:, j], tol=1e-6, m=20, k=8, recycle=rec)
+        assert ok and np.linalg.norm(B[:, j] - S.A @ x) <= 1e-6 * np.linalg.norm(B[:, j])
+        its_rec.append(it)
+        its_plain.append(krylov.fgmres(S.apply_A, S.apply_M, B[:, j], tol=1e-6, m=20)[1])
+    assert its_rec[0] == its_plain[0]                 # nothing recycled yet
+    assert sum(its_rec[1:]) < sum(its_plain[1:]), (its_rec, its_plain)
