@@ -374,6 +374,8 @@ def main():
                     help="coarse solve: direct LDL^T of E, or inner GMRES with coarse one-level ORAS")
     ap.add_argument("--coarse-tol", type=float, default=0.0, help="inner coarse tolerance (0: library default)")
     ap.add_argument("--coarse-maxit", type=int, default=0, help="inner coarse iterations at most (0: default)")
+    ap.add_argument("--recycle", type=int, default=0,
+                    help="GCRO-DR: recycled-space dimension kept across the step's right-hand sides (0: FGMRES)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -450,7 +452,7 @@ def main():
         G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream,
                       leaf_size=args.leaf, max_snode=args.maxsn, block_size=args.block,
                       coarse_solver=hz.HZ_COARSE_ORAS if args.coarse == "oras" else hz.HZ_COARSE_DIRECT,
-                      coarse_tol=args.coarse_tol, coarse_maxit=args.coarse_maxit)
+                      coarse_tol=args.coarse_tol, coarse_maxit=args.coarse_maxit, recycle=args.recycle)
         tf = time.time()
         G.factor()
         torch.cuda.synchronize()
@@ -542,7 +544,7 @@ def main():
         "config": {"workload": args.workload, "n_dofs": n, "nsub": prob.nsub, "overlap": prob.overlap,
                    "levels": 2 if prob.levels == 2 else 1, "restart": prob.restart, "tol": 1e-6,
                    "rhs_per_step": args.nrhs, "block_size": args.block, "freq_hz": prob.freq,
-                   "coarse_solver": args.coarse,
+                   "coarse_solver": args.coarse, "recycle": args.recycle,
                    "l2": "inputs larger than L2 (factors >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "iterations": R["iterations"][-1], "rel_residual": R["rel"],

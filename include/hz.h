@@ -116,6 +116,14 @@ typedef struct {
                                1..63 (0: 30)                                          */
   double coarse_tol;        /* HZ_COARSE_ORAS: inner relative residual estimate
                                (0: 1e-2)                                              */
+  int32_t recycle;          /* GCRO-DR Krylov recycling (the experiments section names
+                               it as the next step for many right-hand sides): keep a
+                               recycled space of this dimension k across cycles and
+                               across right-hand sides of hz_solve, renewed from
+                               harmonic Ritz vectors at every cycle end; cycles then
+                               add restart - k Arnoldi vectors.  hz_factor drops the
+                               space.  0 = off (FGMRES); 1 <= k <= min(16, restart/2);
+                               one right-hand side at a time (block_size <= 1).      */
 } hz_options;
 
 typedef struct {
@@ -145,6 +153,7 @@ typedef struct {
   int64_t launches;         /* kernel launches issued by the library in this process */
   int64_t coarse_solves;    /* iterative coarse solve: inner solves since hz_factor    */
   int64_t coarse_iterations;/* ... and their inner GMRES iterations in total           */
+  int64_t recycle_dim;      /* GCRO-DR: dimension of the recycled space held now       */
 } hz_stats;
 
 /* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */

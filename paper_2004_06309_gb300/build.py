@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "symbolic.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "server.cpp"]
-HEADERS = ["host.h", "dev.h", "engine.h"]
+SOURCES = ["setup.cpp", "symbolic.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "server.cpp", "recycle.cpp"]
+HEADERS = ["host.h", "dev.h", "engine.h", "small_la.h"]
 
 
 def _nvcc():
@@ -65,7 +65,7 @@ def build(force=False, verbose=False):
             if verbose and out:
                 print(out)
     tmp = LIB + ".tmp"
-    run([_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lpthread"])
+    run([_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lpthread", "-lcusolver"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -15,6 +15,7 @@
 #include "dev.h"
 #include "engine.h"
 #include "host.h"
+#include "small_la.h"
 
 using hz::cplx;
 
@@ -59,8 +60,15 @@ struct hz_ctx {
   double2 *H = nullptr, *sn = nullptr, *g = nullptr, *ysol = nullptr;
   double *cs = nullptr, *scal = nullptr;   // scal: est, invh, invbeta, beta, |b|
   // one CUDA graph per inner-iteration index j (captured on first use)
-  std::vector<cudaGraphExec_t> gexec;
+  std::vector<cudaGraphExec_t> gexec;     // index j + restart * (recycled dimension)
   std::vector<long long> gcount;
+  // GCRO-DR recycling (options.recycle = rk > 0): the recycled space C sits right before
+  // the Arnoldi basis, in columns [rk - rdim, rk) of Vx (V = Vx + rk n), so that [C, V]
+  // is one column-major block for CGS2
+  int rk = 0, rdim = 0, ckk = 0;
+  double2 *Vx = nullptr, *Ux = nullptr, *Uh = nullptr, *Ctmp = nullptr, *Uxt = nullptr, *Uht = nullptr;
+  double2 *Hraw = nullptr, *Braw = nullptr, *dcoef = nullptr;
+  hz_small::EigSolver eig;
   bool graphs = true;
   int spmv_lanes = 0;                      // autotuned at the first hz_factor (0: not yet)
   int* brk = nullptr;
@@ -627,14 +635,17 @@ void iteration_kernels(hz_ctx* c, int j) {
   double2* zj = c->Zs + int64_t(j) * n;
   apply_prec(c, vj, zj);
   hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, zj, nullptr, c->w, st);
-  hz::launch_cgs(n, j + 1, c->V, n, nullptr, c->w, j + 1, c->partial, st);   // h1, |w|
-  hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
-  hz::launch_cgs(n, j + 1, c->V, n, c->h1, c->w, j + 1, c->partial, st);     // w -= V h1; h2
-  hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
-  hz::launch_cgs(n, j + 1, c->V, n, c->h2, c->w, 0, c->partial, st);         // w -= V h2; |w|
+  // orthogonalise against [C, v_0..v_j] (C: the recycled space, empty without recycling)
+  const int kk = c->ckk, nc = kk + j + 1;
+  const double2* base = c->V - int64_t(kk) * n;
+  hz::launch_cgs(n, nc, base, n, nullptr, c->w, nc, c->partial, st);        // h1, |w|
+  hz::launch_reduce(c->partial, nb, nc, c->h1, st);
+  hz::launch_cgs(n, nc, base, n, c->h1, c->w, nc, c->partial, st);          // w -= [C V] h1; h2
+  hz::launch_reduce(c->partial, nb, nc, c->h2, st);
+  hz::launch_cgs(n, nc, base, n, c->h2, c->w, 0, c->partial, st);           // w -= [C V] h2; |w|
   hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
   hz::launch_givens(j, m, c->H, c->cs, c->sn, c->g, c->h1, c->h2, c->nrm, c->scal + 4, c->scal, c->brk,
-                    c->scal + 1, st);
+                    c->scal + 1, st, kk, c->rk ? c->Hraw : nullptr, c->Braw, c->rk);
   hz::launch_scale(n, c->w, c->scal + 1, c->V + int64_t(j + 1) * n, st);
   cudaMemcpyAsync(c->h_pin, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(c->h_pin + 4, c->brk, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -643,25 +654,26 @@ void iteration_kernels(hz_ctx* c, int j) {
 // Runs iteration j (as a CUDA graph when the stream can be captured) and waits for it.
 hz_status run_iteration(hz_ctx* c, int j) {
   cudaStream_t st = c->st;
+  const size_t gi = size_t(j) + size_t(c->restart) * size_t(c->ckk);
   if (c->graphs && st != nullptr) {
-    if (!c->gexec[j]) {
+    if (!c->gexec[gi]) {
       const long long l0 = hz::launch_count();
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         iteration_kernels(c, j);
         if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) {
-          if (cudaGraphInstantiate(&c->gexec[j], g, 0) != cudaSuccess) c->gexec[j] = nullptr;
+          if (cudaGraphInstantiate(&c->gexec[gi], g, 0) != cudaSuccess) c->gexec[gi] = nullptr;
           cudaGraphDestroy(g);
         }
       }
       cudaGetLastError();
-      c->gcount[j] = hz::launch_count() - l0;
-      hz::add_launches(-c->gcount[j]);          // capture itself launches nothing
-      if (!c->gexec[j]) c->graphs = false;     // this stream cannot be captured: stay eager
+      c->gcount[gi] = hz::launch_count() - l0;
+      hz::add_launches(-c->gcount[gi]);          // capture itself launches nothing
+      if (!c->gexec[gi]) c->graphs = false;     // this stream cannot be captured: stay eager
     }
-    if (c->gexec[j]) {
-      CU(cudaGraphLaunch(c->gexec[j], st));
-      hz::add_launches(c->gcount[j]);
+    if (c->gexec[gi]) {
+      CU(cudaGraphLaunch(c->gexec[gi], st));
+      hz::add_launches(c->gcount[gi]);
       CU(cudaStreamSynchronize(st));
       return HZ_OK;
     }
@@ -736,6 +748,236 @@ hz_status fgmres_one(hz_ctx* c, double tol, hz_rhs_info* info) {
       return HZ_OK;
     }
     // nrm still holds |r|^2 from norm2 for the next cycle
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GCRO-DR (options.recycle = rk > 0): FGMRES with deflated restarting and a recycled
+// Krylov space kept across right-hand sides (Parks et al. 2006; the Krylov-recycling
+// step the paper names for many right-hand sides).  Right preconditioning: the space
+// lives in the preconditioned space (Uh) and in the solution space (Ux = M^{-1} Uh),
+// with C = A Ux, C^H C = I.  Each cycle orthogonalises against [C, V]; the recycled
+// space is renewed at every cycle end from harmonic Ritz vectors, on the host for the
+// small matrices (order <= restart + 1) and on the device for the n-vectors.
+// ---------------------------------------------------------------------------
+using hz_small::cplx;
+
+std::vector<cplx> to_host(const double2* d, size_t count) {
+  std::vector<cplx> h(count);
+  cudaMemcpy(h.data(), d, count * 16, cudaMemcpyDeviceToHost);
+  return h;
+}
+
+// out (+)= sign * ([B1, B2] coef) with a host coefficient matrix.
+void combo(hz_ctx* c, int nb1, const double2* B1, int nb2, const double2* B2, const std::vector<cplx>& coef,
+           int nout, double2* out, double sign, bool acc) {
+  cudaMemcpyAsync(c->dcoef, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice, c->st);
+  hz::launch_combo(c->n, nb1, B1, c->n, nb2, B2, c->n, c->dcoef, nout, out, c->n, sign, acc, c->st);
+  cudaStreamSynchronize(c->st);                      // coef is a host temporary
+}
+
+// Indices of the kn eigenvalues of smallest modulus (stable order).
+std::vector<int> smallest(const std::vector<cplx>& w, int kn) {
+  std::vector<int> idx(w.size());
+  for (size_t i = 0; i < w.size(); i++) idx[i] = int(i);
+  auto key = [&](int a) {
+    const double f = std::abs(w[size_t(a)]);
+    return std::isfinite(f) ? f : 1e300;
+  };
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key(a) < key(b); });
+  idx.resize(size_t(kn));
+  return idx;
+}
+
+// New recycled space from the cycle that just ended (kk recycled vectors in it, kc
+// Arnoldi steps).  On a numerical failure the previous space is kept.
+hz_status recycle_update(hz_ctx* c, int kk, int kc) {
+  const int m = c->restart, rk = c->rk;
+  const int64_t n = c->n;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  if (kc < 1) return HZ_OK;
+  CU(cudaStreamSynchronize(st));
+  const std::vector<cplx> Hr = to_host(c->Hraw, size_t(m + 1) * kc);     // column j at j (m + 1)
+  auto H = [&](int i, int j) { return Hr[size_t(j) * (m + 1) + i]; };
+  const int nt = kk + kc;                                                // columns of G
+  const int kn = std::min(rk, nt);
+  std::vector<cplx> G(size_t(nt + 1) * nt, 0.0), P, w, VR, Mg;
+  std::vector<double> dsc(size_t(kk), 1.0);
+  std::string err;
+  if (kk == 0) {
+    // harmonic Ritz pairs of H_m: (H_m + |h|^2 H_m^{-H} e_m e_m^H) z = theta z
+    std::vector<cplx> Hm(size_t(kc) * kc), HmH(size_t(kc) * kc), f(size_t(kc), 0.0);
+    for (int j = 0; j < kc; j++)
+      for (int i = 0; i < kc; i++) Hm[size_t(j) * kc + i] = H(i, j);
+    for (int j = 0; j < kc; j++)
+      for (int i = 0; i < kc; i++) HmH[size_t(j) * kc + i] = std::conj(Hm[size_t(i) * kc + j]);
+    f[size_t(kc - 1)] = 1.0;
+    if (!hz_small::lu_solve(kc, HmH, f, 1)) return HZ_OK;
+    const double hl2 = std::norm(H(kc, kc - 1));
+    Mg = Hm;
+    for (int i = 0; i < kc; i++) Mg[size_t(kc - 1) * kc + i] += hl2 * f[size_t(i)];
+    for (int j = 0; j < kc; j++)
+      for (int i = 0; i <= kc; i++) G[size_t(j) * (nt + 1) + i] = H(i, j);
+  } else {
+    // G = [[D, B], [0, H]], Vh^H Wh = [[C^H Uh D, 0], [V^H Uh D, I]]:
+    // harmonic Ritz pairs of G^H G z = theta G^H (Vh^H Wh) z
+    const std::vector<cplx> Bh = to_host(c->Braw, size_t(rk) * kc);        // column j at j rk
+    const double2* Cb = c->V - int64_t(kk) * n;
+    std::vector<cplx> VW(size_t(nt + 1) * nt, 0.0);
+    for (int i = 0; i < kk; i++) {
+      double2* ui = c->Uh + int64_t(i) * n;
+      hz::launch_cgs(n, kk + kc + 1, Cb, n, nullptr, ui, kk + kc + 1, c->partial, st);
+      hz::launch_reduce(c->partial, nb, kk + kc + 1, c->h1, st);
+      CU(cudaStreamSynchronize(st));
+      const std::vector<cplx> hv = to_host(c->h1, 65);
+      dsc[size_t(i)] = 1.0 / std::sqrt(hv[64].real());
+      for (int a = 0; a <= nt; a++) VW[size_t(i) * (nt + 1) + a] = hv[size_t(a)] * dsc[size_t(i)];
+    }
+    for (int j = 0; j < kc; j++) VW[size_t(kk + j) * (nt + 1) + kk + j] = 1.0;
+    for (int i = 0; i < kk; i++) G[size_t(i) * (nt + 1) + i] = dsc[size_t(i)];
+    for (int j = 0; j < kc; j++) {
+      for (int i = 0; i < kk; i++) G[size_t(kk + j) * (nt + 1) + i] = Bh[size_t(j) * rk + i];
+      for (int i = 0; i <= kc; i++) G[size_t(kk + j) * (nt + 1) + kk + i] = H(i, j);
+    }
+    std::vector<cplx> Ag(size_t(nt) * nt, 0.0), Bg(size_t(nt) * nt, 0.0);
+    for (int a = 0; a < nt; a++)
+      for (int b = 0; b < nt; b++) {
+        cplx sa = 0, sb = 0;
+        for (int r = 0; r <= nt; r++) {
+          const cplx gra = std::conj(G[size_t(a) * (nt + 1) + r]);
+          sa += gra * G[size_t(b) * (nt + 1) + r];
+          sb += gra * VW[size_t(b) * (nt + 1) + r];
+        }
+        Ag[size_t(b) * nt + a] = sa;
+        Bg[size_t(b) * nt + a] = sb;
+      }
+    Mg = Ag;
+    if (!hz_small::lu_solve(nt, Bg, Mg, nt)) return HZ_OK;
+  }
+  if (!hz_small::eig(c->eig, st, nt, Mg, w, VR, err)) {
+    c->err = err;
+    return HZ_OK;
+  }
+  const std::vector<int> pick = smallest(w, kn);
+  P.assign(size_t(nt) * kn, 0.0);
+  for (int q = 0; q < kn; q++)
+    for (int i = 0; i < nt; i++) P[size_t(q) * nt + i] = VR[size_t(pick[size_t(q)]) * nt + i];
+  std::vector<cplx> GP(size_t(nt + 1) * kn, 0.0), Q, R;
+  for (int q = 0; q < kn; q++)
+    for (int i = 0; i <= nt; i++) {
+      cplx sacc = 0;
+      for (int j = 0; j < nt; j++) sacc += G[size_t(j) * (nt + 1) + i] * P[size_t(q) * nt + j];
+      GP[size_t(q) * (nt + 1) + i] = sacc;
+    }
+  hz_small::qr_thin(nt + 1, kn, GP, Q, R);
+  if (!hz_small::tri_inv_upper(kn, R)) return HZ_OK;
+  // U coefficients: P R^{-1}, recycled rows scaled by D
+  std::vector<cplx> PU(size_t(nt) * kn, 0.0);
+  for (int q = 0; q < kn; q++)
+    for (int i = 0; i < nt; i++) {
+      cplx sacc = 0;
+      for (int r = 0; r <= q; r++) sacc += P[size_t(r) * nt + i] * R[size_t(q) * kn + r];
+      PU[size_t(q) * nt + i] = (i < kk ? dsc[size_t(i)] : 1.0) * sacc;
+    }
+  const double2* Cb = c->V - int64_t(kk) * n;
+  combo(c, kk, Cb, kc + 1, c->V, Q, kn, c->Ctmp, 1.0, false);       // C = [C, V] Q
+  combo(c, kk, c->Uh, kc, c->V, PU, kn, c->Uht, 1.0, false);        // Uh = [Uh D, V] P R^-1
+  combo(c, kk, c->Ux, kc, c->Zs, PU, kn, c->Uxt, 1.0, false);       // Ux = [Ux D, Z] P R^-1
+  CU(cudaMemcpyAsync(c->V - int64_t(kn) * n, c->Ctmp, size_t(kn) * n * 16, cudaMemcpyDeviceToDevice, st));
+  std::swap(c->Uh, c->Uht);
+  std::swap(c->Ux, c->Uxt);
+  c->rdim = kn;
+  CU(cudaStreamSynchronize(st));
+  CU(cudaGetLastError());
+  return HZ_OK;
+}
+
+// One right-hand side by GCRO-DR (x0 = 0), with the stopping and counting rules of
+// fgmres_one; the recycled space left by the previous right-hand side is used from the
+// first cycle on.
+hz_status gcrodr_one(hz_ctx* c, double tol, hz_rhs_info* info) {
+  const int64_t n = c->n;
+  const int m = c->restart;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  double bnorm = 0;
+  TRY(norm2(c, c->b, bnorm));
+  CU(cudaMemsetAsync(c->x, 0, size_t(n) * 16, st));
+  info->iterations = 0;
+  info->status = HZ_OK;
+  info->rel_residual = 0.0;
+  if (bnorm == 0.0) return HZ_OK;
+  if (!std::isfinite(bnorm)) {
+    info->status = HZ_ERR_BREAKDOWN;
+    return HZ_OK;
+  }
+  c->h_pin[6] = bnorm;
+  CU(cudaMemcpyAsync(c->scal + 4, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
+  hz::launch_axpby_copy(n, c->b, c->w, st);                                   // r = b
+  int its = 0;
+  for (;;) {
+    const int kk = c->rdim;
+    c->ckk = kk;
+    if (kk > 0) {
+      // r orthogonal to C: x += Ux C^H r, r -= C C^H r
+      const double2* Cb = c->V - int64_t(kk) * n;
+      hz::launch_cgs(n, kk, Cb, n, nullptr, c->w, kk, c->partial, st);
+      hz::launch_reduce(c->partial, nb, kk, c->h1, st);
+      hz::launch_cgs(n, kk, Cb, n, c->h1, c->w, 0, c->partial, st);
+      hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+      hz::launch_combo(n, kk, c->Ux, n, 0, nullptr, n, c->h1, 1, c->x, n, 1.0, true, st);
+    } else {
+      hz::launch_cgs(n, 0, c->V, n, nullptr, c->w, 0, c->partial, st);
+      hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+    }
+    hz::launch_init_cycle(c->nrm, c->g, m, c->scal + 2, c->scal + 3, st);
+    hz::launch_scale(n, c->w, c->scal + 2, c->V, st);
+    const int p = m - kk;
+    int k = 0;
+    bool stop_nonfinite = false;
+    for (int j = 0; j < p; j++) {
+      TRY(run_iteration(c, j));
+      its++;
+      k = j + 1;
+      const double est = c->h_pin[0];
+      int brk = 0;
+      std::memcpy(&brk, c->h_pin + 4, sizeof(int));
+      if (!std::isfinite(est)) { stop_nonfinite = true; break; }
+      if (brk || est <= tol || its >= c->max_iter) break;
+    }
+    if (stop_nonfinite) {
+      info->iterations = its;
+      info->status = HZ_ERR_BREAKDOWN;
+      info->rel_residual = NAN;
+      return HZ_OK;
+    }
+    hz::launch_update_x(n, k, c->H, m + 1, c->g, c->ysol, c->Zs, n, c->x, st);   // x += Z y
+    if (kk > 0) {                                                                // x -= Ux (B y)
+      CU(cudaStreamSynchronize(st));
+      const std::vector<cplx> y = to_host(c->ysol, size_t(k));
+      const std::vector<cplx> Bh = to_host(c->Braw, size_t(c->rk) * k);
+      std::vector<cplx> t(size_t(kk), 0.0);
+      for (int i = 0; i < kk; i++)
+        for (int j = 0; j < k; j++) t[size_t(i)] += Bh[size_t(j) * c->rk + i] * y[size_t(j)];
+      combo(c, kk, c->Ux, 0, nullptr, t, 1, c->x, -1.0, true);
+    }
+    hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, c->x, c->b, c->w, st);          // r = b - A x
+    double rn = 0;
+    TRY(norm2(c, c->w, rn));
+    const double rel = rn / bnorm;
+    info->iterations = its;
+    info->rel_residual = rel;
+    if (!std::isfinite(rel)) {
+      info->status = HZ_ERR_BREAKDOWN;
+      return HZ_OK;
+    }
+    TRY(recycle_update(c, kk, k));          // kept for the next cycle and right-hand side
+    if (rel <= tol) return HZ_OK;
+    if (its >= c->max_iter) {
+      info->status = HZ_ERR_NOT_CONVERGED;
+      return HZ_OK;
+    }
   }
 }
 
@@ -1056,6 +1298,7 @@ int64_t hz_ndofs(const hz_ctx* c) { return c ? c->n : -1; }
 hz_status hz_get_stats(const hz_ctx* c, hz_stats* out) {
   if (!c || !out) return HZ_ERR_ARG;
   *out = c->stats;
+  out->recycle_dim = c->rdim;
   out->device_bytes = c->bytes;
   out->launches = hz::launch_count();
   return HZ_OK;
@@ -1104,6 +1347,10 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     return fail(c, HZ_ERR_ARG, "bad coarse_solver");
   if (op->coarse_maxit < 0 || op->coarse_maxit > 63 || !(op->coarse_tol >= 0.0))
     return fail(c, HZ_ERR_ARG, "coarse_maxit must be in [0, 63] and coarse_tol >= 0");
+  if (op->recycle < 0 || op->recycle > 16 || 2 * op->recycle > op->restart)
+    return fail(c, HZ_ERR_ARG, "recycle must be in [0, min(16, restart / 2)]");
+  if (op->recycle > 0 && op->block_size > 1)
+    return fail(c, HZ_ERR_ARG, "recycle and block_size > 1 are exclusive");
   const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
   for (int64_t q = 0; q < ne * 4; q++)
     if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
@@ -1325,7 +1572,22 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
   }
   const int64_t n = c->n;
   const int m = c->restart;
-  SETUP_TRY(dalloc(c, &c->V, n * (m + 1)));
+  c->rk = op->recycle;
+  if (c->rk > 0) {
+    // [C (rk columns, right-aligned), V (m + 1 columns)] in one block; recycled-space buffers
+    SETUP_TRY(dalloc(c, &c->Vx, n * (c->rk + m + 1)));
+    c->V = c->Vx + int64_t(c->rk) * n;
+    SETUP_TRY(dalloc(c, &c->Ux, n * c->rk));
+    SETUP_TRY(dalloc(c, &c->Uh, n * c->rk));
+    SETUP_TRY(dalloc(c, &c->Uxt, n * c->rk));
+    SETUP_TRY(dalloc(c, &c->Uht, n * c->rk));
+    SETUP_TRY(dalloc(c, &c->Ctmp, n * c->rk));
+    SETUP_TRY(dalloc(c, &c->Hraw, int64_t(m + 1) * m));
+    SETUP_TRY(dalloc(c, &c->Braw, int64_t(c->rk) * m));
+    SETUP_TRY(dalloc(c, &c->dcoef, int64_t(hz::kComboMaxCols) * hz::kComboMaxOut));
+  } else {
+    SETUP_TRY(dalloc(c, &c->V, n * (m + 1)));
+  }
   SETUP_TRY(dalloc(c, &c->Zs, n * m));
   SETUP_TRY(dalloc(c, &c->w, n));
   SETUP_TRY(dalloc(c, &c->b, n));
@@ -1342,8 +1604,8 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
   SETUP_TRY(dalloc(c, &c->ysol, m));
   SETUP_TRY(dalloc(c, &c->cs, m));
   SETUP_TRY(dalloc(c, &c->scal, 8));
-  c->gexec.assign(m, nullptr);
-  c->gcount.assign(m, 0);
+  c->gexec.assign(size_t(m) * size_t(c->rk + 1), nullptr);
+  c->gcount.assign(size_t(m) * size_t(c->rk + 1), 0);
   // the iterative coarse solve waits on the host inside each preconditioner application
   c->graphs = std::getenv("HZ_NO_GRAPHS") == nullptr && !c->coarse_oras;
   SETUP_TRY(dalloc(c, &c->brk, 1));
@@ -1448,6 +1710,7 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
   }
   CU(cudaStreamSynchronize(c->st));
   c->stats.min_pivot = minp;
+  c->rdim = 0;                              // a recycled space belongs to one operator
   c->stats.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->factored = true;
   return HZ_OK;
@@ -1492,7 +1755,7 @@ extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double t
     CU(cudaMemcpyAsync(c->b, bj, size_t(n) * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->st));
     hz_rhs_info inf{};
-    TRY(fgmres_one(c, tol, &inf));
+    TRY(c->rk ? gcrodr_one(c, tol, &inf) : fgmres_one(c, tol, &inf));
     CU(cudaMemcpyAsync(xj, c->x, size_t(n) * 16, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        c->st));
     if (info) info[j] = inf;

@@ -146,7 +146,12 @@ void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const doubl
 void launch_reduce(const double2* partial, int nblk, int ncols, double2* out, cudaStream_t st);
 void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
                    const double2* h2, const double2* nrm, const double* bnorm, double* est, int* breakdown,
-                   double* invh, cudaStream_t st);
+                   double* invh, cudaStream_t st, int off = 0, double2* raw_h = nullptr, double2* raw_b = nullptr,
+                   int ldb = 0);
+constexpr int kComboMaxCols = 80, kComboMaxOut = 16;
+void launch_combo(int64_t n, int nb1, const double2* B1, int64_t ld1, int nb2, const double2* B2, int64_t ld2,
+                  const double2* coef, int nout, double2* out, int64_t ldo, double sign, bool accumulate,
+                  cudaStream_t st);
 void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta, cudaStream_t st);
 void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st);
 void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y,

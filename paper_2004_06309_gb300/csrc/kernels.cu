@@ -1417,16 +1417,24 @@ __device__ void givens_cs(double2 a, double2 b, double& c, double2& s) {
   s = cmul(u, bc);
 }
 
+// Givens update of column j of the Hessenberg matrix.  The CGS coefficients of the
+// Arnoldi basis start at h1/h2[off] (the first `off` are those of a recycled space,
+// GCRO-DR); raw_h / raw_b (optional) keep the unrotated column and those `off`
+// coefficients for the cycle-end harmonic Ritz problem.
 __global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
                          const double2* h2, const double2* nrm, const double* bnorm_p, double* est,
-                         int* breakdown, double* invh) {
+                         int* breakdown, double* invh, int off, double2* raw_h, double2* raw_b, int ldb) {
   const double bnorm = *bnorm_p;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double2* col = H + int64_t(j) * (m + 1);
-  for (int i = 0; i <= j; i++) col[i] = cadd(h1[i], h2[i]);
+  for (int i = 0; i <= j; i++) col[i] = cadd(h1[off + i], h2[off + i]);
   const double w0 = sqrt(h1[kMaxCols].x);
   const double hn = sqrt(nrm[kMaxCols].x);
   col[j + 1] = make_double2(hn, 0.0);
+  if (raw_h) {
+    for (int i = 0; i <= j + 1; i++) raw_h[int64_t(j) * (m + 1) + i] = col[i];
+    for (int i = 0; i < off; i++) raw_b[int64_t(j) * ldb + i] = cadd(h1[i], h2[i]);
+  }
   for (int i = 0; i < j; i++) {
     const double2 a = col[i], b = col[i + 1];
     const double2 sc = make_double2(sn[i].x, -sn[i].y);
@@ -1451,9 +1459,46 @@ __global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, doub
 
 void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
                    const double2* h2, const double2* nrm, const double* bnorm, double* est, int* breakdown,
-                   double* invh, cudaStream_t st) {
+                   double* invh, cudaStream_t st, int off, double2* raw_h, double2* raw_b, int ldb) {
   HZ_COUNT();
-  k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, h1, h2, nrm, bnorm, est, breakdown, invh);
+  k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, h1, h2, nrm, bnorm, est, breakdown, invh, off, raw_h, raw_b, ldb);
+}
+
+// out[:, q] (+)= sign * (sum_i B1[:, i] coef[i, q] + sum_i B2[:, i] coef[nb1 + i, q]), q < nout:
+// linear combinations of two column-major bases (recycled-space updates of GCRO-DR).
+// coef is (nb1 + nb2) x nout column-major, staged in shared memory.
+constexpr int kComboCols = 80, kComboOut = 16;
+__global__ void __launch_bounds__(256) k_combo(int64_t n, int nb1, const double2* B1, int64_t ld1, int nb2,
+                                               const double2* B2, int64_t ld2, const double2* coef, int nout,
+                                               double2* out, int64_t ldo, double sign, int accumulate) {
+  __shared__ double2 cf[kComboCols * kComboOut];
+  const int nbt = nb1 + nb2;
+  for (int e = threadIdx.x; e < nbt * nout; e += blockDim.x) cf[e] = coef[e];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    double2 acc[kComboOut];
+#pragma unroll
+    for (int q = 0; q < kComboOut; q++) acc[q] = make_double2(0.0, 0.0);
+    for (int i = 0; i < nbt; i++) {
+      const double2 v = i < nb1 ? B1[r + int64_t(i) * ld1] : B2[r + int64_t(i - nb1) * ld2];
+#pragma unroll
+      for (int q = 0; q < kComboOut; q++)
+        if (q < nout) acc[q] = cmad(v, cf[q * nbt + i], acc[q]);
+    }
+    for (int q = 0; q < nout; q++) {
+      double2* o = out + r + int64_t(q) * ldo;
+      const double2 a = make_double2(sign * acc[q].x, sign * acc[q].y);
+      *o = accumulate ? cadd(*o, a) : a;
+    }
+  }
+}
+void launch_combo(int64_t n, int nb1, const double2* B1, int64_t ld1, int nb2, const double2* B2, int64_t ld2,
+                  const double2* coef, int nout, double2* out, int64_t ldo, double sign, bool accumulate,
+                  cudaStream_t st) {
+  if (n == 0 || nout == 0) return;
+  HZ_COUNT();
+  k_combo<<<grid_for(n, 256), 256, 0, st>>>(n, nb1, B1, ld1, nb2, B2, ld2, coef, nout, out, ldo, sign,
+                                            accumulate ? 1 : 0);
 }
 
 __global__ void k_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta) {
