@@ -42,6 +42,8 @@ WORKLOADS = {
 # Inner iterations the 5 Hz workload takes to 1e-6 (measured on the GPU path, FP64 and mixed
 # alike); the reference arm runs in a separate process and scales its sample by it.
 FULL_WORKLOAD_ITERATIONS = 74
+# DRAM traffic / algorithmic bytes of the complex64 local sweeps (ncu, medium workload)
+LOCAL_SWEEP_TRAFFIC_RATIO = 1.017
 # Oracle sample for the CPU baseline / reference arm: same generator, 1/64 of the dofs.
 ORACLE_SAMPLE = dict(kind="overthrust", cells=None, freq=1.25, nsub=8, overlap=2, restart=50)
 
@@ -533,6 +535,12 @@ def main():
                 "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (copy)"}
     roof.update({"kernel": f"{dom} ({main_p})", "ms_per_launch": ph["ms"], "algorithmic_bytes": ph["bytes"],
                  "flops": ph["flops"], "launches_per_run": ph["launches"]})
+    if dom == "local_solve" and main_p == "mixed":
+        # DRAM bytes per run of the complex64 sweeps: ncu (dram__bytes_read/write) on the
+        # medium workload measured 1.017 x the algorithmic bytes; the traffic grows with the
+        # panel entries, so it is scaled to this workload
+        roof["traffic"] = LOCAL_SWEEP_TRAFFIC_RATIO * ph["bytes"]
+        roof["traffic_source"] = "ncu dram bytes on overthrust-medium, scaled by algorithmic bytes"
 
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": K,
