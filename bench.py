@@ -44,7 +44,7 @@ WORKLOADS = {
 FULL_WORKLOAD_ITERATIONS = 74
 # DRAM traffic / algorithmic bytes of the complex64 local sweeps (ncu, medium workload)
 LOCAL_SWEEP_TRAFFIC_RATIO = 1.017
-# Oracle sample for the CPU baseline / reference arm: same generator, 1/64 of the dofs.
+# Oracle sample for the CPU baseline / reference arm: same generator, 1/43 of the dofs.
 ORACLE_SAMPLE = dict(kind="overthrust", cells=None, freq=1.25, nsub=8, overlap=2, restart=50)
 
 
