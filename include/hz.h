@@ -323,7 +323,7 @@ hz_status hz_server_create(const hz_server_options* opt, hz_server** out);
 /* Registers a problem: mesh (copied; the caller keeps its arrays), solver options
    (nsub, overlap, levels, restart, max_iter, leaf_size, max_snode, elem_part
    copied; precision and block_size come from the server; stream and hbm_budget
-   are the server's) and the frequency.  Nothing runs until a request names it.
+   are the server's; recycle is not used) and the frequency.  Nothing runs until a request names it.
    *problem_id counts from 0 in registration order. */
 hz_status hz_server_add_problem(hz_server* s, const hz_mesh_desc* mesh, const hz_options* opt, double freq_hz,
                                 int32_t* problem_id);

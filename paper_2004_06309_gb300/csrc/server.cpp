@@ -419,6 +419,7 @@ hz_status hz_server_add_problem(hz_server* s, const hz_mesh_desc* md, const hz_o
   p->opt = *op;
   p->opt.precision = s->opt.precision;
   p->opt.block_size = s->opt.slots;
+  p->opt.recycle = 0;                       // slots run pseudo-block FGMRES
   p->xyz.assign(md->xyz, md->xyz + 3 * md->nv);
   p->tets.assign(md->tets, md->tets + 4 * md->ne);
   p->c_re.assign(md->c_re, md->c_re + md->ne);

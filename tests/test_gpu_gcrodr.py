@@ -106,3 +106,22 @@ def test_recycle_rejects_bad_sizes(hzmod):
         hzmod.Solver(p, recycle=p.restart)           # more than restart / 2
     with pytest.raises(hzmod.HzError):
         hzmod.Solver(p, recycle=2, block_size=4)
+
+
+def test_recycle_edge_cases(hzmod):
+    p = synth.tiny_problem()
+    G = hzmod.Solver(p, recycle=4)
+    G.factor()
+    S = OracleSolver(p)
+    b = S.rhs()[:, 0]
+    x, info = G.solve(b)                                   # builds a recycled space
+    assert info[0][1] == 0 and G.stats()["recycle_dim"] == 4
+    z = np.zeros(G.n, np.complex128)
+    x, info = G.solve(z)                                   # zero right-hand side
+    assert np.all(x == 0) and info[0][0] == 0 and info[0][1] == 0
+    x, info = G.solve(np.full(G.n, np.nan + 0j), check=False)
+    assert info[0][1] == hzmod.HZ_ERR_BREAKDOWN
+    x, info = G.solve(b)                                   # still usable afterwards
+    assert info[0][1] == 0
+    assert np.linalg.norm(b - S.A @ x) / np.linalg.norm(b) <= p.tol
+    G.close()
