@@ -1870,12 +1870,40 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   double inner_its = 0;          // iterative coarse solve: mean inner iterations per run
   for (int ph = 0; ph < HZ_PH_COUNT; ph++) {
     run(ph);   // warm-up
+    // Each phase is timed as the solve runs it: captured once as a CUDA graph and replayed
+    // (eagerly where the stream cannot be captured or the phase waits on the host).
+    const bool host_waits = c->coarse_oras && (ph == HZ_PH_COARSE || ph == HZ_PH_PRECOND || ph == HZ_PH_ITERATION);
+    cudaGraphExec_t ge = nullptr;
+    long long per_run = 0;
+    if (c->graphs && st != nullptr && !host_waits) {
+      const long long l0 = hz::launch_count();
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        run(ph);
+        if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) {
+          if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+          cudaGraphDestroy(g);
+        }
+      }
+      cudaGetLastError();
+      per_run = hz::launch_count() - l0;
+      hz::add_launches(-per_run);
+    }
     const long long l0 = hz::launch_count();
     const int64_t c0 = c->stats.coarse_iterations;
+    if (ge) CU(cudaGraphLaunch(ge, st));                                      // warm replay
     CU(cudaEventRecord(e0, st));
-    for (int r = 0; r < reps; r++) run(ph);
+    for (int r = 0; r < reps; r++) {
+      if (ge) {
+        CU(cudaGraphLaunch(ge, st));
+        hz::add_launches(per_run);
+      } else {
+        run(ph);
+      }
+    }
     CU(cudaEventRecord(e1, st));
     CU(cudaEventSynchronize(e1));
+    if (ge) cudaGraphExecDestroy(ge);
     float ms = 0;
     CU(cudaEventElapsedTime(&ms, e0, e1));
     out->ms[ph] = double(ms) / reps;

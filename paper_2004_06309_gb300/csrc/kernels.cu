@@ -605,24 +605,53 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
   const int64_t* cp = cptr + S.rowoff;
-  for (int j = tid; j < k; j += blockDim.x) {
-    V acc = tin[S.first + j];
-    for (int64_t c = cp[j]; c < cp[j + 1]; c++) acc = cadd(acc, u[cidx[c]]);
-    b1[j] = acc;
-  }
-  __syncthreads();
   const int rr = tid % RT, cg = tid / RT;
   const int r = t.y * RT + rr;
   const V* P = panels + S.paneloff;
   V acc = czero<V>(), acc2 = czero<V>();
-  if (r < m) {
+  if constexpr (RT == 16) {
+    // sparse levels: the panel values (at most kMaxK / 16 per thread) are loaded before
+    // the right-hand side is gathered; the sums keep the loop's order (even q: acc)
+    constexpr int MQ = kMaxK / CG;
+    V pv[MQ];
     const int jmax = min(r, k);
-    int j = cg;
-    for (; j + CG < jmax; j += 2 * CG) {
-      acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
-      acc2 = cmad(P[r + int64_t(j + CG) * S.ld], b1[j + CG], acc2);
+#pragma unroll
+    for (int q = 0; q < MQ; q++) {
+      const int j = cg + CG * q;
+      pv[q] = (r < m && j < jmax) ? P[r + int64_t(j) * S.ld] : czero<V>();
     }
-    if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+    for (int j = tid; j < k; j += blockDim.x) {
+      V a = tin[S.first + j];
+      for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, u[cidx[c]]);
+      b1[j] = a;
+    }
+    __syncthreads();
+    if (r < m) {
+#pragma unroll
+      for (int q = 0; q < MQ; q++) {
+        const int j = cg + CG * q;
+        if (j < jmax) {
+          if (q % 2 == 0) acc = cmad(pv[q], b1[j], acc);
+          else acc2 = cmad(pv[q], b1[j], acc2);
+        }
+      }
+    }
+  } else {
+    for (int j = tid; j < k; j += blockDim.x) {
+      V a = tin[S.first + j];
+      for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, u[cidx[c]]);
+      b1[j] = a;
+    }
+    __syncthreads();
+    if (r < m) {
+      const int jmax = min(r, k);
+      int j = cg;
+      for (; j + CG < jmax; j += 2 * CG) {
+        acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+        acc2 = cmad(P[r + int64_t(j + CG) * S.ld], b1[j + CG], acc2);
+      }
+      if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+    }
   }
   part[cg][rr] = cadd(acc, acc2);
   __syncthreads();
@@ -742,14 +771,52 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
   const int k = S.k, m = S.m, tid = threadIdx.x;
   const int pr = tid % NP, cg = tid / NP;
   const int64_t* cp = cptr + S.rowoff;
+  const int r = t.y * ROWS + 2 * pr;                 // rows r, r + 1 (r even, ld % 4 == 0)
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
+  if constexpr (CG == 8) {
+    // sparse levels: this thread's (at most kMaxK / 8) panel values are loaded before the
+    // right-hand side is gathered, so the two latency chains overlap; the sums run in the
+    // order of the loop below (even q on one chain, odd q on the other)
+    constexpr int MQ = kMaxK / CG, PF = 8;              // PF of the MQ columns are prefetched
+    float4 pv[MQ];
+    const int j0 = min(r, k), j1 = min(r + 1, k);
+    const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + (r < m ? r : 0));
+    const int64_t ld4 = S.ld / 2;
+#pragma unroll
+    for (int q = 0; q < PF; q++) {
+      const int j = cg + CG * q;
+      pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int jj = tid; jj < k; jj += blockDim.x) {
+      float2 acc = tin[S.first + jj];
+      for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+      b1[jj] = acc;
+    }
+    __syncthreads();
+    if (r < m) {
+#pragma unroll
+      for (int q = 0; q < MQ; q++) {
+        const int j = cg + CG * q;
+        if (j < j1) {
+          if (q >= PF) pv[q] = P4[int64_t(j) * ld4];
+          const float2 bj = b1[j];
+          if (q % 2 == 0) {
+            a1 = cmad(make_float2(pv[q].z, pv[q].w), bj, a1);
+            if (j < j0) a0 = cmad(make_float2(pv[q].x, pv[q].y), bj, a0);
+          } else {
+            c1 = cmad(make_float2(pv[q].z, pv[q].w), bj, c1);
+            if (j < j0) c0 = cmad(make_float2(pv[q].x, pv[q].y), bj, c0);
+          }
+        }
+      }
+    }
+  } else {
   for (int jj = tid; jj < k; jj += blockDim.x) {
     float2 acc = tin[S.first + jj];
     for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
     b1[jj] = acc;
   }
   __syncthreads();
-  const int r = t.y * ROWS + 2 * pr;                 // rows r, r + 1 (r even, ld % 4 == 0)
-  float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
   if (r < m) {
     const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
     const int64_t ld4 = S.ld / 2;
@@ -770,6 +837,7 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
       a1 = cmad(make_float2(p.z, p.w), bj, a1);
       if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
     }
+  }
   }
   part[cg][2 * pr] = cadd(a0, c0);
   part[cg][2 * pr + 1] = cadd(a1, c1);
