@@ -716,6 +716,9 @@ __device__ __forceinline__ void bwd_finish(const int4 fin, const SnDev& S, const
 // (c, s) sums column j = 32 * block + c over slice s (of 8) of the chunk's rows,
 // reading its column sequentially (L1 reuse of each 128-byte line); the 8 slice
 // sums are then added in a fixed order.  No shuffle reductions on the FP64 pipe.
+// PF (narrow chunks of at most 64 rows, sparse levels): each thread's <= 8 panel values are
+// loaded before the chunk's right-hand side is gathered; the sums keep the loop's order.
+template <bool PF>
 __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, const SnDev* sn,
                                                           const int32_t* rowlist, const double2* panels,
                                                           const double2* zin, double2* x, double2* partial,
@@ -727,20 +730,39 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
   const int k = S.k, m = S.m, tid = threadIdx.x, c = tid & 31, s = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
   const int32_t* rl = rowlist + S.rowoff;
-  for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
-  __syncthreads();
   const int j = t.y * 32 + c;
   const int slice = (rows + 7) / 8;
   const int ra = max(r0 + s * slice, j + 1), rb = min(r1, r0 + (s + 1) * slice);
+  const double2* col = panels + S.paneloff + int64_t(j < k ? j : 0) * S.ld;
+  double2 pre[8];
+  if constexpr (PF) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int r = ra + q;
+      pre[q] = (j < k && r < rb) ? col[r] : make_double2(0.0, 0.0);
+    }
+  }
+  for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
+  __syncthreads();
   double2 a0 = make_double2(0.0, 0.0), a1 = a0;
   if (j < k) {
-    const double2* col = panels + S.paneloff + int64_t(j) * S.ld;
-    int r = ra;
-    for (; r + 1 < rb; r += 2) {
-      a0 = cmad(col[r], vec[r - r0], a0);
-      a1 = cmad(col[r + 1], vec[r + 1 - r0], a1);
+    if constexpr (PF) {
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int r = ra + q;
+        if (r < rb) {
+          if (q % 2 == 0) a0 = cmad(pre[q], vec[r - r0], a0);     // the loop's pairs (r, r + 1)
+          else a1 = cmad(pre[q], vec[r - r0], a1);
+        }
+      }
+    } else {
+      int r = ra;
+      for (; r + 1 < rb; r += 2) {
+        a0 = cmad(col[r], vec[r - r0], a0);
+        a1 = cmad(col[r + 1], vec[r + 1 - r0], a1);
+      }
+      if (r < rb) a0 = cmad(col[r], vec[r - r0], a0);
     }
-    if (r < rb) a0 = cmad(col[r], vec[r - r0], a0);
   }
   red[s][c] = cadd(a0, a1);
   __syncthreads();
@@ -858,7 +880,10 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
   }
 }
 
-// complex64 backward partial sums with 16-byte loads (two rows per lane).
+// complex64 backward partial sums with 16-byte loads (two rows per lane).  PF (narrow
+// chunks of at most 128 rows, sparse levels): each lane's <= 2 row pairs of its 4 columns
+// are loaded before the chunk's right-hand side is gathered; the sums keep their order.
+template <bool PF>
 __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, const SnDev* sn,
                                                          const int32_t* rowlist, const float2* panels,
                                                          const float2* zin, float2* x, float2* partial,
@@ -869,24 +894,52 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
   const int32_t* rl = rowlist + S.rowoff;
+  float4 pre[4][2];
+  if constexpr (PF) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int j = t.y * 32 + wid + 8 * q;
+      const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j < k ? j : 0) * S.ld);
+      const int rs = max(r0, (j + 1) & ~1);
+#pragma unroll
+      for (int it = 0; it < 2; it++) {
+        const int r = rs + 2 * lane + 64 * it;
+        pre[q][it] = (j < k && r < r1) ? col[r >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
   for (int r = r0 + tid; r < r0 + rows + 2; r += blockDim.x)
     vec[r - r0] = (r < r1) ? ((r < k) ? zin[S.first + r] : cneg(x[rl[r]])) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* out = partial + int64_t(blockIdx.x) * 32;
   const float4* vec4 = reinterpret_cast<const float4*>(vec);
+#pragma unroll
   for (int q = 0; q < 4; q++) {
     const int c = wid + 8 * q;
     const int j = t.y * 32 + c;
     float2 acc = make_float2(0.f, 0.f);
     if (j < k) {
-      const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j) * S.ld);
       const int rs = max(r0, (j + 1) & ~1);          // first even row of the pair holding row j + 1
+      if constexpr (PF) {
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+          const int r = rs + 2 * lane + 64 * it;
+          if (r < r1) {
+            const float4 p = pre[q][it];
+            const float4 v = vec4[(r - r0) >> 1];
+            if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
+            acc = cmad(make_float2(p.z, p.w), make_float2(v.z, v.w), acc);
+          }
+        }
+      } else {
+        const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j) * S.ld);
 #pragma unroll 4
-      for (int r = rs + 2 * lane; r < r1; r += 64) {
-        const float4 p = col[r >> 1];
-        const float4 v = vec4[(r - r0) >> 1];
-        if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
-        acc = cmad(make_float2(p.z, p.w), make_float2(v.z, v.w), acc);
+        for (int r = rs + 2 * lane; r < r1; r += 64) {
+          const float4 p = col[r >> 1];
+          const float4 v = vec4[(r - r0) >> 1];
+          if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
+          acc = cmad(make_float2(p.z, p.w), make_float2(v.z, v.w), acc);
+        }
       }
     }
     acc = warp_sum(acc);
@@ -939,13 +992,25 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     if (e > b) {
       HZ_COUNT();
       if constexpr (sizeof(V) == 8)
-        k_bwd_partial_c64<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                           F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows,
-                                                           F.bfin_tasks, F.bwd_counters);
+      {
+        const int rows = F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows;
+        if (rows <= 128)
+          k_bwd_partial_c64<true><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                                   rows, F.bfin_tasks, F.bwd_counters);
+        else
+          k_bwd_partial_c64<false><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x,
+                                                                    part, rows, F.bfin_tasks, F.bwd_counters);
+      }
       else
-        k_bwd_partial_c128<<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                            F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows,
-                                                            F.bfin_tasks, F.bwd_counters);
+      {
+        const int rows = F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows;
+        if (rows <= 64)
+          k_bwd_partial_c128<true><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
+                                                                    rows, F.bfin_tasks, F.bwd_counters);
+        else
+          k_bwd_partial_c128<false><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x,
+                                                                     part, rows, F.bfin_tasks, F.bwd_counters);
+      }
     }
     if (F.level_events) cudaEventRecord(F.level_events[1 + F.nlev + (F.nlev - 1 - l)], st);
   }
