@@ -1195,7 +1195,6 @@ hz_status slots_complete(hz_ctx* c) {
 int slot_count(const hz_ctx* c) { return c->S; }
 void slot_reset(hz_ctx* c, int i) { c->slots[i] = hz_ctx::Slot{}; }
 int slot_state(const hz_ctx* c, int i) { return c->slots[i].state; }
-int64_t slot_tag(const hz_ctx* c, int i) { return c->slots[i].tag; }
 bool slots_running(const hz_ctx* c) {
   for (int i = 0; i < c->S; i++)
     if (c->slots[i].state == hz_ctx::SLOT_RUN) return true;

@@ -30,7 +30,6 @@ int64_t device_bytes(const hz_ctx* c);
 // Slot engine (requires options.block_size > 1).
 int slot_count(const hz_ctx* c);
 int slot_state(const hz_ctx* c, int i);
-int64_t slot_tag(const hz_ctx* c, int i);
 bool slots_running(const hz_ctx* c);
 hz_status slot_point_source(hz_ctx* c, int i, const double xyz[3]);
 hz_status slot_start(hz_ctx* c, int i, double tol, int64_t tag);
