@@ -84,6 +84,7 @@ struct hz_ctx {
   double2 *Hb = nullptr, *snb = nullptr, *gb = nullptr, *yb = nullptr;
   double *csb = nullptr, *scalb = nullptr;
   int* brkb = nullptr;
+  double2 *partial_s = nullptr, *h1s = nullptr, *h2s = nullptr, *nrms = nullptr;   // slot-batched CGS2
   // slot engine (continuous pseudo-block FGMRES): one right-hand side per slot
   enum { SLOT_FREE = hz_engine::SLOT_FREE, SLOT_RUN = hz_engine::SLOT_RUN, SLOT_DONE = hz_engine::SLOT_DONE };
   struct Slot {
@@ -1116,23 +1117,39 @@ void slots_issue(hz_ctx* c) {
   hz::launch_deinterleave(n, S, zout, c->Yi, c->Zb, st);
   hz::launch_spmv_multi(n, S, c->d_rp, c->d_ci, c->d_A, c->Yi, nullptr, c->Wi, st);
   hz::launch_deinterleave(n, S, wout, c->Wi, c->Wc, st);
-  for (int i = 0; i < S; i++) {
-    const hz_ctx::Slot& s = c->slots[i];
-    if (s.state != hz_ctx::SLOT_RUN) continue;
-    const int j = s.j;
-    double2* w = slot_col(c, c->Wc, i);
-    double2* V = slot_V(c, i);
-    hz::launch_cgs(n, j + 1, V, n, nullptr, w, j + 1, c->partial, st);
-    hz::launch_reduce(c->partial, nb, j + 1, c->h1, st);
-    hz::launch_cgs(n, j + 1, V, n, c->h1, w, j + 1, c->partial, st);
-    hz::launch_reduce(c->partial, nb, j + 1, c->h2, st);
-    hz::launch_cgs(n, j + 1, V, n, c->h2, w, 0, c->partial, st);
-    hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
-    hz::launch_givens(j, m, c->Hb + int64_t(i) * (m + 1) * m, c->csb + int64_t(i) * m, c->snb + int64_t(i) * m,
-                      c->gb + int64_t(i) * (m + 1), c->h1, c->h2, c->nrm, slot_scal(c, i) + 4, slot_scal(c, i),
-                      c->brkb + i, slot_scal(c, i) + 1, st);
-    hz::launch_scale(n, w, slot_scal(c, i) + 1, V + int64_t(j + 1) * n, st);
+  // CGS2 against each slot's own basis, the Givens update at its own j and v_{j+1},
+  // every step one launch for all slots
+  hz::SlotCgs pc{};
+  hz::SlotGivens pg{};
+  hz::SlotScale ps{};
+  pg.m = m;
+  pg.H = c->Hb;
+  pg.sn = c->snb;
+  pg.g = c->gb;
+  pg.cs = c->csb;
+  pg.h1 = c->h1s;
+  pg.h2 = c->h2s;
+  pg.nrm = c->nrms;
+  pg.scal = c->scalb;
+  pg.brk = c->brkb;
+  for (int i = 0; i < 16; i++) {
+    const bool run = i < S && c->slots[i].state == hz_ctx::SLOT_RUN;
+    const int j = run ? c->slots[i].j : -1;
+    pc.V[i] = run ? slot_V(c, i) : nullptr;
+    pc.w[i] = run ? slot_col(c, c->Wc, i) : nullptr;
+    pc.h[i] = c->h1s + int64_t(i) * 65;
+    pc.ncols[i] = run ? j + 1 : -1;
+    pg.j[i] = j;
+    ps.w[i] = pc.w[i];
+    ps.s[i] = run ? slot_scal(c, i) + 1 : nullptr;
+    ps.out[i] = run ? slot_V(c, i) + int64_t(j + 1) * n : nullptr;
   }
+  hz::launch_cgs_slots(n, S, pc, false, true, c->partial_s, c->h1s, st);    // h1 = V^H w
+  hz::launch_cgs_slots(n, S, pc, true, true, c->partial_s, c->h2s, st);     // w -= V h1; h2 = V^H w
+  for (int i = 0; i < 16; i++) pc.h[i] = c->h2s + int64_t(i) * 65;
+  hz::launch_cgs_slots(n, S, pc, true, false, c->partial_s, c->nrms, st);   // w -= V h2; |w|^2
+  hz::launch_givens_slots(S, pg, st);
+  hz::launch_scale_slots(n, S, ps, st);
   cudaMemcpyAsync(c->h_pin + hz_ctx::PIN_SLOT, c->scalb, size_t(S) * 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(c->h_pin + hz_ctx::PIN_FLAGS, c->brkb, size_t(S) * sizeof(int), cudaMemcpyDeviceToHost, st);
 }
@@ -1646,6 +1663,10 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
     SETUP_TRY(dalloc(c, &c->csb, int64_t(S) * m));
     SETUP_TRY(dalloc(c, &c->scalb, int64_t(S) * 8));
     SETUP_TRY(dalloc(c, &c->brkb, int64_t(S)));
+    SETUP_TRY(dalloc(c, &c->partial_s, int64_t(S) * hz::cgs_blocks() * 65));
+    SETUP_TRY(dalloc(c, &c->h1s, int64_t(S) * 65));
+    SETUP_TRY(dalloc(c, &c->h2s, int64_t(S) * 65));
+    SETUP_TRY(dalloc(c, &c->nrms, int64_t(S) * 65));
     c->slots.assign(S, hz_ctx::Slot{});
   }
   // pinned scalars: 8 for the single-RHS loop, then 16 x 8 per-RHS scalars and 16 flags

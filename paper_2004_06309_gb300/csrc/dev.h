@@ -98,6 +98,31 @@ struct SlotCols {
   int64_t o[16];
 };
 
+// Per-slot operands of the slot-batched CGS2 passes (ncols < 0: empty slot).
+struct SlotCgs {
+  const double2* V[16];       // the slot's basis, column-major, leading dimension n
+  double2* w[16];
+  const double2* h[16];       // coefficients of the update pass
+  int ncols[16];
+};
+
+// Per-slot Givens update: slot i's arrays at fixed strides from these bases (j < 0: skip).
+struct SlotGivens {
+  int m;
+  int j[16];
+  double2 *H, *sn, *g;
+  double* cs;
+  const double2 *h1, *h2, *nrm;    // S x 65 each
+  double* scal;                    // S x 8: estimate, 1 / h_{j+1,j}, ..., |b| at 4
+  int* brk;
+};
+
+struct SlotScale {
+  const double2* w[16];
+  const double* s[16];
+  double2* out[16];                // null: empty slot
+};
+
 // One point source's right-hand side: at most 10 basis functions (P2 tetrahedron).
 struct PointRhs {
   int64_t idx[10];
@@ -131,6 +156,11 @@ void launch_interleave(int64_t n, int S, const SlotCols& off, const double2* bas
 void launch_deinterleave(int64_t n, int S, const SlotCols& off, const double2* inter, double2* base, cudaStream_t st);
 void launch_point_rhs(const PointRhs& p, double2* out, cudaStream_t st);
 void launch_interleave_put(int64_t n, int S, int i, const double2* col, double2* inter, cudaStream_t st);
+// out (S x 65): per slot, maxpy pass (w -= V h) and / or dot pass (V^H w, |w|^2), reduced.
+void launch_cgs_slots(int64_t n, int S, const SlotCgs& p, bool maxpy, bool dots, double2* partial, double2* out,
+                      cudaStream_t st);
+void launch_givens_slots(int S, const SlotGivens& p, cudaStream_t st);
+void launch_scale_slots(int64_t n, int S, const SlotScale& p, cudaStream_t st);
 void launch_spmv_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double2* val, const double2* x,
                        const double2* sub, double2* y, cudaStream_t st);
 void launch_spmv_real_multi(int64_t n, int S, const int64_t* rp, const int32_t* ci, const double* val,

@@ -1433,12 +1433,11 @@ int cgs_blocks() { return 152 * 4; }
 
 // Multi-dot: partial[b][j] = sum over the block's rows of conj(V[r][j]) w[r] (j < ncols);
 // partial[b][64] = sum |w[r]|^2.  One warp per column, lanes over rows.
-__global__ void __launch_bounds__(256) k_mdot(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
-                                              const double2* __restrict__ w, double2* partial, int64_t chunk) {
+__device__ __forceinline__ void mdot_block(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
+                                           const double2* __restrict__ w, double2* out, int64_t chunk, int bx) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row0 = blockIdx.x * chunk;
+  const int64_t row0 = bx * chunk;
   const int64_t row1 = min(n, row0 + chunk);
-  double2* out = partial + int64_t(blockIdx.x) * kPartStride;
   for (int j = wid; j < kMaxCols; j += 8) {
     double2 acc = make_double2(0.0, 0.0);
     if (j < ncols) {
@@ -1459,16 +1458,20 @@ __global__ void __launch_bounds__(256) k_mdot(int64_t n, int ncols, const double
     if (lane == 0) out[kMaxCols] = make_double2(s, 0.0);
   }
 }
+__global__ void __launch_bounds__(256) k_mdot(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
+                                              const double2* __restrict__ w, double2* partial, int64_t chunk) {
+  mdot_block(n, ncols, V, ldv, w, partial + int64_t(blockIdx.x) * kPartStride, chunk, blockIdx.x);
+}
 
 // Multi-axpy: w[r] -= sum_j V[r][j] h[j]; partial[b][64] = sum |w[r]|^2 (new w).
-__global__ void __launch_bounds__(256) k_maxpy(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
-                                               const double2* __restrict__ h, double2* w, double2* partial,
-                                               int64_t chunk) {
+__device__ __forceinline__ void maxpy_block(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
+                                            const double2* __restrict__ h, double2* w, double2* out, int64_t chunk,
+                                            int bx) {
   __shared__ double2 hs[kMaxCols];
   __shared__ double red[8];
   for (int j = threadIdx.x; j < ncols; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
-  const int64_t row0 = blockIdx.x * chunk;
+  const int64_t row0 = bx * chunk;
   const int64_t row1 = min(n, row0 + chunk);
   double s = 0.0;
   for (int64_t r = row0 + threadIdx.x; r < row1; r += blockDim.x) {
@@ -1485,8 +1488,13 @@ __global__ void __launch_bounds__(256) k_maxpy(int64_t n, int ncols, const doubl
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < 8; q++) t += red[q];
-    partial[int64_t(blockIdx.x) * kPartStride + kMaxCols] = make_double2(t, 0.0);
+    out[kMaxCols] = make_double2(t, 0.0);
   }
+}
+__global__ void __launch_bounds__(256) k_maxpy(int64_t n, int ncols, const double2* __restrict__ V, int64_t ldv,
+                                               const double2* __restrict__ h, double2* w, double2* partial,
+                                               int64_t chunk) {
+  maxpy_block(n, ncols, V, ldv, h, w, partial + int64_t(blockIdx.x) * kPartStride, chunk, blockIdx.x);
 }
 
 static int64_t cgs_chunk(int64_t n) {
@@ -1512,9 +1520,8 @@ void launch_cgs(int64_t n, int ncols, const double2* V, int64_t ldv, const doubl
 }
 
 // out[j] = sum over blocks of partial[b][j]; one CTA per j, fixed-order tree.
-__global__ void __launch_bounds__(256) k_reduce(const double2* partial, int nblk, double2* out) {
+__device__ __forceinline__ void reduce_block(const double2* partial, int nblk, double2* out, int j) {
   __shared__ double2 red[256];
-  const int j = blockIdx.x;
   double2 s = make_double2(0.0, 0.0);
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) s = cadd(s, partial[int64_t(b) * kPartStride + j]);
   red[threadIdx.x] = s;
@@ -1524,6 +1531,9 @@ __global__ void __launch_bounds__(256) k_reduce(const double2* partial, int nblk
     __syncthreads();
   }
   if (threadIdx.x == 0) out[j] = red[0];
+}
+__global__ void __launch_bounds__(256) k_reduce(const double2* partial, int nblk, double2* out) {
+  reduce_block(partial, nblk, out, blockIdx.x);
 }
 
 // Sums all 65 slots (columns and the norm slot 64).
@@ -1554,11 +1564,12 @@ __device__ void givens_cs(double2 a, double2 b, double& c, double2& s) {
 // Arnoldi basis start at h1/h2[off] (the first `off` are those of a recycled space,
 // GCRO-DR); raw_h / raw_b (optional) keep the unrotated column and those `off`
 // coefficients for the cycle-end harmonic Ritz problem.
-__global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
-                         const double2* h2, const double2* nrm, const double* bnorm_p, double* est,
-                         int* breakdown, double* invh, int off, double2* raw_h, double2* raw_b, int ldb) {
+__device__ void k_givens_body(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
+                              const double2* h2, const double2* nrm, const double* bnorm_p, double* est,
+                              int* breakdown, double* invh, int off = 0, double2* raw_h = nullptr,
+                              double2* raw_b = nullptr, int ldb = 0) {
+  if (threadIdx.x != 0) return;
   const double bnorm = *bnorm_p;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double2* col = H + int64_t(j) * (m + 1);
   for (int i = 0; i <= j; i++) col[i] = cadd(h1[off + i], h2[off + i]);
   const double w0 = sqrt(h1[kMaxCols].x);
@@ -1589,12 +1600,78 @@ __global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, doub
   *breakdown = (hn <= 1e-14 * w0) ? 1 : 0;
   *invh = 1.0 / hn;
 }
+__global__ void k_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
+                         const double2* h2, const double2* nrm, const double* bnorm_p, double* est,
+                         int* breakdown, double* invh, int off, double2* raw_h, double2* raw_b, int ldb) {
+  if (blockIdx.x != 0) return;
+  k_givens_body(j, m, H, cs, sn, g, h1, h2, nrm, bnorm_p, est, breakdown, invh, off, raw_h, raw_b, ldb);
+}
 
 void launch_givens(int j, int m, double2* H, double* cs, double2* sn, double2* g, const double2* h1,
                    const double2* h2, const double2* nrm, const double* bnorm, double* est, int* breakdown,
                    double* invh, cudaStream_t st, int off, double2* raw_h, double2* raw_b, int ldb) {
   HZ_COUNT();
   k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, h1, h2, nrm, bnorm, est, breakdown, invh, off, raw_h, raw_b, ldb);
+}
+
+// ---------------------------------------------------------------------------
+// The same CGS2 / Givens / scaling steps for the S slots of a pseudo-block solve in one
+// launch each (grid.y = slot); each slot's arithmetic is the single-vector kernels'
+// block for block, so its results do not depend on the other slots.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cgs_slots(int64_t n, SlotCgs p, double2* partial, int64_t chunk,
+                                                   int mode) {
+  const int i = blockIdx.y, nb = gridDim.x;
+  if (p.ncols[i] < 0) return;
+  double2* out = partial + (int64_t(i) * nb + blockIdx.x) * kPartStride;
+  if (mode == 0)
+    mdot_block(n, p.ncols[i], p.V[i], n, p.w[i], out, chunk, blockIdx.x);
+  else
+    maxpy_block(n, p.ncols[i], p.V[i], n, p.h[i], p.w[i], out, chunk, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) k_reduce_slots(const double2* partial, int nblk, SlotCgs p, double2* out) {
+  const int i = blockIdx.y;
+  if (p.ncols[i] < 0) return;
+  reduce_block(partial + int64_t(i) * nblk * kPartStride, nblk, out + int64_t(i) * kPartStride, blockIdx.x);
+}
+void launch_cgs_slots(int64_t n, int S, const SlotCgs& p, bool maxpy, bool dots, double2* partial, double2* out,
+                      cudaStream_t st) {
+  const int nb = cgs_blocks();
+  const int64_t chunk = cgs_chunk(n);
+  if (maxpy) {
+    HZ_COUNT();
+    k_cgs_slots<<<dim3(nb, S), 256, 0, st>>>(n, p, partial, chunk, 1);
+  }
+  if (dots) {
+    HZ_COUNT();
+    k_cgs_slots<<<dim3(nb, S), 256, 0, st>>>(n, p, partial, chunk, 0);
+  }
+  HZ_COUNT();
+  k_reduce_slots<<<dim3(kMaxCols + 1, S), 256, 0, st>>>(partial, nb, p, out);
+}
+__global__ void k_givens_slots(SlotGivens p) {
+  const int i = blockIdx.x;
+  if (p.j[i] < 0) return;
+  const int m = p.m;
+  k_givens_body(p.j[i], m, p.H + int64_t(i) * (m + 1) * m, p.cs + int64_t(i) * m, p.sn + int64_t(i) * m,
+                p.g + int64_t(i) * (m + 1), p.h1 + int64_t(i) * kPartStride, p.h2 + int64_t(i) * kPartStride,
+                p.nrm + int64_t(i) * kPartStride, p.scal + int64_t(i) * 8 + 4, p.scal + int64_t(i) * 8,
+                p.brk + i, p.scal + int64_t(i) * 8 + 1);
+}
+void launch_givens_slots(int S, const SlotGivens& p, cudaStream_t st) {
+  HZ_COUNT();
+  k_givens_slots<<<S, 32, 0, st>>>(p);
+}
+__global__ void k_scale_slots(int64_t n, SlotScale p) {
+  const int i = blockIdx.y;
+  if (!p.out[i]) return;
+  const double a = *p.s[i];
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x)
+    p.out[i][r] = make_double2(p.w[i][r].x * a, p.w[i][r].y * a);
+}
+void launch_scale_slots(int64_t n, int S, const SlotScale& p, cudaStream_t st) {
+  HZ_COUNT();
+  k_scale_slots<<<dim3(std::max(1u, grid_for(n, 256) / unsigned(S)), S), 256, 0, st>>>(n, p);
 }
 
 // out[:, q] (+)= sign * (sum_i B1[:, i] coef[i, q] + sum_i B2[:, i] coef[nb1 + i, q]), q < nout:
