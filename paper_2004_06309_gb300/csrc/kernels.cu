@@ -779,9 +779,12 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
 // with 16-byte loads; the right-hand side b1 is gathered once per task.  CG = 2 (256
 // rows) where a tree level has many supernodes; CG = 8 (64 rows, each warp one column
 // group) on sparse levels, where a task's serial walk over its columns, not bandwidth,
-// sets the time.
+// sets the time.  In both, a thread's first 8 panel values are loaded, and the update
+// rows' child contributions b2 gathered, before the barrier that publishes b1, so the
+// load chains overlap; every sum keeps the order of the column loop (even q on one
+// chain, odd q on the other).
 template <int CG>
-__global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+__global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                                  const int64_t* cidx, const float2* panels, const float2* tin,
                                                  float2* zout, float2* u) {
   constexpr int NP = 256 / CG;                       // row pairs per task
@@ -794,11 +797,9 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
   const int pr = tid % NP, cg = tid / NP;
   const int64_t* cp = cptr + S.rowoff;
   const int r = t.y * ROWS + 2 * pr;                 // rows r, r + 1 (r even, ld % 4 == 0)
-  float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
+  const int rr = t.y * ROWS + tid;                   // update row finished by this thread
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0, b2 = a0;
   if constexpr (CG == 8) {
-    // sparse levels: this thread's (at most kMaxK / 8) panel values are loaded before the
-    // right-hand side is gathered, so the two latency chains overlap; the sums run in the
-    // order of the loop below (even q on one chain, odd q on the other)
     constexpr int MQ = kMaxK / CG, PF = 8;              // PF of the MQ columns are prefetched
     float4 pv[MQ];
     const int j0 = min(r, k), j1 = min(r + 1, k);
@@ -814,6 +815,8 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
       for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
       b1[jj] = acc;
     }
+    if (tid < ROWS && rr >= k && rr < m)
+      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
     __syncthreads();
     if (r < m) {
 #pragma unroll
@@ -833,50 +836,69 @@ __global__ void __launch_bounds__(256) k_fwd_c64(const int2* tasks, const SnDev*
       }
     }
   } else {
-  for (int jj = tid; jj < k; jj += blockDim.x) {
-    float2 acc = tin[S.first + jj];
-    for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
-    b1[jj] = acc;
-  }
-  __syncthreads();
-  if (r < m) {
-    const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + r);
-    const int64_t ld4 = S.ld / 2;
+    constexpr int PF = 8;                              // columns q < PF are prefetched
+    float4 pv[PF];
     const int j0 = min(r, k), j1 = min(r + 1, k);
-    int j = cg;
-    for (; j + CG < j1; j += 2 * CG) {                 // two independent chains
-      const float4 p = P4[int64_t(j) * ld4];
-      const float4 q = P4[int64_t(j + CG) * ld4];
-      const float2 bj = b1[j], bq = b1[j + CG];
-      a1 = cmad(make_float2(p.z, p.w), bj, a1);
-      c1 = cmad(make_float2(q.z, q.w), bq, c1);
-      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
-      if (j + CG < j0) c0 = cmad(make_float2(q.x, q.y), bq, c0);
+    const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + (r < m ? r : 0));
+    const int64_t ld4 = S.ld / 2;
+#pragma unroll
+    for (int q = 0; q < PF; q++) {
+      const int j = cg + CG * q;
+      pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (j < j1) {
-      const float4 p = P4[int64_t(j) * ld4];
-      const float2 bj = b1[j];
-      a1 = cmad(make_float2(p.z, p.w), bj, a1);
-      if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+    for (int jj = tid; jj < k; jj += blockDim.x) {
+      float2 acc = tin[S.first + jj];
+      for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+      b1[jj] = acc;
     }
-  }
+    if (tid < ROWS && rr >= k && rr < m)
+      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+    __syncthreads();
+    if (r < m) {
+#pragma unroll
+      for (int q = 0; q < PF; q++) {
+        const int j = cg + CG * q;
+        if (j < j1) {
+          const float2 bj = b1[j];
+          if (q % 2 == 0) {
+            a1 = cmad(make_float2(pv[q].z, pv[q].w), bj, a1);
+            if (j < j0) a0 = cmad(make_float2(pv[q].x, pv[q].y), bj, a0);
+          } else {
+            c1 = cmad(make_float2(pv[q].z, pv[q].w), bj, c1);
+            if (j < j0) c0 = cmad(make_float2(pv[q].x, pv[q].y), bj, c0);
+          }
+        }
+      }
+      int j = cg + CG * PF;
+      for (; j + CG < j1; j += 2 * CG) {               // two independent chains
+        const float4 p = P4[int64_t(j) * ld4];
+        const float4 q = P4[int64_t(j + CG) * ld4];
+        const float2 bj = b1[j], bq = b1[j + CG];
+        a1 = cmad(make_float2(p.z, p.w), bj, a1);
+        c1 = cmad(make_float2(q.z, q.w), bq, c1);
+        if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+        if (j + CG < j0) c0 = cmad(make_float2(q.x, q.y), bq, c0);
+      }
+      if (j < j1) {
+        const float4 p = P4[int64_t(j) * ld4];
+        const float2 bj = b1[j];
+        a1 = cmad(make_float2(p.z, p.w), bj, a1);
+        if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+      }
+    }
   }
   part[cg][2 * pr] = cadd(a0, c0);
   part[cg][2 * pr + 1] = cadd(a1, c1);
   __syncthreads();
-  const int rr = t.y * ROWS + tid;
   if (tid < ROWS && rr < m) {
     float2 tot = part[0][tid];
 #pragma unroll
     for (int q = 1; q < CG; q++) tot = cadd(tot, part[q][tid]);
     const float2* P = panels + S.paneloff;
-    if (rr < k) {
+    if (rr < k)
       zout[S.first + rr] = cmul(P[rr + int64_t(rr) * S.ld], cadd(b1[rr], tot));
-    } else {
-      float2 b2 = make_float2(0.f, 0.f);
-      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+    else
       u[S.uoff + (rr - k)] = csub(b2, tot);
-    }
   }
 }
 
