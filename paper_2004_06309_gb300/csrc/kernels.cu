@@ -718,6 +718,8 @@ __device__ __forceinline__ void bwd_finish(const int4 fin, const SnDev& S, const
 // sums are then added in a fixed order.  No shuffle reductions on the FP64 pipe.
 // PF (narrow chunks of at most 64 rows, sparse levels): each thread's <= 8 panel values are
 // loaded before the chunk's right-hand side is gathered; the sums keep the loop's order.
+// A supernode that fits in one chunk is finished by its own CTA, with the same sums, without
+// the partial-sum round trip and ticket of bwd_finish.
 template <bool PF>
 __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, const SnDev* sn,
                                                           const int32_t* rowlist, const double2* panels,
@@ -766,12 +768,16 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
   }
   red[s][c] = cadd(a0, a1);
   __syncthreads();
+  const bool single = m <= rows;                     // the only chunk: finish here, no ticket
   if (s == 0) {
     double2 tot = red[0][c];
     for (int q = 1; q < 8; q++) tot = cadd(tot, red[q][c]);
-    partial[int64_t(blockIdx.x) * 32 + c] = tot;
+    if (!single)
+      partial[int64_t(blockIdx.x) * 32 + c] = tot;
+    else if (j < k)
+      x[S.first + j] = cadd(zin[S.first + j], cadd(make_double2(0.0, 0.0), tot));
   }
-  bwd_finish<double2>(fins[t.w], S, zin, partial, x, counters + t.w);
+  if (!single) bwd_finish<double2>(fins[t.w], S, zin, partial, x, counters + t.w);
 }
 
 // complex64 forward, 512 / CG rows of one supernode per task: thread t owns the row
@@ -905,6 +911,8 @@ __global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnD
 // complex64 backward partial sums with 16-byte loads (two rows per lane).  PF (narrow
 // chunks of at most 128 rows, sparse levels): each lane's <= 2 row pairs of its 4 columns
 // are loaded before the chunk's right-hand side is gathered; the sums keep their order.
+// A supernode that fits in one chunk is finished by its own CTA (lane 0 of each column's
+// warp), with the same sums, without the partial-sum round trip and ticket of bwd_finish.
 template <bool PF>
 __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, const SnDev* sn,
                                                          const int32_t* rowlist, const float2* panels,
@@ -934,6 +942,7 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
     vec[r - r0] = (r < r1) ? ((r < k) ? zin[S.first + r] : cneg(x[rl[r]])) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* out = partial + int64_t(blockIdx.x) * 32;
+  const bool single = m <= rows;                     // the only chunk: finish here, no ticket
   const float4* vec4 = reinterpret_cast<const float4*>(vec);
 #pragma unroll
   for (int q = 0; q < 4; q++) {
@@ -965,9 +974,14 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) out[c] = acc;
+    if (lane == 0) {
+      if (!single)
+        out[c] = acc;
+      else if (j < k)
+        x[S.first + j] = cadd(zin[S.first + j], cadd(make_float2(0.f, 0.f), acc));
+    }
   }
-  bwd_finish<float2>(fins[t.w], S, zin, partial, x, counters + t.w);
+  if (!single) bwd_finish<float2>(fins[t.w], S, zin, partial, x, counters + t.w);
 }
 
 template <typename V>
