@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -46,6 +47,13 @@ FULL_WORKLOAD_ITERATIONS = 74
 LOCAL_SWEEP_TRAFFIC_RATIO = 1.017
 # Oracle sample for the CPU baseline / reference arm: same generator, 1/43 of the dofs.
 ORACLE_SAMPLE = dict(kind="overthrust", cells=None, freq=1.25, nsub=8, overlap=2, restart=50)
+
+
+def clocks_dir(args):
+    """Folder for the clock-sample CSV written during the timed region."""
+    d = args.clocks_dir or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return d
 
 
 def synth_cells(spec):
@@ -224,8 +232,7 @@ def serve_bench(args):
         rate = 0.7 * cap / ((1 + args.serve_batch) / 2.0)        # ~70 % of the measured capacity
         stream = serve_requests(np.random.default_rng(12), args.steps, rate, args.serve_batch)
         s0 = srv.stats()
-        clocks = Clocks(0, os.path.join(ROOT, "gpurun_out", f"clocks_serve_{pname}.csv")) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(0, f"/tmp/clocks_serve_{pname}.csv")
+        clocks = Clocks(0, os.path.join(clocks_dir(args), f"clocks_serve_{pname}.csv"))
         done = []
         lock = threading.Lock()
 
@@ -366,6 +373,8 @@ def main():
     ap.add_argument("--serve-batch", type=int, default=16, help="largest sources per request (serving)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default="",
+                    help="folder for the nvidia-smi clock samples of the timed region (default: system temp)")
     ap.add_argument("--block", type=int, default=0,
                     help="pseudo-block FGMRES block size (right-hand sides sharing each operator application)")
     ap.add_argument("--nrhs", type=int, default=1,
@@ -469,8 +478,7 @@ def main():
         for _ in range(args.warmup):
             x, info = G.solve(b_dev)
         st0 = G.stats()["launches"]
-        clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_{pname}_r{rank}.csv")) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/clocks_{pname}.csv")
+        clocks = Clocks(local, os.path.join(clocks_dir(args), f"clocks_{pname}_r{rank}.csv"))
         barrier()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev[0].record(stream)
