@@ -311,6 +311,45 @@ def global_system(problem, freq=None):
     return apply_dirichlet(A, dd), dm, dd
 
 
+def sampled_rows(problem, rows, freq=None, dm=None):
+    """Rows ``rows`` of the assembled global A of ``global_system`` (Eq. 1-2, after the
+    symmetric Dirichlet elimination), for problems too large to assemble whole.
+
+    Row i of the assembled matrix is the sum of the element terms of the elements whose
+    dof lists hold i and of the absorbing-face terms of the faces whose dof lists hold
+    i; no other term touches it.  So the assembly is restricted to exactly those
+    elements and faces, and the requested rows are read off.  The owner of such a face
+    holds the face, hence dof i, so it is among the kept elements.  The elimination then
+    zeroes the Dirichlet columns of every row and turns Dirichlet rows into identity
+    rows, as ``apply_dirichlet`` does for the whole matrix.
+
+    Returns (rows of A as CSR, shape (len(rows), n), the DofMap, the Dirichlet dofs).
+    """
+    freq = problem.freq if freq is None else freq
+    mesh = problem.mesh
+    if dm is None:
+        dm = DofMap(mesh.xyz, mesh.tets, problem.order)
+    rows = np.asarray(rows, np.int64)
+    want = np.zeros(dm.n, bool)
+    want[rows] = True
+    elems = np.nonzero(want[dm.elem_dofs].any(axis=1))[0]
+    abc = mesh.faces[mesh.face_tag == TAG_ABC]
+    if len(abc):
+        abc = abc[want[dm.face_dofs(abc)].any(axis=1)]
+    owner = elems[face_owner(mesh.tets[elems], abc)] if len(abc) else np.zeros(0, np.int64)
+    _, K, Mp, Bp = assemble_parts(mesh, problem.c, problem.order, elems=elems, faces=abc,
+                                  face_coef_elem=owner, dm=dm)
+    A = helmholtz_matrix(K, Mp, Bp, freq)[rows]
+    dd = dm.dirichlet_dofs(mesh.faces, mesh.face_tag)
+    keep = np.ones(dm.n)
+    keep[dd] = 0.0
+    ident = sp.coo_matrix((1.0 - keep[rows], (np.arange(len(rows)), rows)), shape=A.shape)
+    out = (sp.diags(keep[rows]) @ A @ sp.diags(keep) + ident).tocsr()
+    out.eliminate_zeros()
+    out.sort_indices()
+    return out, dm, dd
+
+
 def locate(xyz, tets, pts):
     """For each point, the lowest-index tet that contains it and its barycentrics."""
     out_e = np.empty(len(pts), np.int64)

@@ -1,0 +1,72 @@
+"""GPU parity at the full size bench.py times: the 5 Hz Overthrust-shaped workload
+(coarse (63, 63, 9) cells, 2,368,333 P2 dofs, 64 subdomains, overlap 2, two levels,
+FGMRES(50), the source at (2.5, 2.5, 0.58) km), one right-hand side resident on the
+device, in both precisions.
+
+The oracle cannot assemble or solve this size in seconds, so it is compared on outputs
+it computes one by one (``fem.sampled_rows``: each row of A from only the elements and
+absorbing faces holding its dof):
+- the point-source right-hand side, entry by entry over all dofs;
+- sampled rows of ``hz_apply_A`` applied to the GPU solution, per row to 1e-13 of the
+  row's absolute sum (the same element terms summed in another order);
+- sampled rows of the true residual b - A x of the GPU solution: each |r_i| is at most
+  ||b - A x||, so each is bounded by tol * ||b|| (plus the rounding above).
+
+The sample holds Dirichlet rows, rows on the absorbing boundary, the source's rows and
+2,000 seeded random rows across every subdomain."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def hzmod():
+    from paper_2004_06309_gb300 import build, hz
+    build.build()
+    return hz
+
+
+@pytest.fixture(scope="module")
+def full():
+    p = synth.overthrust_problem(seed=0, freq=5.0, nsub=64, overlap=2, restart=50, levels=2)
+    dm = fem.DofMap(p.mesh.xyz, p.mesh.tets, p.order)
+    assert dm.n == 2368333
+    dd = dm.dirichlet_dofs(p.mesh.faces, p.mesh.face_tag)
+    b_ref = fem.point_sources(p, dm, dd, p.sources)[:, 0]
+    abc = p.mesh.faces[p.mesh.face_tag == fem.TAG_ABC]
+    on_abc = np.setdiff1d(np.unique(dm.face_dofs(abc).ravel()), dd)
+    rng = np.random.default_rng(11)
+    rows = np.unique(np.concatenate([rng.choice(dd, 50, replace=False), rng.choice(on_abc, 200, replace=False),
+                                     np.nonzero(b_ref)[0], rng.choice(dm.n, 2000, replace=False)]))
+    R = fem.sampled_rows(p, rows, dm=dm)[0]
+    return p, b_ref, rows, R
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_solve_against_sampled_oracle_rows(hzmod, full, precision):
+    import torch
+    p, b_ref, rows, R = full
+    G = hzmod.Solver(p, precision=hzmod.HZ_MIXED if precision == "mixed" else hzmod.HZ_FP64)
+    try:
+        G.factor()
+        assert G.n == len(b_ref)
+        b = G.point_sources()[:, 0]
+        assert np.abs(b - b_ref).max() <= 1e-14 * np.abs(b_ref).max()
+        x_dev, info = G.solve(torch.from_numpy(b).cuda(), tol=TOL)
+        its, status, rel = info[0]
+        assert status == 0 and 0 < its and rel <= TOL, info
+        y = G.apply_A(x_dev.contiguous()).cpu().numpy()
+        x = x_dev.cpu().numpy()
+    finally:
+        G.close()
+    Ax = R @ x
+    scale = abs(R) @ np.abs(x)
+    assert np.all(np.abs(y[rows] - Ax) <= 1e-13 * scale), np.abs(y[rows] - Ax).max()
+    r = b_ref[rows] - Ax
+    assert np.all(np.abs(r) <= TOL * np.linalg.norm(b_ref) + 1e-13 * scale), np.abs(r).max()

@@ -195,3 +195,30 @@ def test_point_source_at_vertex_is_unit_vector():
     v = 6 + 13 * (6 + 13 * 6)
     e = np.zeros(dm.n); e[v] = -1.0
     assert np.allclose(b, e, atol=1e-14)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.unit_cube_problem(n=5, order=2, nsub=4, overlap=1, freq=1.5),
+    lambda: synth.small_overthrust(levels=2, cells=(4, 4, 2), freq=0.5, nsub=8),
+    lambda: synth.unit_cube_problem(n=6, order=1, nsub=4, overlap=1, freq=1.2),
+], ids=["cube_p2", "overthrust_p2", "cube_p1"])
+def test_sampled_rows_equal_rows_of_the_global_system(make):
+    """Rows assembled from only the elements and absorbing faces holding their dof are the
+    rows of the whole assembly: Dirichlet rows, absorbing-boundary rows, vertex and edge
+    dofs, interior rows, and an unsorted sample with a repeated row."""
+    p = make()
+    A, dm, dd = fem.global_system(p)
+    B = fem.global_system(p, freq=0.8 * p.freq)[0]
+    abc = p.mesh.faces[p.mesh.face_tag == fem.TAG_ABC]
+    on_abc = np.setdiff1d(np.unique(dm.face_dofs(abc).ravel()), dd)
+    rng = np.random.default_rng(4)
+    rows = np.concatenate([dd[:5], on_abc[:7], rng.choice(dm.n, 40, replace=False), [dm.n - 1, 0, 0]])
+    assert len(dd) and len(on_abc) and (p.order == 1 or dm.n - 1 >= dm.nv)   # every kind of row
+    R, dm2, dd2 = fem.sampled_rows(p, rows)
+    assert np.array_equal(dd2, dd)
+    ref = A[rows].toarray()
+    got = R.toarray()
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+    assert np.array_equal(got != 0, ref != 0)                        # same sparsity, no dropped term
+    Rf = fem.sampled_rows(p, rows, freq=0.8 * p.freq, dm=dm)[0].toarray()
+    assert np.abs(Rf - B[rows].toarray()).max() <= 1e-14 * np.abs(ref).max()
