@@ -674,11 +674,12 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
 //   vec = (z, -x[ancestor rows]) for 32 pivot columns j of one supernode;
 // then x[j] = z[j] + sum of the partials in chunk order (deterministic).
 constexpr int kBwdRows = 512;
-// Fused second stage of the backward sweep ("last block done"): every partial-sum
-// CTA of a (supernode, column block) publishes its 32 sums, fences, and bumps the
-// pair's counter; the CTA that brings it to `chunks` adds the partials in chunk
-// order (deterministic), writes x, and resets the counter for the next sweep.
-// No CTA ever waits on another.
+// Fused second stage of the backward sweep ("last block done"), for a (supernode,
+// column block) split over several row chunks: every partial-sum CTA of the pair
+// publishes its 32 sums, fences, and bumps the pair's counter; the CTA that brings it
+// to `chunks` adds the partials in chunk order (deterministic), writes x, and resets
+// the counter for the next sweep.  No CTA ever waits on another.  (The single-chunk
+// case finishes inside its own CTA and never touches the counter.)
 template <typename V>
 __device__ __forceinline__ void bwd_finish(const int4 fin, const SnDev& S, const V* zin, const V* partial_level,
                                            V* x, unsigned int* counter) {
