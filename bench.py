@@ -387,6 +387,8 @@ def main():
     ap.add_argument("--coarse-maxit", type=int, default=0, help="inner coarse iterations at most (0: default)")
     ap.add_argument("--recycle", type=int, default=0,
                     help="GCRO-DR: recycled-space dimension kept across the step's right-hand sides (0: FGMRES)")
+    ap.add_argument("--one-level-steps", type=int, default=3,
+                    help="timed steps of the one-level arm on the same mesh (mixed precision; 0: skip)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -509,6 +511,38 @@ def main():
         del G
         torch.cuda.empty_cache()
 
+    # one-level arm (Eq. 4 alone) on the same mesh and partition, mixed precision: shows
+    # where the coarse space pays and where it does not (its resolution, not the method)
+    one = None
+    if args.one_level_steps > 0 and prob.levels == 2 and "mixed" in precs and args.nrhs == 1:
+        import dataclasses
+        p1 = dataclasses.replace(prob, levels=1, coarse=None, fine_parent=None)
+        G = hz.Solver(p1, precision=hz.HZ_MIXED, stream=stream, leaf_size=args.leaf, max_snode=args.maxsn)
+        tf = time.time()
+        G.factor()
+        torch.cuda.synchronize()
+        t_factor1 = time.time() - tf
+        b1 = torch.from_numpy(G.point_sources(prob.sources)[:, 0].copy()).cuda()
+        for _ in range(min(args.warmup, 2)):
+            G.solve(b1)
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.one_level_steps + 1)]
+        ev[0].record(stream)
+        its1 = []
+        for s in range(args.one_level_steps):
+            x1, info1 = G.solve(b1)
+            ev[s + 1].record(stream)
+            its1.append(info1[0][0])
+        barrier()
+        ms1 = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.one_level_steps)]
+        tot1 = maxall(sum(ms1))
+        one = dict(value=world * args.one_level_steps / (tot1 / 1e3), ms_per_step=tot1 / args.one_level_steps,
+                   iterations=its1[-1], rel_residual=info1[0][2], factor_seconds=t_factor1,
+                   latency_ms={"p50": float(np.percentile(ms1, 50)), "p99": float(np.percentile(ms1, 99))})
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -588,6 +622,9 @@ def main():
                         "phases_ms": {k: round(v["ms"], 4) for k, v in F["profile"].items()},
                         "phases_gflops": {k: round(v["flops"] / 1e9, 4) for k, v in F["profile"].items()},
                         "clocks": F["clocks"]}
+    if one is not None:
+        line["one_level"] = dict(one, precision="mixed",
+                                 note="levels=1 on the same mesh and partition; no coarse space")
     if not args.no_cpu_baseline and world == 1:
         try:
             samp = oracle_subprocess(1, 1)

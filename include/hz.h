@@ -124,6 +124,24 @@ typedef struct {
                                add restart - k Arnoldi vectors.  hz_factor drops the
                                space.  0 = off (FGMRES); 1 <= k <= min(16, restart/2);
                                one right-hand side at a time (block_size <= 1).      */
+  /* Task shapes of the batched triangular sweeps (A_i^{-1} of Eq. 4 and the coarse
+     E^{-1} of Eq. 3).  Results differ only by the rounding of the summation order.  */
+  int32_t sweep_tasks;      /* 0: chosen per assembly-tree level from its task count
+                               (levels with fewer tasks than the GPU holds at once get
+                               narrow tasks); 1: wide tasks on every level; 2: narrow
+                               tasks on every level.  Wide: 256-row forward tasks and
+                               bwd_chunk-row backward chunks (complex64), 64 / bwd_chunk
+                               (complex128); narrow: 64 / 128 (complex64), 16 / 64
+                               (complex128).                                          */
+  int32_t bwd_chunk;        /* rows of a wide backward chunk; 0: 512 for complex64 local
+                               factors, 256 otherwise; else even, in [32, 512].  A
+                               supernode taller than a chunk sums its chunks' partial
+                               results in a fixed order in the CTA that finishes last. */
+  int32_t tc_wait_limit;    /* complex64 factorisation: polls of the first bounded wait
+                               on each tensor-core completion barrier; 0: 2^22; < 0:
+                               none, so that wait runs out at once (a test of the
+                               HZ_ERR_TIMEOUT path).  The wait that drains MMAs still in
+                               flight before tensor memory is freed keeps 2^22.       */
 } hz_options;
 
 typedef struct {
@@ -154,6 +172,19 @@ typedef struct {
   int64_t coarse_solves;    /* iterative coarse solve: inner solves since hz_factor    */
   int64_t coarse_iterations;/* ... and their inner GMRES iterations in total           */
   int64_t recycle_dim;      /* GCRO-DR: dimension of the recycled space held now       */
+  /* Kernel variants of the local factors (fixed by the symbolic analysis and the
+     options; hz_plan reports them too), so that a caller can tell which code paths a
+     run takes. */
+  int32_t fwd_levels_wide;  /* tree levels swept forward with wide tasks                */
+  int32_t fwd_levels_narrow;/* ... with narrow tasks                                    */
+  int32_t bwd_levels_wide;  /* tree levels swept backward in wide row chunks            */
+  int32_t bwd_levels_narrow;/* ... in narrow row chunks                                 */
+  int64_t bwd_split_blocks; /* 32-column blocks whose backward sums span several row
+                               chunks (added up by the CTA that finishes last)        */
+  int64_t tc_tiles;         /* complex64: 128 x 128 tensor-core tiles of Schur updates  */
+  int64_t tc_multi_fronts;  /* complex64: fronts whose update spans several tiles       */
+  int32_t tc_max_kstages;   /* complex64: most 32-deep K stages of one tile (2k / 32)   */
+  int32_t max_snode_width;  /* widest local supernode (pivot columns)                   */
 } hz_stats;
 
 /* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */
@@ -242,7 +273,10 @@ hz_status hz_cgs2(hz_ctx* ctx, const void* V, int64_t ldv, int32_t ncols, void* 
    until the process exits.  ncols outside [1, 64] returns HZ_ERR_ARG with a
    message on stderr.  The first call on a device looks the array's device address
    up (cudaGetSymbolAddress, once per device, with that device current); make that
-   first call before any stream capture.  All calls share the array and it keeps
+   first call before any stream capture.  The address stays cached for the life of
+   the process: after a cudaDeviceReset (or any teardown of the device's primary
+   context) the cached address is stale, so do not call this entry point again in
+   that process.  All calls share the array and it keeps
    the last call's contents: calls that overlap on the GPU (different streams, or
    different host threads on one device) race on it and must be serialised by the
    caller. */

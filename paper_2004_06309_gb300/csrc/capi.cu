@@ -174,9 +174,64 @@ std::vector<double2> to_d2(const std::vector<cplx>& v) {
 }
 
 // Device copy of a symbolic set with its task lists.
+// Task shapes of the batched triangular sweeps per assembly-tree level, and the kernel
+// variants they imply (host-only; shared by the device upload and hz_plan).
+// Sparse tree levels get narrow tasks.  complex128 (FP64 arithmetic bound): fewer
+// tasks than two per SM -> 16-row forward tasks, 64-row backward chunks, so that such a
+// level reaches every SM.  complex64: fewer tasks than one resident wave (8 CTAs per
+// SM) -> 64-row forward tasks and 128-row backward chunks, which shorten each task's
+// serial walk over its columns and rows (the time of a latency-bound level).
+// sweep_tasks (hz_options) forces wide (1) or narrow (2) shapes on every level.
+struct SweepPlan {
+  std::vector<int> fwd_rt, bwd_rows;   // per level: forward task rows, backward chunk rows
+  int32_t fwd_wide = 0, fwd_narrow = 0, bwd_wide = 0, bwd_narrow = 0;
+  int64_t bwd_split = 0, tc_tiles = 0, tc_multi = 0;
+  int32_t tc_kstages = 0, max_k = 0;
+};
+
+SweepPlan plan_sweeps(const hz::SymbolicSet& S, int precision, int bwd_rows, int sweep_tasks) {
+  SweepPlan sp;
+  const int nlev = S.nlev;
+  const int wide = precision == 0 ? 64 : 256;
+  sp.fwd_rt.assign(nlev, wide);
+  sp.bwd_rows.assign(nlev, bwd_rows);
+  for (int l = 0; l < nlev; l++) {
+    int64_t nf = 0, nbk = 0;
+    for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+      const int s = S.lev_sn[q];
+      nf += (S.sn_m[s] + wide - 1) / wide;
+      nbk += int64_t((S.sn_k[s] + 31) / 32) * ((S.sn_m[s] + bwd_rows - 1) / bwd_rows);
+    }
+    const int64_t sparse = precision == 0 ? 2 * 152 : 8 * 152;
+    const bool narrow_f = sweep_tasks == 2 || (sweep_tasks == 0 && nf < sparse);
+    const bool narrow_b = sweep_tasks == 2 || (sweep_tasks == 0 && nbk < sparse);
+    if (narrow_f) sp.fwd_rt[l] = precision == 0 ? 16 : 64;
+    if (narrow_b) sp.bwd_rows[l] = std::min(bwd_rows, precision == 0 ? 64 : 128);
+    if (S.lev_ptr[l + 1] == S.lev_ptr[l]) continue;
+    // the launchers pick the narrow kernels by shape (forward rows; chunk <= 128 / 64 rows)
+    (narrow_f ? sp.fwd_narrow : sp.fwd_wide)++;
+    (sp.bwd_rows[l] > (precision == 0 ? 64 : 128) ? sp.bwd_wide : sp.bwd_narrow)++;
+    for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
+      const int s = S.lev_sn[q];
+      const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
+      if ((m + sp.bwd_rows[l] - 1) / sp.bwd_rows[l] > 1) sp.bwd_split += (k + 31) / 32;
+      sp.max_k = std::max(sp.max_k, k);
+      if (precision == 1 && r > 0) {
+        const int64_t T = (r + 127) / 128;
+        sp.tc_tiles += T * (T + 1) / 2;
+        if (T > 1) sp.tc_multi++;
+        sp.tc_kstages = std::max(sp.tc_kstages, (2 * k + 31) / 32);
+      }
+    }
+  }
+  return sp;
+}
+
+// sweep_tasks / bwd_chunk: hz_options fields of the same names (task shapes per level).
 hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
-                        double maxabs[3], int bwd_rows, int nrhs_block) {
+                        double maxabs[3], int bwd_rows, int nrhs_block, int sweep_tasks, int bwd_chunk) {
   F = hz::FactorDev();
+  if (bwd_chunk > 0) bwd_rows = bwd_chunk;
   F.bwd_rows = bwd_rows;
   F.precision = precision;
   F.nmat = S.nmat;
@@ -282,24 +337,18 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
       cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1), tc_ptr(nlev + 1);
   int64_t scratch = 0;
-  // Sparse tree levels get narrow tasks.  complex128 (FP64 arithmetic bound): fewer
-  // tasks than two per SM -> 16-row forward tasks, 64-row backward chunks, so that such a
-  // level reaches every SM.  complex64: fewer tasks than one resident wave (8 CTAs per
-  // SM) -> 64-row forward tasks and 128-row backward chunks, which shorten each task's
-  // serial walk over its columns and rows (the time of a latency-bound level).
-  const int wide = precision == 0 ? 64 : 256;
-  std::vector<int> fwd_rt(nlev, wide), lev_bwd_rows(nlev, bwd_rows);
-  for (int l = 0; l < nlev; l++) {
-    int64_t nf = 0, nbk = 0;
-    for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
-      const int s = S.lev_sn[q];
-      nf += (S.sn_m[s] + wide - 1) / wide;
-      nbk += int64_t((S.sn_k[s] + 31) / 32) * ((S.sn_m[s] + bwd_rows - 1) / bwd_rows);
-    }
-    const int64_t sparse = precision == 0 ? 2 * 152 : 8 * 152;
-    if (nf < sparse) fwd_rt[l] = precision == 0 ? 16 : 64;
-    if (nbk < sparse) lev_bwd_rows[l] = std::min(bwd_rows, precision == 0 ? 64 : 128);
-  }
+  const SweepPlan sp = plan_sweeps(S, precision, bwd_rows, sweep_tasks);
+  const std::vector<int>& fwd_rt = sp.fwd_rt;
+  const std::vector<int>& lev_bwd_rows = sp.bwd_rows;
+  F.v_fwd_wide = sp.fwd_wide;
+  F.v_fwd_narrow = sp.fwd_narrow;
+  F.v_bwd_wide = sp.bwd_wide;
+  F.v_bwd_narrow = sp.bwd_narrow;
+  F.v_bwd_split = sp.bwd_split;
+  F.v_tc_tiles = sp.tc_tiles;
+  F.v_tc_multi = sp.tc_multi;
+  F.v_tc_kstages = sp.tc_kstages;
+  F.v_max_k = sp.max_k;
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
     fwd_ptr[l] = int64_t(fwd.size());
@@ -525,7 +574,10 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
     std::fprintf(stderr, "[hz] factor: status read and workspace freed in %.3f s\n",
                  std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
   min_pivot = std::min(min_pivot, out.min_pivot);
-  if (out.timeout) return fail(c, HZ_ERR_TIMEOUT, "a tensor-core completion wait ran out in the factorisation");
+  if (out.timeout)
+    return fail(c, HZ_ERR_TIMEOUT, (out.timeout & 2u)
+                                       ? "a tensor-core completion wait and its drain wait ran out in the factorisation"
+                                       : "a tensor-core completion wait ran out in the factorisation");
   if (out.zero_pivot) return fail(c, HZ_ERR_ZERO_PIVOT, "tiny pivot in a local LDL^T factor");
   return HZ_OK;
 }
@@ -1381,6 +1433,9 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     return fail(c, HZ_ERR_ARG, "recycle must be in [0, min(16, restart / 2)]");
   if (op->recycle > 0 && op->block_size > 1)
     return fail(c, HZ_ERR_ARG, "recycle and block_size > 1 are exclusive");
+  if (op->sweep_tasks < 0 || op->sweep_tasks > 2) return fail(c, HZ_ERR_ARG, "sweep_tasks must be 0, 1 or 2");
+  if (op->bwd_chunk != 0 && (op->bwd_chunk < 32 || op->bwd_chunk > 512 || op->bwd_chunk % 2 != 0))
+    return fail(c, HZ_ERR_ARG, "bwd_chunk must be 0 or even in [32, 512]");
   const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
   for (int64_t q = 0; q < ne * 4; q++)
     if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
@@ -1516,6 +1571,21 @@ extern "C" hz_status hz_plan(const hz_mesh_desc* md, const hz_options* op, hz_st
     return s;
   }
   fill_stats(&tmp, P);
+  {
+    const int prec = op->precision == HZ_MIXED ? 1 : 0;
+    const int rows = op->bwd_chunk > 0 ? op->bwd_chunk : (prec == 1 ? 512 : 256);
+    const SweepPlan sp = plan_sweeps(P.local, prec, rows, op->sweep_tasks);
+    hz_stats& st = tmp.stats;
+    st.fwd_levels_wide = sp.fwd_wide;
+    st.fwd_levels_narrow = sp.fwd_narrow;
+    st.bwd_levels_wide = sp.bwd_wide;
+    st.bwd_levels_narrow = sp.bwd_narrow;
+    st.bwd_split_blocks = sp.bwd_split;
+    st.tc_tiles = sp.tc_tiles;
+    st.tc_multi_fronts = sp.tc_multi;
+    st.tc_max_kstages = sp.tc_kstages;
+    st.max_snode_width = sp.max_k;
+  }
   tmp.stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // device bytes a context would hold after hz_factor (excluding transient fronts)
   int64_t persistent = 0, transient = 0;
@@ -1563,7 +1633,22 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
     }
   }
   SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max,
-                          op->precision == HZ_MIXED ? 512 : 256, c->S));
+                          op->precision == HZ_MIXED ? 512 : 256, c->S, op->sweep_tasks, op->bwd_chunk));
+  {
+    const hz::FactorDev& F = c->loc;
+    hz_stats& st = c->stats;
+    st.fwd_levels_wide = F.v_fwd_wide;
+    st.fwd_levels_narrow = F.v_fwd_narrow;
+    st.bwd_levels_wide = F.v_bwd_wide;
+    st.bwd_levels_narrow = F.v_bwd_narrow;
+    st.bwd_split_blocks = F.v_bwd_split;
+    st.tc_tiles = F.v_tc_tiles;
+    st.tc_multi_fronts = F.v_tc_multi;
+    st.tc_max_kstages = F.v_tc_kstages;
+    st.max_snode_width = F.v_max_k;
+  }
+  const int tc_wait = op->tc_wait_limit == 0 ? (1 << 22) : std::max(op->tc_wait_limit, 0);
+  c->loc.tc_wait = tc_wait;
   if (c->levels == 2) {
     SETUP_TRY(upload(c, &c->d_Zrp, P.Z.ptr));
     SETUP_TRY(upload(c, &c->d_Zci, P.Z.col));
@@ -1576,7 +1661,8 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
       c->cmaxit = op->coarse_maxit > 0 ? op->coarse_maxit : 30;
       c->ctol = op->coarse_tol > 0.0 ? op->coarse_tol : 1e-2;
       SETUP_TRY(upload_factor(c, P.clocal, op->precision == HZ_MIXED ? 1 : 0, c->nH, c->cloc, c->cloc_max,
-                              op->precision == HZ_MIXED ? 512 : 256, 0));
+                              op->precision == HZ_MIXED ? 512 : 256, 0, op->sweep_tasks, op->bwd_chunk));
+      c->cloc.tc_wait = tc_wait;
       SETUP_TRY(upload(c, &c->d_Erp, P.E.pat.ptr));
       SETUP_TRY(upload(c, &c->d_Eci, P.E.pat.col));
       SETUP_TRY(upload(c, &c->d_EK, P.E.K));
@@ -1595,7 +1681,8 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
       SETUP_TRY(dalloc(c, &c->scalH, 8));
       SETUP_TRY(dalloc(c, &c->brkH, 1));
     } else {
-      SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S));
+      SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S, op->sweep_tasks,
+                              op->bwd_chunk));
     }
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));

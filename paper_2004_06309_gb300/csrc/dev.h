@@ -63,6 +63,11 @@ struct FactorDev {
   int* h_fwd_rt = nullptr;            // nlev: complex128 forward task rows (16 or 64)
   int* h_bwd_rows = nullptr;          // nlev: complex128 backward chunk rows
   int32_t max_slot = 0;
+  // kernel variants of the schedule (host-side counts, reported through hz_stats)
+  int32_t v_fwd_wide = 0, v_fwd_narrow = 0, v_bwd_wide = 0, v_bwd_narrow = 0;
+  int64_t v_bwd_split = 0, v_tc_tiles = 0, v_tc_multi = 0;
+  int32_t v_tc_kstages = 0, v_max_k = 0;
+  int32_t tc_wait = 1 << 22;          // polls of the first wait on a tensor-core completion barrier
   int64_t scratch_elems = 0;          // max over levels of sum (m-k) k
   // algorithmic cost of one forward+backward sweep (host-side)
   double solve_bytes = 0, solve_flops = 0;

@@ -320,8 +320,15 @@ __global__ void __launch_bounds__(256) k_cb(const int4* tasks, const SnDev* sn, 
 // accumulated in FP32 in tensor memory (Re: columns 0-127, Im: 128-255).
 // Operands are staged K-major in shared memory as 8-row x 16-byte core matrices
 // (no swizzle), 32 K-elements per stage.  Every wait on the MMA-completion
-// barrier is bounded: on timeout the CTA raises status->timeout, skips its
-// epilogue and still frees its tensor memory.
+// barrier is bounded.  The per-stage wait polls at most first_wait times; when it
+// runs out the CTA raises status->timeout (bit 0), skips its epilogue and drains
+// the MMAs it issued with a second wait of kTcDrainPolls polls before it frees
+// its tensor memory.  The MMAs read only this CTA's shared memory and write only
+// its tensor memory, so they finish in bounded time and the drain ends; should it
+// run out as well (a faulty tensor pipe), bit 1 is raised and the memory is still
+// freed, because a CTA that exits holding tensor memory would leave later
+// allocations on its SM waiting forever.  Either bit makes hz_factor return
+// HZ_ERR_TIMEOUT and leaves the context unfactored.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -343,9 +350,10 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, 
                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
                :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
-__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t phase) {
+constexpr int kTcDrainPolls = 1 << 22;
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t phase, int polls) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; it++)
+  for (int it = 0; it < polls && !done; it++)
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(smem_addr(mbar)), "r"(phase));
   return done != 0;
@@ -367,7 +375,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t ta, float* out) {
 
 constexpr int kTcSmemFloats = 6 * 128 * 32;   // Ah, Al, B1h, B1l, B2h, B2l: 96 KB
 __global__ void __launch_bounds__(128) k_cb_tc(const int4* tasks, const SnDev* sn, const int64_t* scr_off,
-                                               float2* fronts, const float2* scratch, DevStatus* status) {
+                                               float2* fronts, const float2* scratch, DevStatus* status,
+                                               int first_wait) {
   extern __shared__ __align__(1024) float tsm[];
   float* Ah = tsm;
   float* Al = Ah + 4096;
@@ -443,14 +452,14 @@ __global__ void __launch_bounds__(128) k_cb_tc(const int4* tasks, const SnDev* s
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_addr(&mbar)));
     }
-    const bool mine = tc_wait(&mbar, phase);
+    const bool mine = tc_wait(&mbar, phase, first_wait);
     ok = __syncthreads_and(mine) != 0;                 // block-uniform; the stage may be overwritten
     if (ok) phase ^= 1u;
   }
   if (!ok) {
-    if (tid == 0) atomicOr(&status->timeout, 1u);
-    tc_wait(&mbar, phase);                             // second bounded wait for MMAs still in flight
-    __syncthreads();
+    const bool drained = tc_wait(&mbar, phase, kTcDrainPolls);   // MMAs of the last stage still in flight
+    const bool all = __syncthreads_and(drained) != 0;
+    if (tid == 0) atomicOr(&status->timeout, all ? 1u : 3u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
@@ -540,7 +549,7 @@ static void factor_level_t(const FactorDev& F, int lev, double w, V* fronts, V* 
     if (te > tb) {
       HZ_COUNT();
       k_cb_tc<<<unsigned(te - tb), 128, kTcSmemFloats * sizeof(float), st>>>(F.tc_tasks + tb, F.sn, F.scr_off,
-                                                                            fronts, scratch, status);
+                                                                            fronts, scratch, status, F.tc_wait);
     }
   } else {
     const int64_t cbb = F.h_cb_ptr[lev], cbe = F.h_cb_ptr[lev + 1];

@@ -31,7 +31,8 @@ double2* g_scratch[kMaxDevices] = {};
 
 // The device address of g_cgs2_scratch for the current device.  The name of the
 // array in host code is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached for the life of the
+// process; a device reset in between would leave the cached address stale.
 hz_status scratch_address(double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -50,6 +50,7 @@ class Options(C.Structure):
         ("hbm_budget", C.c_uint64), ("elem_part", C.c_void_p), ("stream", C.c_void_p),
         ("block_size", C.c_int32), ("spmv_lanes", C.c_int32), ("coarse_solver", C.c_int32),
         ("coarse_maxit", C.c_int32), ("coarse_tol", C.c_double), ("recycle", C.c_int32),
+        ("sweep_tasks", C.c_int32), ("bwd_chunk", C.c_int32), ("tc_wait_limit", C.c_int32),
     ]
 
 
@@ -66,6 +67,9 @@ class Stats(C.Structure):
         ("factor_flops", C.c_double), ("setup_seconds", C.c_double), ("factor_seconds", C.c_double),
         ("min_pivot", C.c_double), ("launches", C.c_int64), ("coarse_solves", C.c_int64),
         ("coarse_iterations", C.c_int64), ("recycle_dim", C.c_int64),
+        ("fwd_levels_wide", C.c_int32), ("fwd_levels_narrow", C.c_int32), ("bwd_levels_wide", C.c_int32),
+        ("bwd_levels_narrow", C.c_int32), ("bwd_split_blocks", C.c_int64), ("tc_tiles", C.c_int64),
+        ("tc_multi_fronts", C.c_int64), ("tc_max_kstages", C.c_int32), ("max_snode_width", C.c_int32),
     ]
 
     def as_dict(self):
@@ -209,7 +213,8 @@ class _MeshArrays:
 
 def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=2000, leaf_size=0,
                  max_snode=0, hbm_budget=0, elem_part=None, stream=0, block_size=0, spmv_lanes=0,
-                 coarse_solver=0, coarse_maxit=0, coarse_tol=0.0, recycle=0):
+                 coarse_solver=0, coarse_maxit=0, coarse_tol=0.0, recycle=0, sweep_tasks=0, bwd_chunk=0,
+                 tc_wait_limit=0):
     o = Options()
     o.nsub, o.overlap, o.levels, o.restart = int(nsub), int(overlap), int(levels), int(restart)
     o.precision, o.max_iter = int(precision), int(max_iter)
@@ -222,6 +227,7 @@ def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=200
     o.spmv_lanes = int(spmv_lanes)
     o.coarse_solver, o.coarse_maxit, o.coarse_tol = int(coarse_solver), int(coarse_maxit), float(coarse_tol)
     o.recycle = int(recycle)
+    o.sweep_tasks, o.bwd_chunk, o.tc_wait_limit = int(sweep_tasks), int(bwd_chunk), int(tc_wait_limit)
     return o, part
 
 

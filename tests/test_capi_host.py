@@ -78,3 +78,27 @@ def test_plan_builtin_partition(hzmod):
     a = hzmod.plan(p, use_partition=True)
     b = hzmod.plan(p, use_partition=False)   # the library's own coordinate bisection
     assert a["sum_ni"] == b["sum_ni"]
+
+
+def test_sweep_schedules_cover_every_kernel_variant(hzmod):
+    """The case test_gpu_variants runs on the GPU: across the default, wide-everywhere and
+    narrow-everywhere schedules (host-only analysis) every sweep variant occurs, with
+    128-wide complex64 supernodes (112 in FP64), split backward column blocks and
+    multi-tile, multi-stage tensor-core Schur updates; bad schedule options are rejected."""
+    p = synth.overthrust_problem(seed=0, freq=1.25, nsub=7, overlap=2, restart=50, levels=2)
+    for prec, width in ((hzmod.HZ_FP64, 112), (hzmod.HZ_MIXED, 128)):
+        plans = {sw: hzmod.plan(p, precision=prec, sweep_tasks=sw) for sw in (0, 1, 2)}
+        for st in plans.values():
+            assert st["max_snode_width"] == width
+            assert st["fwd_levels_wide"] + st["fwd_levels_narrow"] == st["nlevels"]
+            assert st["bwd_levels_wide"] + st["bwd_levels_narrow"] == st["nlevels"]
+            assert st["bwd_split_blocks"] > 0
+        assert plans[1]["fwd_levels_narrow"] == 0 and plans[1]["bwd_levels_narrow"] == 0
+        assert plans[2]["fwd_levels_wide"] == 0 and plans[2]["bwd_levels_wide"] == 0
+        if prec == hzmod.HZ_MIXED:
+            st = plans[0]
+            assert st["tc_multi_fronts"] > 0 and st["tc_max_kstages"] == 8
+            assert st["tc_tiles"] > st["tc_multi_fronts"]
+    for bad in (dict(sweep_tasks=3), dict(bwd_chunk=31), dict(bwd_chunk=33), dict(bwd_chunk=514)):
+        with pytest.raises(hzmod.HzError):
+            hzmod.plan(synth.tiny_problem(), **bad)

@@ -13,7 +13,12 @@ absorbing faces holding its dof):
   ||b - A x||, so each is bounded by tol * ||b|| (plus the rounding above).
 
 The sample holds Dirichlet rows, rows on the absorbing boundary, the source's rows and
-2,000 seeded random rows across every subdomain."""
+2,000 seeded random rows across every subdomain.
+
+Iterations: both precisions have taken 74 inner iterations to 1e-6 on this workload in
+every run so far; the test allows 74 +- 2 (rounding differences between summation
+orders, and between the complex64 and complex128 local solves, can move the count when
+an estimate lands near the tolerance)."""
 import numpy as np
 import pytest
 
@@ -23,6 +28,7 @@ from oracle import fem
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-6
+ITERATIONS = 74
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +66,7 @@ def test_full_size_solve_against_sampled_oracle_rows(hzmod, full, precision):
         assert np.abs(b - b_ref).max() <= 1e-14 * np.abs(b_ref).max()
         x_dev, info = G.solve(torch.from_numpy(b).cuda(), tol=TOL)
         its, status, rel = info[0]
-        assert status == 0 and 0 < its and rel <= TOL, info
+        assert status == 0 and abs(its - ITERATIONS) <= 2 and rel <= TOL, info
         y = G.apply_A(x_dev.contiguous()).cpu().numpy()
         x = x_dev.cpu().numpy()
     finally:

@@ -46,8 +46,35 @@ def test_noalloc_cgs2_matches_context_cgs2():
             assert torch.allclose(h_na, h_ref, rtol=0, atol=tol * float(h_ref.abs().max()))
             assert torch.allclose(w_na, w_ref, rtol=0, atol=tol * float(abs(w).max()))
             assert abs(float(nrm_na[0]) - nrm_ref) <= tol * nrm_ref
-    # a size beyond the fixed scratch is rejected
-    bad = lib.hz_cgs2_noalloc(C.c_void_p(Vt.data_ptr()), n, n, 65, C.c_void_p(w_na.data_ptr()),
-                              C.c_void_p(h_na.data_ptr()), C.c_void_p(nrm_na.data_ptr()), None)
-    assert bad == hz.HZ_ERR_ARG
+    # the widest call the fixed scratch holds (64 columns), with V stored at a padded
+    # leading dimension, against hz_cgs2 with the same layout
+    ncols, ldv = 64, n + 7
+    V = rng.standard_normal((n, ncols)) + 1j * rng.standard_normal((n, ncols))
+    V, _ = np.linalg.qr(V)
+    Vpad = np.zeros((ncols, ldv), np.complex128)           # column-major n x ncols, ld = n + 7
+    Vpad[:, :n] = V.T
+    Vp = torch.from_numpy(Vpad).cuda()
+    w = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    w_ref = torch.from_numpy(w).cuda()
+    h_ref = torch.empty(ncols, dtype=torch.complex128, device="cuda")
+    nrm_ref = C.c_double()
+    assert lib.hz_cgs2(G.h, C.c_void_p(Vp.data_ptr()), ldv, ncols, C.c_void_p(w_ref.data_ptr()),
+                       C.c_void_p(h_ref.data_ptr()), C.byref(nrm_ref)) == hz.HZ_OK
+    w_na = torch.from_numpy(w).cuda()
+    h_na = torch.empty(ncols, dtype=torch.complex128, device="cuda")
+    nrm_na = torch.empty(1, dtype=torch.float64, device="cuda")
+    s = lib.hz_cgs2_noalloc(C.c_void_p(Vp.data_ptr()), n, ldv, ncols, C.c_void_p(w_na.data_ptr()),
+                            C.c_void_p(h_na.data_ptr()), C.c_void_p(nrm_na.data_ptr()),
+                            C.c_void_p(torch.cuda.current_stream().cuda_stream or None))
+    assert s == hz.HZ_OK
+    torch.cuda.synchronize()
+    tol = 1e-12
+    assert torch.allclose(h_na, h_ref, rtol=0, atol=tol * float(h_ref.abs().max()))
+    assert torch.allclose(w_na, w_ref, rtol=0, atol=tol * float(abs(w).max()))
+    assert abs(float(nrm_na[0]) - nrm_ref.value) <= tol * nrm_ref.value
+    # sizes outside [1, 64] columns are rejected
+    for bad_cols in (65, 0):
+        bad = lib.hz_cgs2_noalloc(C.c_void_p(Vt.data_ptr()), n, n, bad_cols, C.c_void_p(w_na.data_ptr()),
+                                  C.c_void_p(h_na.data_ptr()), C.c_void_p(nrm_na.data_ptr()), None)
+        assert bad == hz.HZ_ERR_ARG
     G.close()
