@@ -363,13 +363,54 @@ def trends_bench(args):
     print(json.dumps(line))
 
 
+def crossover_bench(args):
+    """One level against two on the 5 Hz workload's mesh (coarse (63, 63, 9) cells, 2.37M
+    P2 dofs, 64 subdomains) at four frequencies, i.e. at 1.25, 1.5, 2 and 2.5 coarse element
+    edges per slowest wavelength (2.5, 3, 4 and 5 fine P2 elements): where the coarse space
+    starts to pay.  Mixed precision, tol 1e-6, one source at (2.5, 2.5, 0.58) km; one
+    warm-up and one timed solve per row."""
+    import torch
+    import synth
+    from paper_2004_06309_gb300 import build, hz
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    cells = synth.overthrust_cells(5.0, 1.25)
+    rows = []
+    for epw in (1.25, 1.5, 2.0, 2.5):
+        f = 5.0 * 1.25 / epw
+        row = {"coarse_elems_per_wavelength": epw, "fine_elems_per_wavelength": 2 * epw, "freq_hz": f,
+               "cells": list(cells)}
+        for lv in (1, 2):
+            p = synth.overthrust_problem(seed=0, freq=f, cells=cells, nsub=64, overlap=2, levels=lv)
+            G = hz.Solver(p, precision=hz.HZ_MIXED, stream=stream)
+            G.factor()
+            b = torch.from_numpy(G.point_sources(p.sources)[:, 0].copy()).cuda()
+            G.solve(b)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            x, info = G.solve(b)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            row["n_dofs"] = G.n
+            row[f"{lv}level"] = {"iterations": info[0][0], "seconds": dt, "rhs_per_s": 1.0 / dt,
+                                 "ok": info[0][1] == 0}
+            G.close()
+            torch.cuda.empty_cache()
+        rows.append(row)
+    print(json.dumps({"experiment": "one level against two on the 5 Hz mesh", "rows": rows,
+                      "precision": "mixed", "tol": 1e-6}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
-    ap.add_argument("--workload", default="overthrust-5hz", choices=list(WORKLOADS) + ["serving", "trends"])
+    ap.add_argument("--workload", default="overthrust-5hz",
+                    choices=list(WORKLOADS) + ["serving", "trends", "crossover"])
     ap.add_argument("--serve-batch", type=int, default=16, help="largest sources per request (serving)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -396,9 +437,9 @@ def main():
         print(json.dumps(run_oracle_sample(args.steps, args.warmup)))
         return
 
-    if args.workload in ("serving", "trends") and args.impl == "hz":
+    if args.workload in ("serving", "trends", "crossover") and args.impl == "hz":
         if int(os.environ.get("RANK", "0")) == 0:
-            (serve_bench if args.workload == "serving" else trends_bench)(args)
+            {"serving": serve_bench, "trends": trends_bench, "crossover": crossover_bench}[args.workload](args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

@@ -1405,10 +1405,29 @@ void hz_free(hz_ctx* c) {
 }  // extern "C"
 
 // Host analysis shared by hz_setup_mesh and hz_plan.  HZ_VERBOSE=1 prints phase times.
+// Resident and peak host memory of this process in GB (Linux /proc; 0 elsewhere).
+static void host_rss_gb(double& rss, double& peak) {
+  rss = peak = 0.0;
+  if (FILE* f = std::fopen("/proc/self/status", "r")) {
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+      long long kb = 0;
+      if (std::sscanf(line, "VmRSS: %lld", &kb) == 1) rss = kb / 1e6;
+      if (std::sscanf(line, "VmHWM: %lld", &kb) == 1) peak = kb / 1e6;
+    }
+    std::fclose(f);
+  }
+}
+
 static void phase(const char* what, std::chrono::steady_clock::time_point& t) {
   static const bool on = std::getenv("HZ_VERBOSE") != nullptr;
   const auto now = std::chrono::steady_clock::now();
-  if (on) std::fprintf(stderr, "[hz] %-28s %8.3f s\n", what, std::chrono::duration<double>(now - t).count());
+  if (on) {
+    double rss, peak;
+    host_rss_gb(rss, peak);
+    std::fprintf(stderr, "[hz] %-28s %8.3f s   host RSS %6.2f GB (peak %6.2f)\n", what,
+                 std::chrono::duration<double>(now - t).count(), rss, peak);
+  }
   t = now;
 }
 
