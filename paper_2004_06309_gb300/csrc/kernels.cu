@@ -590,6 +590,12 @@ void launch_factor_level(const FactorDev& F, int lev, double w, void* fronts, vo
 // ---------------------------------------------------------------------------
 // batched supernodal solves  (A_i^{-1}: forward with D^{-1}, then backward)
 // ---------------------------------------------------------------------------
+// Loads of solve vectors (t, u, z, x) bypass L1 (ld.global.cg): each value is read
+// once per sweep, so caching it in L1 only evicts panel lines.
+template <typename V> __device__ __forceinline__ V ldv(const V* p);
+template <> __device__ __forceinline__ float2 ldv<float2>(const float2* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double2 ldv<double2>(const double2* p) { return __ldcg(p); }
+
 template <typename V>
 __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, V* dst) {
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < ntot; q += int64_t(gridDim.x) * blockDim.x)
@@ -604,13 +610,11 @@ __global__ void k_gather(int64_t ntot, const int32_t* gidx, const double2* src, 
 // where it has few (the top of a single tree), so that such a level still spreads
 // over every SM (its FP64 arithmetic, not its bytes, is the bound there).
 template <typename V, int RT>
-__global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
-                                             const int64_t* cidx, const V* panels, const V* tin, V* zout,
-                                             V* u) {
+__device__ __forceinline__ void fwd_item(const int2 t, const SnDev* sn, const int64_t* cptr, const int64_t* cidx,
+                                         const V* panels, const V* tin, V* zout, V* u) {
   constexpr int CG = 256 / RT;
   __shared__ V b1[kMaxK];
   __shared__ V part[CG][RT];
-  const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
   const int64_t* cp = cptr + S.rowoff;
@@ -630,8 +634,8 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
       pv[q] = (r < m && j < jmax) ? P[r + int64_t(j) * S.ld] : czero<V>();
     }
     for (int j = tid; j < k; j += blockDim.x) {
-      V a = tin[S.first + j];
-      for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, u[cidx[c]]);
+      V a = ldv(tin + S.first + j);
+      for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, ldv(u + cidx[c]));
       b1[j] = a;
     }
     __syncthreads();
@@ -647,8 +651,8 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
     }
   } else {
     for (int j = tid; j < k; j += blockDim.x) {
-      V a = tin[S.first + j];
-      for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, u[cidx[c]]);
+      V a = ldv(tin + S.first + j);
+      for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, ldv(u + cidx[c]));
       b1[j] = a;
     }
     __syncthreads();
@@ -672,10 +676,18 @@ __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn,
       zout[S.first + r] = cmul(P[r + int64_t(r) * S.ld], cadd(b1[r], tot));
     } else {
       V b2 = czero<V>();
-      for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+      for (int64_t c = cp[r]; c < cp[r + 1]; c++) b2 = cadd(b2, ldv(u + cidx[c]));
       u[S.uoff + (r - k)] = csub(b2, tot);
     }
   }
+  __syncthreads();                                   // b1 / part are reused by the next item
+}
+
+template <typename V, int RT>
+__global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+                                             const int64_t* cidx, const V* panels, const V* tin, V* zout,
+                                             V* u) {
+  fwd_item<V, RT>(tasks[blockIdx.x], sn, cptr, cidx, panels, tin, zout, u);
 }
 
 // Backward, split over row chunks so that tall supernodes use many CTAs:
@@ -800,14 +812,13 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
 // load chains overlap; every sum keeps the order of the column loop (even q on one
 // chain, odd q on the other).
 template <int CG>
-__global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
-                                                 const int64_t* cidx, const float2* panels, const float2* tin,
-                                                 float2* zout, float2* u) {
+__device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, const int64_t* cptr,
+                                             const int64_t* cidx, const float2* panels, const float2* tin,
+                                             float2* zout, float2* u) {
   constexpr int NP = 256 / CG;                       // row pairs per task
   constexpr int ROWS = 2 * NP;
   __shared__ float2 b1[kMaxK];
   __shared__ float2 part[CG][ROWS];
-  const int2 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
   const int pr = tid % NP, cg = tid / NP;
@@ -827,12 +838,12 @@ __global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnD
       pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int jj = tid; jj < k; jj += blockDim.x) {
-      float2 acc = tin[S.first + jj];
-      for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+      float2 acc = ldv(tin + S.first + jj);
+      for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, ldv(u + cidx[c]));
       b1[jj] = acc;
     }
     if (tid < ROWS && rr >= k && rr < m)
-      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, ldv(u + cidx[c]));
     __syncthreads();
     if (r < m) {
 #pragma unroll
@@ -863,12 +874,12 @@ __global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnD
       pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int jj = tid; jj < k; jj += blockDim.x) {
-      float2 acc = tin[S.first + jj];
-      for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, u[cidx[c]]);
+      float2 acc = ldv(tin + S.first + jj);
+      for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, ldv(u + cidx[c]));
       b1[jj] = acc;
     }
     if (tid < ROWS && rr >= k && rr < m)
-      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, u[cidx[c]]);
+      for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, ldv(u + cidx[c]));
     __syncthreads();
     if (r < m) {
 #pragma unroll
@@ -916,6 +927,14 @@ __global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnD
     else
       u[S.uoff + (rr - k)] = csub(b2, tot);
   }
+  __syncthreads();                                   // b1 / part are reused by the next item
+}
+
+template <int CG>
+__global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
+                                                 const int64_t* cidx, const float2* panels, const float2* tin,
+                                                 float2* zout, float2* u) {
+  fwd_c64_item<CG>(tasks[blockIdx.x], sn, cptr, cidx, panels, tin, zout, u);
 }
 
 // complex64 backward partial sums with 16-byte loads (two rows per lane).  PF (narrow
