@@ -38,6 +38,13 @@ WORKLOADS = {
                               restart=50),
     "overthrust-small": dict(kind="overthrust", cells=None, freq=1.25, nsub=8, overlap=2,
                              restart=50),
+    # the precision form at 10 Hz: about 15M P2 dofs (1.19 coarse edges per slowest
+    # wavelength), 512 subdomains, complex64 local factors with the FP64 outer loop.  Overlap
+    # 1, the iterative coarse solve and factorisation in groups of 64 subdomains keep it on
+    # one GPU; there is no FP64 arm (its complex128 factors alone would need about 220 GB).
+    "overthrust-10hz": dict(kind="overthrust", cells=None, epw=1.19, freq=10.0, nsub=512, overlap=1,
+                            restart=50, coarse="oras", factor_group=64, precisions=["mixed"],
+                            fp64_check_tol=1e-10),
     "tiny": dict(kind="tiny"),
 }
 # Inner iterations the 5 Hz workload takes to 1e-6 (measured on the GPU path, FP64 and mixed
@@ -58,14 +65,14 @@ def clocks_dir(args):
 
 def synth_cells(spec):
     import synth
-    return spec["cells"] or synth.overthrust_cells(spec["freq"])
+    return spec["cells"] or synth.overthrust_cells(spec["freq"], spec.get("epw", 1.25))
 
 
 def make_problem(spec):
     import synth
     if spec["kind"] == "tiny":
         return synth.tiny_problem()
-    return synth.overthrust_problem(seed=0, freq=spec["freq"], cells=spec["cells"], nsub=spec["nsub"],
+    return synth.overthrust_problem(seed=0, freq=spec["freq"], cells=synth_cells(spec), nsub=spec["nsub"],
                                     overlap=spec["overlap"], restart=spec["restart"], levels=2)
 
 
@@ -498,6 +505,8 @@ def main():
         return max_over_ranks(x, dist, "cuda") if dist else x
 
     precs = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    precs = [q for q in precs if q in spec.get("precisions", precs)]
+    coarse = spec.get("coarse", args.coarse)
     results = {}
     # a dedicated (non-default) stream, so that the library can capture its iterations as CUDA graphs
     stream = torch.cuda.Stream()
@@ -505,8 +514,9 @@ def main():
     for pname in precs:
         G = hz.Solver(prob, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, stream=stream,
                       leaf_size=args.leaf, max_snode=args.maxsn, block_size=args.block,
-                      coarse_solver=hz.HZ_COARSE_ORAS if args.coarse == "oras" else hz.HZ_COARSE_DIRECT,
-                      coarse_tol=args.coarse_tol, coarse_maxit=args.coarse_maxit, recycle=args.recycle)
+                      coarse_solver=hz.HZ_COARSE_ORAS if coarse == "oras" else hz.HZ_COARSE_DIRECT,
+                      coarse_tol=args.coarse_tol, coarse_maxit=args.coarse_maxit, recycle=args.recycle,
+                      factor_group=spec.get("factor_group", 0))
         tf = time.time()
         G.factor()
         torch.cuda.synchronize()
@@ -543,11 +553,21 @@ def main():
             xh, infoh = G.solve(b_host)
         torch.cuda.synchronize()
         e2e_s = maxall(time.perf_counter() - te)
+        check = None
+        if spec.get("fp64_check_tol") and args.nrhs == 1:
+            # no FP64 factors fit: the FP64 outer FGMRES driven to a tight tolerance gives the
+            # FP64 solution (to kappa * tol), against which the timed solution's error is taken
+            xr, infor = G.solve(b_dev, tol=spec["fp64_check_tol"])
+            x1 = x.reshape(-1)
+            check = {"reference": f"same context solved to {spec['fp64_check_tol']:g} (FP64 outer FGMRES)",
+                     "reference_iterations": infor[0][0], "reference_rel_residual": infor[0][2],
+                     "rel_l2_vs_reference": float(torch.linalg.norm(x1 - xr.reshape(-1)) /
+                                                  torch.linalg.norm(xr.reshape(-1)))}
         prof = G.profile(reps=3)
         stats = G.stats()
         results[pname] = dict(total_ms=total_ms, step_ms=step_ms, iterations=its, rel=rel, clocks=ck,
                               launches=launches, e2e_s=e2e_s, profile=prof, stats=stats,
-                              t_factor=t_factor, n=G.n)
+                              t_factor=t_factor, n=G.n, check=check)
         G.close()
         del G
         torch.cuda.empty_cache()
@@ -555,7 +575,8 @@ def main():
     # one-level arm (Eq. 4 alone) on the same mesh and partition, mixed precision: shows
     # where the coarse space pays and where it does not (its resolution, not the method)
     one = None
-    if args.one_level_steps > 0 and prob.levels == 2 and "mixed" in precs and args.nrhs == 1:
+    if (args.one_level_steps > 0 and prob.levels == 2 and "mixed" in precs and args.nrhs == 1
+            and args.workload == "overthrust-5hz"):
         import dataclasses
         p1 = dataclasses.replace(prob, levels=1, coarse=None, fine_parent=None)
         G = hz.Solver(p1, precision=hz.HZ_MIXED, stream=stream, leaf_size=args.leaf, max_snode=args.maxsn)
@@ -635,7 +656,8 @@ def main():
         "config": {"workload": args.workload, "n_dofs": n, "nsub": prob.nsub, "overlap": prob.overlap,
                    "levels": 2 if prob.levels == 2 else 1, "restart": prob.restart, "tol": 1e-6,
                    "rhs_per_step": args.nrhs, "block_size": args.block, "freq_hz": prob.freq,
-                   "coarse_solver": args.coarse, "recycle": args.recycle,
+                   "coarse_solver": coarse, "recycle": args.recycle,
+                   "factor_group": spec.get("factor_group", 0),
                    "l2": "inputs larger than L2 (factors >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "iterations": R["iterations"][-1], "rel_residual": R["rel"],
@@ -663,6 +685,10 @@ def main():
                         "phases_ms": {k: round(v["ms"], 4) for k, v in F["profile"].items()},
                         "phases_gflops": {k: round(v["flops"] / 1e9, 4) for k, v in F["profile"].items()},
                         "clocks": F["clocks"]}
+    if R.get("check"):
+        line["fp64_check"] = R["check"]
+    if "fp64" not in results and spec.get("precisions") == ["mixed"]:
+        line["fp64"] = {"value": None, "note": "not run: complex128 local factors do not fit one GPU at this size"}
     if one is not None:
         line["one_level"] = dict(one, precision="mixed",
                                  note="levels=1 on the same mesh and partition; no coarse space")

@@ -142,6 +142,11 @@ typedef struct {
                                none, so that wait runs out at once (a test of the
                                HZ_ERR_TIMEOUT path).  The wait that drains MMAs still in
                                flight before tensor memory is freed keeps 2^22.       */
+  int32_t factor_group;     /* subdomains factorised together: their fronts share the
+                               frontal workspace at once, and the groups run one after
+                               the other, so the workspace (hz_stats.front_bytes) is
+                               that of the largest group.  0: all subdomains at once.
+                               The factors do not depend on it.                       */
 } hz_options;
 
 typedef struct {

@@ -337,6 +337,20 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
       cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1), tc_ptr(nlev + 1);
   int64_t scratch = 0;
+  // factorisation groups: per level (and extend-add slot) the start of each group's
+  // tasks; every list is ordered by supernode within a level, hence by group
+  const int G = std::max(1, int(S.grp_sn.size()) - 1);
+  const std::vector<int32_t> grp_sn = S.grp_sn.size() >= 2 ? S.grp_sn : std::vector<int32_t>{0, ns};
+  auto grp_of = [&](int sn) { return int(std::upper_bound(grp_sn.begin(), grp_sn.end(), sn) - grp_sn.begin()) - 1; };
+  std::vector<int64_t> lev_g(size_t(nlev) * (G + 1)), wg_g(lev_g.size()), cb_g(lev_g.size()), tc_g(lev_g.size()),
+      ea_g(size_t(nlev) * max_slot * (G + 1));
+  struct Split {                      // fills out[base + g] with the list size where group g starts
+    std::vector<int64_t>& out;
+    size_t base;
+    int G, next;
+    void enter(int g, int64_t size) { while (next <= g) out[base + next++] = size; }
+    void finish(int64_t size) { while (next <= G) out[base + next++] = size; }
+  };
   const SweepPlan sp = plan_sweeps(S, precision, bwd_rows, sweep_tasks);
   const std::vector<int>& fwd_rt = sp.fwd_rt;
   const std::vector<int>& lev_bwd_rows = sp.bwd_rows;
@@ -358,9 +372,21 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     cb_ptr[l] = int64_t(cbt.size());
     tc_ptr[l] = int64_t(tct.size());
     int64_t lev_scr = 0;
+    int cur_g = -1;
+    Split sl{lev_g, size_t(l) * (G + 1), G, 0}, sw{wg_g, size_t(l) * (G + 1), G, 0},
+        sc{cb_g, size_t(l) * (G + 1), G, 0}, st{tc_g, size_t(l) * (G + 1), G, 0};
     for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
       const int s = S.lev_sn[q];
       const int k = S.sn_k[s], m = S.sn_m[s], r = m - k;
+      const int gs = grp_of(s);
+      if (gs != cur_g) {                           // a group's W blocks start the scratch again
+        cur_g = gs;
+        lev_scr = 0;
+        sl.enter(gs, q);
+        sw.enter(gs, int64_t(wg.size()));
+        sc.enter(gs, int64_t(cbt.size()));
+        st.enter(gs, int64_t(tct.size()));
+      }
       const int frows = fwd_rt[l];                     // forward task rows (k_fwd / k_fwd_c64)
       for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
       const int nch = (m + lev_bwd_rows[l] - 1) / lev_bwd_rows[l];
@@ -381,19 +407,26 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
       }
       scr_off[s] = lev_scr;
       lev_scr += int64_t(r) * k;
+      scratch = std::max(scratch, lev_scr);
     }
-    scratch = std::max(scratch, lev_scr);
+    sl.finish(S.lev_ptr[l + 1]);
+    sw.finish(int64_t(wg.size()));
+    sc.finish(int64_t(cbt.size()));
+    st.finish(int64_t(tct.size()));
     max_bwd_level = std::max(max_bwd_level, int64_t(bwd.size()) - bwd_ptr[l]);
     for (int q = 0; q < max_slot; q++) {
       ea_ptr[int64_t(l) * max_slot + q] = int64_t(ea.size());
+      Split se{ea_g, (size_t(l) * max_slot + q) * (G + 1), G, 0};
       for (int32_t z = S.lev_ptr[l]; z < S.lev_ptr[l + 1]; z++) {
         const int p = S.lev_sn[z];
+        se.enter(grp_of(p), int64_t(ea.size()));
         if (q < int(children[p].size())) {
           const int ch = children[p][q];
           const int r = S.sn_m[ch] - S.sn_k[ch];
           for (int cb = 0; cb * 8 < r; cb++) ea.push_back(make_int2(ch, cb));
         }
       }
+      se.finish(int64_t(ea.size()));
     }
   }
   lev_ptr[nlev] = S.lev_ptr[nlev];
@@ -443,6 +476,20 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.h_tc_ptr = hcopy(tc_ptr);
   F.h_ea_ptr = hcopy(ea_ptr);
   F.h_ent_ptr = hcopy(S.ent_ptr);
+  F.ngrp = G;
+  F.h_lev_g = hcopy(lev_g);
+  F.h_wg_g = hcopy(wg_g);
+  F.h_cb_g = hcopy(cb_g);
+  F.h_tc_g = hcopy(tc_g);
+  F.h_ea_g = hcopy(ea_g);
+  F.h_ent_g = hcopy(S.ent_gptr.size() == size_t(nlev) * (G + 1) ? S.ent_gptr : [&] {
+    std::vector<int64_t> v(size_t(nlev) * (G + 1));      // one group: the level's whole range
+    for (int l = 0; l < nlev; l++) {
+      v[size_t(l) * (G + 1)] = S.ent_ptr[l];
+      v[size_t(l) * (G + 1) + 1] = S.ent_ptr[l + 1];
+    }
+    return v;
+  }());
   F.h_fwd_rt = new int[nlev];
   F.h_bwd_rows = new int[nlev];
   std::copy(fwd_rt.begin(), fwd_rt.end(), F.h_fwd_rt);
@@ -523,6 +570,13 @@ void free_host_ptrs(hz::FactorDev& F) {
   F.h_tc_ptr = nullptr;
   delete[] F.h_ea_ptr;
   delete[] F.h_ent_ptr;
+  delete[] F.h_lev_g;
+  delete[] F.h_ent_g;
+  delete[] F.h_wg_g;
+  delete[] F.h_cb_g;
+  delete[] F.h_tc_g;
+  delete[] F.h_ea_g;
+  F.h_lev_g = F.h_ent_g = F.h_wg_g = F.h_cb_g = F.h_tc_g = F.h_ea_g = nullptr;
   delete[] F.h_mfwd_ptr;
   delete[] F.h_fwd_rt;
   delete[] F.h_bwd_rows;
@@ -557,7 +611,8 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
                  std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     t0 = std::chrono::steady_clock::now();
   }
-  for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, w, fronts, scratch, c->status, tiny, c->st);
+  for (int g = 0; g < F.ngrp; g++)                 // groups one after the other in one workspace
+    for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, g, w, fronts, scratch, c->status, tiny, c->st);
   if (verbose) {
     cudaStreamSynchronize(c->st);
     std::fprintf(stderr, "[hz] factor: %d levels in %.3f s\n", F.nlev,
@@ -1455,6 +1510,7 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
   if (op->sweep_tasks < 0 || op->sweep_tasks > 2) return fail(c, HZ_ERR_ARG, "sweep_tasks must be 0, 1 or 2");
   if (op->bwd_chunk != 0 && (op->bwd_chunk < 32 || op->bwd_chunk > 512 || op->bwd_chunk % 2 != 0))
     return fail(c, HZ_ERR_ARG, "bwd_chunk must be 0 or even in [32, 512]");
+  if (op->factor_group < 0) return fail(c, HZ_ERR_ARG, "factor_group must be >= 0");
   const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
   for (int64_t q = 0; q < ne * 4; q++)
     if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
@@ -1517,8 +1573,10 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
       mats[i].coord = coords[i].data();
       mats[i].gidx = S.dofs.data();
       mats[i].weight = S.D.data();
+      mats[i].release = &P.subs[i].A;     // its values live on in the symbolic entries
+      P.nnz_local += S.A.pat.nnz();
     }
-    hz::symbolic_batch(mats, leaf, maxsn, P.local);
+    hz::symbolic_batch(mats, leaf, maxsn, P.local, op->factor_group);
   }
   phase("local symbolic", tp);
   if (op->levels == 2 && op->coarse_solver == HZ_COARSE_ORAS) {
@@ -1537,8 +1595,9 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
       mats[i].coord = coords[i].data();
       mats[i].gidx = P.cgidx[i].data();
       mats[i].weight = S.D.data();
+      mats[i].release = &P.csubs[i].A;
     }
-    hz::symbolic_batch(mats, leaf, maxsn, P.clocal);
+    hz::symbolic_batch(mats, leaf, maxsn, P.clocal, op->factor_group);
     phase("coarse local symbolic", tp);
   } else if (op->levels == 2) {
     hz::build_coarse(P);
@@ -1564,9 +1623,7 @@ static void fill_stats(hz_ctx* c, const hz::HostProblem& P) {
   s.n_coarse = P.nH;
   s.nnz_coarse = P.E.pat.nnz();
   s.sum_ni = P.local.voff.empty() ? 0 : P.local.voff.back();
-  int64_t nl = 0;
-  for (const auto& S : P.subs) nl += S.A.pat.nnz();
-  s.nnz_local = nl;
+  s.nnz_local = P.nnz_local;
   s.nnz_factor = P.local.panel_elems;
   const bool it = !P.clocal.voff.empty();           // iterative coarse solve
   s.nnz_factor_coarse = it ? P.clocal.panel_elems : P.coarse.panel_elems;

@@ -59,6 +59,11 @@ struct FactorDev {
   int64_t* h_cb_ptr = nullptr;
   int64_t* h_ea_ptr = nullptr;        // nlev * maxslot + 1, grouped (level, slot)
   int64_t* h_ent_ptr = nullptr;       // nlev + 1: entries of each level's fronts
+  // factorisation groups (whole matrices, one after the other in one frontal workspace):
+  // per level (and slot) the start of each group's tasks, groups + 1 entries each
+  int32_t ngrp = 1;
+  int64_t *h_lev_g = nullptr, *h_ent_g = nullptr, *h_wg_g = nullptr, *h_cb_g = nullptr, *h_tc_g = nullptr;
+  int64_t* h_ea_g = nullptr;          // ((level * max_slot + slot) * (groups + 1) + group)
   cudaEvent_t* level_events = nullptr;  // optional (diagnostics): 2 * nlev + 1 events around sweep levels
   int* h_fwd_rt = nullptr;            // nlev: complex128 forward task rows (16 or 64)
   int* h_bwd_rows = nullptr;          // nlev: complex128 backward chunk rows
@@ -148,8 +153,8 @@ void launch_fill_values(int64_t nnz, const double* K, const double2* M, const do
                         double2* out, cudaStream_t st);
 // One assembly-tree level: zero and fill its fronts (A_i(omega) entries), extend-add the
 // children, factor, and copy the panels to the factor store.
-void launch_factor_level(const FactorDev& F, int lev, double w, void* fronts, void* scratch, DevStatus* status,
-                         double tiny, cudaStream_t st);
+void launch_factor_level(const FactorDev& F, int lev, int grp, double w, void* fronts, void* scratch,
+                         DevStatus* status, double tiny, cudaStream_t st);
 
 void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st);
 void launch_solve(const FactorDev& F, cudaStream_t st);

@@ -68,6 +68,7 @@ struct SymbolicSet {
   // entries of the lower triangles: front position and frequency-free values
   std::vector<int64_t> epos;           // grouped by level: ent_ptr[l] .. ent_ptr[l+1]
   std::vector<int64_t> ent_ptr;
+  std::vector<int64_t> ent_gptr;       // nlev * (groups + 1): entries of each (level, group)
   std::vector<double> ek;
   std::vector<cplx> em, eb;
   // extend-add: relative positions of each child's contribution rows in its parent
@@ -78,6 +79,9 @@ struct SymbolicSet {
   std::vector<int64_t> cidx;
   int64_t front_elems = 0, panel_elems = 0, u_elems = 0;
   double flops = 0;                        // real flops of the numeric factorisation
+  // factorisation groups: supernodes [grp_sn[g], grp_sn[g + 1]) (whole matrices), each
+  // group's fronts planned from offset 0 of the same workspace
+  std::vector<int32_t> grp_sn;
 };
 
 struct HostProblem {
@@ -86,6 +90,7 @@ struct HostProblem {
   Dofs dofs, cdofs;
   Parts A;                            // global operator pieces
   std::vector<Subdomain> subs;
+  int64_t nnz_local = 0;              // nonzeros of all A_i (their values are released after analysis)
   SymbolicSet local;                  // all A_i
   // coarse level
   int64_t nH = 0;
@@ -120,7 +125,10 @@ struct MatrixInput {
   const double* coord;        // n*3
   const int64_t* gidx;        // n: global index of each local dof (for gather/scatter)
   const double* weight;       // n: prolongation weights
+  Parts* release = nullptr;   // if set (== A): emptied once its entries are copied
 };
-void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, SymbolicSet& S);
+// group: matrices whose fronts are planned (and factorised) together in one frontal
+// workspace; groups run one after the other and reuse it.  0: all matrices at once.
+void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, SymbolicSet& S, int group = 0);
 
 }  // namespace hz

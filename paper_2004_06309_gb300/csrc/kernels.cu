@@ -511,16 +511,26 @@ __global__ void k_panel_copy(const int32_t* lev_sn, const SnDev* sn, const V* fr
 static size_t diag_smem(int kmax, size_t vs) { return (size_t(kmax + 1) * kmax + 2 * kmax) * vs; }
 static size_t wg_smem(int kmax, size_t vs) { return (size_t(64) * kmax + kmax) * vs; }
 
+// One tree level of one factorisation group (whole matrices whose fronts share the
+// workspace at once): each task list holds, per level, the groups' tasks in order.
 template <typename V>
-static void factor_level_t(const FactorDev& F, int lev, double w, V* fronts, V* scratch, DevStatus* status,
-                           double tiny, cudaStream_t st) {
-  const int64_t nb = F.h_lev_ptr[lev + 1] - F.h_lev_ptr[lev];
-  const int32_t* lsn = F.lev_sn + F.h_lev_ptr[lev];
+static void factor_level_t(const FactorDev& F, int lev, int grp, double w, V* fronts, V* scratch,
+                           DevStatus* status, double tiny, cudaStream_t st) {
+  const int G1 = F.ngrp + 1;
+  auto range = [&](const int64_t* gp, int64_t row, int64_t& b, int64_t& e) {
+    b = gp[row * G1 + grp];
+    e = gp[row * G1 + grp + 1];
+  };
+  int64_t lb, le;
+  range(F.h_lev_g, lev, lb, le);
+  const int64_t nb = le - lb;
+  const int32_t* lsn = F.lev_sn + lb;
   if (nb > 0) {
     HZ_COUNT();
     k_front_zero<V><<<unsigned(nb), 256, 0, st>>>(lsn, F.sn, fronts);
   }
-  const int64_t e0 = F.h_ent_ptr[lev], e1 = F.h_ent_ptr[lev + 1];
+  int64_t e0, e1;
+  range(F.h_ent_g, lev, e0, e1);
   if (e1 > e0) {
     HZ_COUNT();
     k_front_fill<V><<<grid_for(e1 - e0, 256), 256, 0, st>>>(e1 - e0, F.epos + e0, F.ek + e0, F.em + e0, F.eb + e0,
@@ -528,7 +538,8 @@ static void factor_level_t(const FactorDev& F, int lev, double w, V* fronts, V* 
   }
   // extend-add, one child slot per launch so that no parent entry is written twice
   for (int q = 0; q < F.max_slot; q++) {
-    const int64_t b = F.h_ea_ptr[int64_t(lev) * F.max_slot + q], e = F.h_ea_ptr[int64_t(lev) * F.max_slot + q + 1];
+    int64_t b, e;
+    range(F.h_ea_g, int64_t(lev) * F.max_slot + q, b, e);
     if (e > b) {
       HZ_COUNT();
       k_extend_add<V><<<unsigned(e - b), 256, 0, st>>>(F.ea_tasks + b, F.sn, F.rel, F.reloff, fronts);
@@ -538,21 +549,24 @@ static void factor_level_t(const FactorDev& F, int lev, double w, V* fronts, V* 
   const size_t ds = diag_smem(F.maxk, sizeof(V));
   HZ_COUNT();
   k_diag<V><<<unsigned(nb), 256, ds, st>>>(lsn, F.sn, fronts, status, tiny);
-  const int64_t wb = F.h_wg_ptr[lev], we = F.h_wg_ptr[lev + 1];
+  int64_t wb, we;
+  range(F.h_wg_g, lev, wb, we);
   if (we > wb) {
     HZ_COUNT();
     k_wg<V><<<unsigned(we - wb), 256, wg_smem(F.maxk, sizeof(V)), st>>>(F.wg_tasks + wb, F.sn, F.scr_off, fronts,
                                                                        scratch);
   }
   if constexpr (sizeof(V) == 8) {
-    const int64_t tb = F.h_tc_ptr[lev], te = F.h_tc_ptr[lev + 1];
+    int64_t tb, te;
+    range(F.h_tc_g, lev, tb, te);
     if (te > tb) {
       HZ_COUNT();
       k_cb_tc<<<unsigned(te - tb), 128, kTcSmemFloats * sizeof(float), st>>>(F.tc_tasks + tb, F.sn, F.scr_off,
                                                                             fronts, scratch, status, F.tc_wait);
     }
   } else {
-    const int64_t cbb = F.h_cb_ptr[lev], cbe = F.h_cb_ptr[lev + 1];
+    int64_t cbb, cbe;
+    range(F.h_cb_g, lev, cbb, cbe);
     if (cbe > cbb) {
       HZ_COUNT();
       k_cb<V><<<unsigned(cbe - cbb), 256, 0, st>>>(F.cb_tasks + cbb, F.sn, F.scr_off, fronts, scratch);
@@ -578,13 +592,13 @@ static void set_attrs(int prec, int kmax) {
   (void)kmax;
 }
 
-void launch_factor_level(const FactorDev& F, int lev, double w, void* fronts, void* scratch, DevStatus* status,
-                         double tiny, cudaStream_t st) {
+void launch_factor_level(const FactorDev& F, int lev, int grp, double w, void* fronts, void* scratch,
+                         DevStatus* status, double tiny, cudaStream_t st) {
   set_attrs(F.precision, F.maxk);
   if (F.precision == 0)
-    factor_level_t<double2>(F, lev, w, (double2*)fronts, (double2*)scratch, status, tiny, st);
+    factor_level_t<double2>(F, lev, grp, w, (double2*)fronts, (double2*)scratch, status, tiny, st);
   else
-    factor_level_t<float2>(F, lev, w, (float2*)fronts, (float2*)scratch, status, tiny, st);
+    factor_level_t<float2>(F, lev, grp, w, (float2*)fronts, (float2*)scratch, status, tiny, st);
 }
 
 // ---------------------------------------------------------------------------

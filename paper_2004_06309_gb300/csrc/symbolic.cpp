@@ -171,7 +171,7 @@ void analyse_one(const MatrixInput& in, int leaf, int maxsn, SymOne& S) {
 
 }  // namespace
 
-void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, SymbolicSet& S) {
+void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, SymbolicSet& S, int group) {
   const int nmat = int(mats.size());
   std::vector<SymOne> one(nmat);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -239,10 +239,19 @@ void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, S
     std::vector<int32_t> fill(S.lev_ptr.begin(), S.lev_ptr.end() - 1);
     for (int32_t g = 0; g < ns; g++) S.lev_sn[fill[S.sn_level[g]]++] = g;
   }
-  // Frontal workspace: a static first-fit plan.  The front of supernode s is
-  // allocated when its level starts and released once its parent's level has
-  // absorbed it (extend-add), so only the live part of the tree is resident.
+  // factorisation groups of whole matrices
   {
+    const int gsz = group > 0 ? group : std::max(nmat, 1);
+    S.grp_sn.clear();
+    for (int i = 0; i < nmat; i += gsz) S.grp_sn.push_back(sn_base[i]);
+    S.grp_sn.push_back(ns);
+  }
+  // Frontal workspace: a static best-fit plan per group.  The front of supernode s is
+  // allocated when its level starts and released once its parent's level has
+  // absorbed it (extend-add), so only the live part of the tree is resident; the
+  // groups are factorised one after the other and each plans from offset 0.
+  for (size_t grp = 0; grp + 1 < S.grp_sn.size(); grp++) {
+    const int32_t g0 = S.grp_sn[grp], g1 = S.grp_sn[grp + 1];
     // best fit: free blocks indexed by size (for take) and by offset (to coalesce)
     std::map<int64_t, int64_t> by_off;              // offset -> size
     std::set<std::pair<int64_t, int64_t>> by_size;  // (size, offset)
@@ -294,15 +303,17 @@ void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, S
     for (int l = 0; l < S.nlev; l++) {
       for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
         const int32_t g = S.lev_sn[q];
+        if (g < g0 || g >= g1) continue;
         S.sn_frontoff[g] = take(int64_t(S.sn_m[g]) * S.sn_m[g]);
       }
       for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
         const int32_t g = S.lev_sn[q];
+        if (g < g0 || g >= g1) continue;
         for (int32_t c : kids[g]) give(S.sn_frontoff[c], int64_t(S.sn_m[c]) * S.sn_m[c]);
         if (S.sn_parent[g] < 0) give(S.sn_frontoff[g], int64_t(S.sn_m[g]) * S.sn_m[g]);
       }
     }
-    S.front_elems = peak;
+    S.front_elems = std::max(S.front_elems, peak);
   }
   // entries, grouped by the level of the supernode owning their column
   int64_t ne = 0;
@@ -316,9 +327,28 @@ void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, S
     for (int32_t sl : one[i].e_sn) S.ent_ptr[S.sn_level[sn_base[i] + sl] + 1]++;
   for (int l = 0; l < S.nlev; l++) S.ent_ptr[l + 1] += S.ent_ptr[l];
   {
+    // per (level, group) starts: entries are filled matrix by matrix, so each level's
+    // entries are ordered by matrix and hence by group
+    const int G = int(S.grp_sn.size()) - 1;
+    std::vector<int64_t> cnt(size_t(S.nlev) * G, 0);
+    for (int i = 0; i < nmat; i++) {
+      const int g = int(std::upper_bound(S.grp_sn.begin(), S.grp_sn.end(), sn_base[i]) - S.grp_sn.begin()) - 1;
+      for (int32_t sl : one[i].e_sn) cnt[size_t(S.sn_level[sn_base[i] + sl]) * G + g]++;
+    }
+    S.ent_gptr.assign(size_t(S.nlev) * (G + 1), 0);
+    for (int l = 0; l < S.nlev; l++) {
+      int64_t at = S.ent_ptr[l];
+      for (int g = 0; g < G; g++) {
+        S.ent_gptr[size_t(l) * (G + 1) + g] = at;
+        at += cnt[size_t(l) * G + g];
+      }
+      S.ent_gptr[size_t(l) * (G + 1) + G] = at;
+    }
+  }
+  {
     std::vector<int64_t> fill(S.ent_ptr.begin(), S.ent_ptr.end() - 1);
     for (int i = 0; i < nmat; i++) {
-      const SymOne& O = one[i];
+      SymOne& O = one[i];
       const Parts& A = *mats[i].A;
       for (size_t t = 0; t < O.e_sn.size(); t++) {
         const int32_t g = sn_base[i] + O.e_sn[t];
@@ -328,6 +358,11 @@ void symbolic_batch(const std::vector<MatrixInput>& mats, int leaf, int maxsn, S
         S.em[q] = A.M[O.e_src[t]];
         S.eb[q] = A.B[O.e_src[t]];
       }
+      // the per-entry maps and (when asked) the input values are not needed any more
+      std::vector<int32_t>().swap(O.e_sn);
+      std::vector<int64_t>().swap(O.e_off);
+      std::vector<int64_t>().swap(O.e_src);
+      if (mats[i].release) *mats[i].release = Parts();
     }
   }
   // extend-add maps and forward-solve contributors

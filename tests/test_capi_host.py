@@ -102,3 +102,16 @@ def test_sweep_schedules_cover_every_kernel_variant(hzmod):
     for bad in (dict(sweep_tasks=3), dict(bwd_chunk=31), dict(bwd_chunk=33), dict(bwd_chunk=514)):
         with pytest.raises(hzmod.HzError):
             hzmod.plan(synth.tiny_problem(), **bad)
+
+
+def test_factor_groups_shrink_the_frontal_workspace(hzmod):
+    """Factorising the subdomains in groups plans each group's fronts from the start of one
+    workspace: the workspace shrinks, nothing else in the plan changes."""
+    p = synth.overthrust_problem(seed=0, freq=1.25, nsub=8, overlap=2, restart=50, levels=2)
+    a = hzmod.plan(p, precision=hzmod.HZ_MIXED)
+    b = hzmod.plan(p, precision=hzmod.HZ_MIXED, factor_group=2)
+    assert b["front_bytes"] < a["front_bytes"]
+    for key in ("n", "sum_ni", "nnz_factor", "nnz_local", "nsupernodes", "device_bytes"):
+        assert a[key] == b[key], key
+    with pytest.raises(hzmod.HzError):
+        hzmod.plan(p, factor_group=-1)

@@ -152,3 +152,23 @@ def test_mixed_solve_against_oracle(hzmod, case, sweep):
     itg, ito, _ = out[1e-6]
     assert abs(itg - ito) <= 1, out
     assert out[1e-9][2] <= 1e-6, out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grouped_factorisation_is_bitwise_identical(hzmod, case, prec):
+    """factor_group = 2 factorises the 7 subdomains in four groups that reuse one frontal
+    workspace; every front sees the same kernels in the same order, so M^{-1} v is bitwise
+    that of the all-at-once factorisation (and so matches the oracle as above)."""
+    import torch
+    p, S, kappa, v, ref = case
+    out = []
+    for grp in (0, 2):
+        G = hzmod.Solver(p, precision=hzmod.HZ_MIXED if prec == "mixed" else hzmod.HZ_FP64, factor_group=grp)
+        try:
+            G.factor()
+            st = G.stats()
+            out.append((st["front_bytes"], G.apply_M(torch.from_numpy(v).cuda()).cpu().numpy()))
+        finally:
+            G.close()
+    assert out[1][0] < out[0][0]                       # a smaller workspace
+    assert np.array_equal(out[0][1], out[1][1])
