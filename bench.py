@@ -45,10 +45,12 @@ WORKLOADS = {
     # the batching form: 128 sources on the 16 x 8 surface grid at 50 m depth, uneven parts
     # (weights drawn in [0.6, 1.4]), pseudo-block FGMRES with 16 slots, mixed precision
     "overthrust-5hz-128": dict(kind="overthrust", cells=None, freq=5.0, nsub=64, overlap=2, restart=50,
-                               part_jitter=0.4, nrhs=128, block=16, precisions=["mixed"]),
+                               part_jitter=0.4, nrhs=128, block=16, precisions=["mixed"],
+                               fp64_note="not run in this workload: the 5 Hz FP64 figure is in overthrust-5hz"),
     "overthrust-10hz": dict(kind="overthrust", cells=None, epw=1.19, freq=10.0, nsub=512, overlap=1,
                             restart=50, coarse="oras", coarse_tol=0.1, factor_group=64, precisions=["mixed"],
-                            fp64_check_tol=1e-10),
+                            fp64_check_tol=1e-10,
+                            fp64_note="not run: the complex128 local factors alone would need about 240 GB"),
     "tiny": dict(kind="tiny"),
 }
 # Inner iterations each full workload takes to 1e-6 on the GPU path (the 5 Hz count, 74 in both
@@ -791,8 +793,8 @@ def main():
                         "clocks": F["clocks"]}
     if R.get("check"):
         line["fp64_check"] = R["check"]
-    if "fp64" not in results and spec.get("precisions") == ["mixed"]:
-        line["fp64"] = {"value": None, "note": "not run: complex128 local factors do not fit one GPU at this size"}
+    if "fp64" not in results and spec.get("fp64_note"):
+        line["fp64"] = {"value": None, "note": spec["fp64_note"]}
     if one is not None:
         line["one_level"] = dict(one, precision="mixed",
                                  note="levels=1 on the same mesh and partition; no coarse space")
