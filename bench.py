@@ -505,6 +505,44 @@ def crossover_bench(args):
                       "precision": "mixed", "tol": 1e-6}))
 
 
+def block_bench(args):
+    """Block FGMRES against pseudo-block FGMRES on the 5 Hz workload: 16 sources from the
+    16 x 8 surface grid at 50 m depth, solved with block sizes 4, 8 and 16 (16 / S batches
+    of one block Krylov space each, against 16 / S rounds of S independent slots), mixed
+    precision, tol 1e-6.  One warm-up solve of the first batch, then one timed solve of
+    all 16 sources per configuration."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2004_06309_gb300 import build, hz
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    p = make_problem(WORKLOADS["overthrust-5hz"])
+    rows = []
+    for S in args.block_sizes:
+        for kind in ("pseudo", "block"):
+            G = hz.Solver(p, precision=hz.HZ_MIXED, stream=stream, block_size=S,
+                          krylov=hz.HZ_KRYLOV_BLOCK if kind == "block" else hz.HZ_KRYLOV_PSEUDO_BLOCK)
+            G.factor()
+            B = torch.from_numpy(np.asfortranarray(G.point_sources(synth.surface_source_grid()[:16]))).cuda()
+            G.solve(B[:, :S].contiguous())
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            X, info = G.solve(B)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            rows.append({"block_size": S, "krylov": kind, "rhs_per_s": 16 / dt, "seconds": dt,
+                         "iterations": [int(i[0]) for i in info], "ok": all(i[1] == 0 for i in info),
+                         "max_rel_residual": max(i[2] for i in info)})
+            G.close()
+            torch.cuda.empty_cache()
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"experiment": "block FGMRES against pseudo-block FGMRES, 5 Hz workload, 16 sources",
+                      "rows": rows, "precision": "mixed", "tol": 1e-6}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -512,7 +550,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--workload", default="overthrust-5hz",
-                    choices=list(WORKLOADS) + ["serving", "trends", "crossover"])
+                    choices=list(WORKLOADS) + ["serving", "trends", "crossover", "block"])
     ap.add_argument("--serve-batch", type=int, default=16, help="largest sources per request (serving)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -530,6 +568,8 @@ def main():
     ap.add_argument("--coarse-maxit", type=int, default=0, help="inner coarse iterations at most (0: default)")
     ap.add_argument("--recycle", type=int, default=0,
                     help="GCRO-DR: recycled-space dimension kept across the step's right-hand sides (0: FGMRES)")
+    ap.add_argument("--block-sizes", type=int, nargs="+", default=[4, 8, 16],
+                    help="block sizes of the block-against-pseudo-block comparison (--workload block)")
     ap.add_argument("--one-level-steps", type=int, default=3,
                     help="timed steps of the one-level arm on the same mesh (mixed precision; 0: skip)")
     ap.add_argument("--oracle-sample", default="", help=argparse.SUPPRESS)
@@ -539,9 +579,10 @@ def main():
         print(json.dumps(run_oracle_sample(args.oracle_sample, args.steps, args.warmup)))
         return
 
-    if args.workload in ("serving", "trends", "crossover") and args.impl == "hz":
+    if args.workload in ("serving", "trends", "crossover", "block") and args.impl == "hz":
         if int(os.environ.get("RANK", "0")) == 0:
-            {"serving": serve_bench, "trends": trends_bench, "crossover": crossover_bench}[args.workload](args)
+            {"serving": serve_bench, "trends": trends_bench, "crossover": crossover_bench,
+             "block": block_bench}[args.workload](args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

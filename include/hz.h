@@ -53,6 +53,7 @@ typedef enum {
 enum { HZ_TAG_DIRICHLET = 0, HZ_TAG_ABC = 1 };
 enum { HZ_FP64 = 0, HZ_MIXED = 1 };
 enum { HZ_COARSE_DIRECT = 0, HZ_COARSE_ORAS = 1 };
+enum { HZ_KRYLOV_PSEUDO_BLOCK = 0, HZ_KRYLOV_BLOCK = 1 };
 
 /* Mesh (Eq. 1-2).  All arrays are host pointers, read during hz_setup_mesh only. */
 typedef struct {
@@ -147,6 +148,15 @@ typedef struct {
                                the other, so the workspace (hz_stats.front_bytes) is
                                that of the largest group.  0: all subdomains at once.
                                The factors do not depend on it.                       */
+  int32_t krylov;           /* with block_size > 1: HZ_KRYLOV_PSEUDO_BLOCK (default): each
+                               right-hand side keeps its own Krylov space; HZ_KRYLOV_BLOCK:
+                               block FGMRES, one block Krylov space for up to block_size
+                               right-hand sides at a time (block CGS2 against the basis,
+                               the new block orthonormalised column by column, Givens
+                               rotations of the band Hessenberg matrix; the iteration
+                               count is the number of block steps).  The multi-source
+                               remark of the experiments section sets block GMRES
+                               beside pseudo-block GMRES.                             */
 } hz_options;
 
 typedef struct {

@@ -85,6 +85,10 @@ struct hz_ctx {
   double *csb = nullptr, *scalb = nullptr;
   int* brkb = nullptr;
   double2 *partial_s = nullptr, *h1s = nullptr, *h2s = nullptr, *nrms = nullptr;   // slot-batched CGS2
+  // block FGMRES (krylov == HZ_KRYLOV_BLOCK): coefficients of the chunked block CGS2 passes
+  // (2 passes x chunks of 64 basis columns x S columns x 65) and the cycle-end Y (m S x S)
+  int krylov = 0;
+  double2 *hblk = nullptr, *yblk = nullptr;
   // slot engine (continuous pseudo-block FGMRES): one right-hand side per slot
   enum { SLOT_FREE = hz_engine::SLOT_FREE, SLOT_RUN = hz_engine::SLOT_RUN, SLOT_DONE = hz_engine::SLOT_DONE };
   struct Slot {
@@ -1373,6 +1377,271 @@ hz_status solve_slots(hz_ctx* c, const double2* rhs, int nrhs, double tol, doubl
   return HZ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Block FGMRES (krylov == HZ_KRYLOV_BLOCK): one block Krylov space for s <= S
+// right-hand sides.  The steps are those of the oracle's block_fgmres:
+//   * the residual block is factored column by column (CGS2 against the block's
+//     earlier columns) into V_0 and the upper-triangular beta;
+//   * block step j: Z_j = M^{-1} V_j and W = A Z_j on the interleaved slot operators;
+//     two classical Gram-Schmidt passes of the s columns against V_0..V_j, in chunks of
+//     64 basis columns (all chunks' coefficients before any update), then the columns
+//     of W orthonormalised among themselves into V_{j+1};
+//   * the band Hessenberg matrix is reduced by Givens rotations on the host (each
+//     between the diagonal row and one of the s rows below it, bottom row first), the
+//     same rotations are applied to G = [beta; 0], and the estimate of right-hand side i
+//     is the norm of column i of G's rows below the triangle;
+//   * the cycle ends when every estimate / ||b_i|| <= tol, on a happy breakdown or at
+//     max_iter; x += Z R^{-1} G_top; the true residuals are checked and the next cycle
+//     restarts from them.
+// Device storage is the slot engine's: V = Vb as one n x (m + 1) S block, Z = Zb,
+// W = Wc, B = Bc, X = Xc.  The host waits once per column of the per-block
+// orthonormalisation, so block steps run as eager launches.
+// ---------------------------------------------------------------------------
+hz_status block_orthonormalise(hz_ctx* c, double2* W, int s, double2* Q, std::vector<cplx>& R, const double* w0,
+                               bool& brk) {
+  const int64_t n = c->n;
+  const int nb = hz::cgs_blocks();
+  cudaStream_t st = c->st;
+  R.assign(size_t(s) * s, cplx(0.0, 0.0));
+  brk = false;
+  std::vector<double2> hh(3 * 65);
+  for (int q = 0; q < s; q++) {
+    double2* w = W + int64_t(q) * n;
+    if (q > 0) {
+      hz::launch_cgs(n, q, Q, n, nullptr, w, q, c->partial, st);
+      hz::launch_reduce(c->partial, nb, q, c->h1, st);
+      hz::launch_cgs(n, q, Q, n, c->h1, w, q, c->partial, st);
+      hz::launch_reduce(c->partial, nb, q, c->h2, st);
+      hz::launch_cgs(n, q, Q, n, c->h2, w, 0, c->partial, st);
+    } else {
+      hz::launch_cgs(n, 0, Q, n, nullptr, w, 0, c->partial, st);
+    }
+    hz::launch_reduce(c->partial, nb, 0, c->nrm, st);
+    CU(cudaMemcpyAsync(hh.data(), c->h1, 65 * 16, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(hh.data() + 65, c->h2, 65 * 16, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(hh.data() + 130, c->nrm, 65 * 16, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (int i = 0; i < q; i++) R[i + size_t(q) * s] = cplx(hh[i].x + hh[65 + i].x, hh[i].y + hh[65 + i].y);
+    const double nr = std::sqrt(hh[130 + 64].x);
+    R[q + size_t(q) * s] = nr;
+    if (!(nr > 1e-14 * w0[q])) brk = true;
+    c->h_pin[6] = nr > 0.0 ? 1.0 / nr : 0.0;
+    CU(cudaMemcpyAsync(c->scal + 6, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
+    hz::launch_scale(n, w, c->scal + 6, Q + int64_t(q) * n, st);
+  }
+  CU(cudaStreamSynchronize(st));
+  return HZ_OK;
+}
+
+// Block step j: Z_j = M^{-1} V_j, W = A Z_j, block CGS2 against V_0..V_j and the new block.
+// hcol ((j + 2) s x s, column-major, host): the step's column of the block Hessenberg matrix.
+hz_status block_step(hz_ctx* c, int j, int s, std::vector<cplx>& hcol, bool& brk) {
+  const int S = c->S;
+  const int64_t n = c->n;
+  cudaStream_t st = c->st;
+  hz::SlotCols vin, zout, wout;
+  for (int i = 0; i < 16; i++) vin.o[i] = zout.o[i] = wout.o[i] = -1;
+  for (int i = 0; i < s; i++) {
+    vin.o[i] = int64_t(j * s + i) * n;
+    zout.o[i] = int64_t(j * s + i) * n;
+    wout.o[i] = int64_t(i) * n;
+  }
+  hz::launch_interleave(n, S, vin, c->Vb, c->Xi, st);
+  apply_prec_multi(c, c->Xi, c->Yi);
+  hz::launch_deinterleave(n, S, zout, c->Yi, c->Zb, st);
+  hz::launch_spmv_multi(n, S, c->d_rp, c->d_ci, c->d_A, c->Yi, nullptr, c->Wi, st);
+  hz::launch_deinterleave(n, S, wout, c->Wi, c->Wc, st);
+  std::vector<double> w0(s);
+  for (int i = 0; i < s; i++) TRY(norm2(c, c->Wc + int64_t(i) * n, w0[i]));
+  const int p = (j + 1) * s;
+  const int nch = (p + 63) / 64;
+  hz::SlotCgs pc{};
+  for (int pass = 0; pass < 2; pass++) {
+    for (int k = 0; k < nch; k++) {
+      for (int i = 0; i < 16; i++) {
+        const bool on = i < s;
+        pc.V[i] = on ? c->Vb + int64_t(64) * k * n : nullptr;
+        pc.w[i] = on ? c->Wc + int64_t(i) * n : nullptr;
+        pc.h[i] = nullptr;
+        pc.ncols[i] = on ? std::min(64, p - 64 * k) : -1;
+      }
+      hz::launch_cgs_slots(n, S, pc, false, true, c->partial_s, c->hblk + (int64_t(pass) * nch + k) * S * 65, st);
+    }
+    for (int k = 0; k < nch; k++) {
+      for (int i = 0; i < 16; i++) {
+        const bool on = i < s;
+        pc.V[i] = on ? c->Vb + int64_t(64) * k * n : nullptr;
+        pc.w[i] = on ? c->Wc + int64_t(i) * n : nullptr;
+        pc.h[i] = on ? c->hblk + ((int64_t(pass) * nch + k) * S + i) * 65 : nullptr;
+        pc.ncols[i] = on ? std::min(64, p - 64 * k) : -1;
+      }
+      hz::launch_cgs_slots(n, S, pc, true, false, c->partial_s, c->nrms, st);
+    }
+  }
+  std::vector<double2> hb(size_t(2) * nch * S * 65);
+  CU(cudaMemcpyAsync(hb.data(), c->hblk, hb.size() * 16, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const int ld = p + s;
+  hcol.assign(size_t(ld) * s, cplx(0.0, 0.0));
+  for (int i = 0; i < s; i++)
+    for (int r = 0; r < p; r++) {
+      const int k = r / 64, jj = r % 64;
+      const double2 a = hb[((size_t(0) * nch + k) * S + i) * 65 + jj];
+      const double2 b = hb[((size_t(1) * nch + k) * S + i) * 65 + jj];
+      hcol[r + size_t(i) * ld] = cplx(a.x + b.x, a.y + b.y);
+    }
+  std::vector<cplx> R;
+  TRY(block_orthonormalise(c, c->Wc, s, c->Vb + int64_t(p) * n, R, w0.data(), brk));
+  for (int i = 0; i < s; i++)
+    for (int r = 0; r < s; r++) hcol[p + r + size_t(i) * ld] = R[r + size_t(i) * s];
+  return HZ_OK;
+}
+
+// Solves the s right-hand sides in Bc[0..s) (all nonzero) into Xc[0..s).
+hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
+  const int64_t n = c->n;
+  const int m = c->restart;
+  cudaStream_t st = c->st;
+  for (int i = 0; i < c->S; i++) c->slots[i].state = i < s ? hz_ctx::SLOT_RUN : hz_ctx::SLOT_FREE;
+  std::vector<double> bn(s), rel(s, 0.0);
+  for (int i = 0; i < s; i++) TRY(norm2(c, c->Bc + int64_t(i) * n, bn[i]));
+  CU(cudaMemsetAsync(c->Xc, 0, size_t(s) * n * 16, st));
+  CU(cudaMemcpyAsync(c->Wc, c->Bc, size_t(s) * n * 16, cudaMemcpyDeviceToDevice, st));
+  const int ldh = (m + 1) * s;
+  std::vector<cplx> H, G, hcol, beta;
+  struct Rot { int i, r; double cs; cplx sn; };
+  std::vector<Rot> rots;
+  auto givens = [](cplx a, cplx b, double& cs, cplx& sn) {
+    const double aa = std::abs(a);
+    if (aa == 0.0) { cs = 0.0; sn = cplx(1.0, 0.0); return; }
+    const double rho = std::sqrt(aa * aa + std::norm(b));
+    cs = aa / rho;
+    sn = (a / aa) * std::conj(b) / rho;
+  };
+  int its = 0;
+  bool nonfinite = false;
+  for (;;) {
+    std::vector<double> rn(s);
+    for (int i = 0; i < s; i++) TRY(norm2(c, c->Wc + int64_t(i) * n, rn[i]));
+    bool brk0 = false;
+    TRY(block_orthonormalise(c, c->Wc, s, c->Vb, beta, rn.data(), brk0));
+    H.assign(size_t(ldh) * m * s, cplx(0.0, 0.0));
+    G.assign(size_t(ldh) * s, cplx(0.0, 0.0));
+    for (int i = 0; i < s; i++)
+      for (int r = 0; r <= i; r++) G[r + size_t(i) * ldh] = beta[r + size_t(i) * s];
+    rots.clear();
+    int k = 0;
+    for (int j = 0; j < m; j++) {
+      bool brk = false;
+      TRY(block_step(c, j, s, hcol, brk));
+      const int lc = (j + 2) * s;
+      for (int q = 0; q < s; q++)
+        for (int r = 0; r < lc; r++) H[r + size_t(j * s + q) * ldh] = hcol[r + size_t(q) * lc];
+      for (int q = 0; q < s; q++) {
+        const int col = j * s + q;
+        cplx* hc = H.data() + size_t(col) * ldh;
+        for (const Rot& g : rots) {
+          const cplx t = g.cs * hc[g.i] + g.sn * hc[g.r];
+          hc[g.r] = -std::conj(g.sn) * hc[g.i] + g.cs * hc[g.r];
+          hc[g.i] = t;
+        }
+        for (int r = col + s; r > col; r--) {               // bottom row first
+          double cs;
+          cplx sn;
+          givens(hc[col], hc[r], cs, sn);
+          hc[col] = cs * hc[col] + sn * hc[r];
+          hc[r] = 0.0;
+          for (int i = 0; i < s; i++) {
+            cplx* gi = G.data() + size_t(i) * ldh;
+            const cplx t = cs * gi[col] + sn * gi[r];
+            gi[r] = -std::conj(sn) * gi[col] + cs * gi[r];
+            gi[col] = t;
+          }
+          rots.push_back({col, r, cs, sn});
+        }
+      }
+      its++;
+      k = j + 1;
+      bool all = true;
+      for (int i = 0; i < s; i++) {
+        double e = 0.0;
+        for (int r = k * s; r < (k + 1) * s; r++) e += std::norm(G[r + size_t(i) * ldh]);
+        const double est = std::sqrt(e) / bn[i];
+        if (!std::isfinite(est)) nonfinite = true;
+        all = all && est <= tol;
+      }
+      if (brk || all || nonfinite || its >= c->max_iter) break;
+    }
+    // Y = R^{-1} G_top, x += Z Y (64 columns of Z at a time)
+    const int p = k * s;
+    std::vector<cplx> Y(size_t(p) * s);
+    for (int i = 0; i < s; i++)
+      for (int r = p - 1; r >= 0; r--) {
+        cplx acc = G[r + size_t(i) * ldh];
+        for (int l = r + 1; l < p; l++) acc -= H[r + size_t(l) * ldh] * Y[l + size_t(i) * p];
+        Y[r + size_t(i) * p] = acc / H[r + size_t(r) * ldh];
+      }
+    CU(cudaMemcpyAsync(c->yblk, Y.data(), Y.size() * 16, cudaMemcpyHostToDevice, st));
+    for (int i = 0; i < s; i++)
+      for (int q0 = 0; q0 < p; q0 += 64)
+        hz::launch_gemv_add(n, std::min(64, p - q0), c->yblk + size_t(i) * p + q0, c->Zb + int64_t(q0) * n, n,
+                            c->Xc + int64_t(i) * n, st);
+    // true residuals (into W, the next cycle's residual block)
+    bool done = true;
+    for (int i = 0; i < s; i++) {
+      hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, c->Xc + int64_t(i) * n, c->Bc + int64_t(i) * n,
+                      c->Wc + int64_t(i) * n, st);
+      double r;
+      TRY(norm2(c, c->Wc + int64_t(i) * n, r));
+      rel[i] = r / bn[i];
+      if (!std::isfinite(rel[i])) nonfinite = true;
+      done = done && rel[i] <= tol;
+    }
+    if (done || nonfinite || its >= c->max_iter) break;
+  }
+  for (int i = 0; i < s; i++) {
+    info[i].iterations = its;
+    info[i].rel_residual = rel[i];
+    info[i].status = nonfinite ? HZ_ERR_BREAKDOWN : (rel[i] <= tol ? HZ_OK : HZ_ERR_NOT_CONVERGED);
+  }
+  for (int i = 0; i < c->S; i++) c->slots[i].state = hz_ctx::SLOT_FREE;
+  return HZ_OK;
+}
+
+// Block FGMRES over nrhs right-hand sides in batches of S; zero columns get x = 0.
+hz_status solve_block(hz_ctx* c, const double2* rhs, int nrhs, double tol, double2* x, bool on_device,
+                      hz_rhs_info* info, hz_status& worst) {
+  const int64_t n = c->n;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  int next = 0;
+  while (next < nrhs) {
+    std::vector<int> cols;
+    while (next < nrhs && int(cols.size()) < c->S) {
+      const int k = next++;
+      CU(cudaMemcpyAsync(c->Bc + int64_t(cols.size()) * n, rhs + int64_t(k) * n, size_t(n) * 16, kin, c->st));
+      double bnorm;
+      TRY(norm2(c, c->Bc + int64_t(cols.size()) * n, bnorm));
+      if (bnorm == 0.0) {                                    // x = 0, no iteration
+        CU(cudaMemsetAsync(c->w, 0, size_t(n) * 16, c->st));
+        CU(cudaMemcpyAsync(x + int64_t(k) * n, c->w, size_t(n) * 16, kout, c->st));
+        if (info) info[k] = hz_rhs_info{0, HZ_OK, 0.0};
+        continue;
+      }
+      cols.push_back(k);
+    }
+    if (cols.empty()) continue;
+    std::vector<hz_rhs_info> inf(cols.size());
+    TRY(block_batch(c, int(cols.size()), tol, inf.data()));
+    for (size_t i = 0; i < cols.size(); i++) {
+      CU(cudaMemcpyAsync(x + int64_t(cols[i]) * n, c->Xc + int64_t(i) * n, size_t(n) * 16, kout, c->st));
+      if (info) info[cols[i]] = inf[i];
+      if (inf[i].status != HZ_OK && worst == HZ_OK) worst = hz_status(inf[i].status);
+    }
+  }
+  return HZ_OK;
+}
+
 // Autotuner: lanes per row of the complex SpMV, timed on this matrix (3 runs each
 // after a warm-up, CUDA events on the context stream); the fastest is kept.
 hz_status tune_spmv(hz_ctx* c) {
@@ -1511,6 +1780,10 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
   if (op->bwd_chunk != 0 && (op->bwd_chunk < 32 || op->bwd_chunk > 512 || op->bwd_chunk % 2 != 0))
     return fail(c, HZ_ERR_ARG, "bwd_chunk must be 0 or even in [32, 512]");
   if (op->factor_group < 0) return fail(c, HZ_ERR_ARG, "factor_group must be >= 0");
+  if (op->krylov != HZ_KRYLOV_PSEUDO_BLOCK && op->krylov != HZ_KRYLOV_BLOCK)
+    return fail(c, HZ_ERR_ARG, "krylov must be HZ_KRYLOV_PSEUDO_BLOCK or HZ_KRYLOV_BLOCK");
+  if (op->krylov == HZ_KRYLOV_BLOCK && op->block_size < 2)
+    return fail(c, HZ_ERR_ARG, "block FGMRES needs block_size >= 2");
   const int64_t nv = md->nv, ne = md->ne, nf = md->nf;
   for (int64_t q = 0; q < ne * 4; q++)
     if (md->tets[q] < 0 || md->tets[q] >= nv) return fail(c, HZ_ERR_ARG, "tet vertex id out of range");
@@ -1831,6 +2104,12 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
     SETUP_TRY(dalloc(c, &c->h2s, int64_t(S) * 65));
     SETUP_TRY(dalloc(c, &c->nrms, int64_t(S) * 65));
     c->slots.assign(S, hz_ctx::Slot{});
+    c->krylov = op->krylov;
+    if (c->krylov == HZ_KRYLOV_BLOCK) {
+      const int64_t nch = (int64_t(m) * S + 63) / 64;
+      SETUP_TRY(dalloc(c, &c->hblk, 2 * nch * S * 65));
+      SETUP_TRY(dalloc(c, &c->yblk, int64_t(m) * S * S));
+    }
   }
   // pinned scalars: 8 for the single-RHS loop, then 16 x 8 per-RHS scalars and 16 flags
   if (cudaMallocHost((void**)&c->h_pin, hz_ctx::PIN_TOTAL * sizeof(double)) != cudaSuccess) {
@@ -1941,6 +2220,11 @@ extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double t
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run before hz_solve");
   const int64_t n = c->n;
   hz_status worst = HZ_OK;
+  if (c->S && nrhs > 1 && c->krylov == HZ_KRYLOV_BLOCK) {
+    TRY(solve_block(c, (const double2*)rhs, nrhs, tol, (double2*)x, on_device != 0, info, worst));
+    CU(cudaStreamSynchronize(c->st));
+    return worst;
+  }
   if (c->S && nrhs > 1) {
     TRY(solve_slots(c, (const double2*)rhs, nrhs, tol, (double2*)x, on_device != 0, info, worst));
     CU(cudaStreamSynchronize(c->st));

@@ -194,6 +194,7 @@ void launch_combo(int64_t n, int nb1, const double2* B1, int64_t ld1, int nb2, c
                   cudaStream_t st);
 void launch_init_cycle(const double2* nrm2, double2* g, int m, double* invbeta, double* beta, cudaStream_t st);
 void launch_scale(int64_t n, const double2* w, const double* s, double2* out, cudaStream_t st);
+void launch_gemv_add(int64_t n, int k, const double2* y, const double2* Zs, int64_t ldz, double2* x, cudaStream_t st);
 void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y,
                      const double2* Zs, int64_t ldz, double2* x, cudaStream_t st);
 void launch_add2(int n, const double2* a, const double2* b, double2* out, cudaStream_t st);

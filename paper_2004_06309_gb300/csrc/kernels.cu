@@ -1837,6 +1837,12 @@ __global__ void k_gemv_add(int64_t n, int k, const double2* y, const double2* Zs
   }
 }
 
+// x += Zs[:, 0:k) y (k <= 64)
+void launch_gemv_add(int64_t n, int k, const double2* y, const double2* Zs, int64_t ldz, double2* x, cudaStream_t st) {
+  HZ_COUNT();
+  k_gemv_add<<<grid_for(n, 256), 256, 0, st>>>(n, k, y, Zs, ldz, x);
+}
+
 void launch_update_x(int64_t n, int k, const double2* H, int ldh, const double2* g, double2* y, const double2* Zs,
                      int64_t ldz, double2* x, cudaStream_t st) {
   HZ_COUNT();

@@ -154,3 +154,84 @@ def test_recycling_helps_the_next_right_hand_side():
         its_plain.append(krylov.fgmres(S.apply_A, S.apply_M, B[:, j], tol=1e-6, m=20)[1])
     assert its_rec[0] == its_plain[0]                 # nothing recycled yet
     assert sum(its_rec[1:]) < sum(its_plain[1:]), (its_rec, its_plain)
+
+
+# --- block FGMRES ------------------------------------------------------------------
+
+def _block_problem(n=60, s=3, seed=7):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 3 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    d = 1.0 + rng.uniform(0, 1, n)                       # a diagonal right preconditioner
+    B = rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))
+    return A, (lambda v: A @ v), (lambda v: v / d), d, B
+
+
+def test_block_fgmres_with_one_column_is_fgmres():
+    A, fa, fm, d, B = _block_problem()
+    x1, i1, r1, o1 = krylov.fgmres(fa, fm, B[:, 0], tol=1e-10, m=8)
+    X, ib, rb, ob = krylov.block_fgmres(fa, fm, B[:, :1], tol=1e-10, m=8)
+    assert o1 and ob and i1 == ib
+    assert np.linalg.norm(X[:, 0] - x1) <= 1e-12 * np.linalg.norm(x1)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+def test_block_fgmres_minimises_over_the_block_krylov_space(k):
+    """After k block steps of one cycle, each column's residual is the least-squares minimum
+    of ||b_i - A M^{-1} K y|| over the whole block Krylov space K = [B, A M^{-1} B, ...]
+    (every column searches the space spanned by all the columns' Krylov vectors)."""
+    A, fa, fm, d, B = _block_problem()
+    s = B.shape[1]
+    X, its, rel, ok = krylov.block_fgmres(fa, fm, B, tol=1e-300, m=20, maxit=k)
+    assert its == k
+    blocks = [B]
+    for _ in range(1, k):
+        Q = blocks[-1]
+        blocks.append(np.column_stack([fa(fm(Q[:, c])) for c in range(s)]))
+    Q, _ = np.linalg.qr(np.hstack(blocks))
+    AMQ = np.column_stack([fa(fm(Q[:, c])) for c in range(Q.shape[1])])
+    for i in range(s):
+        y, *_ = np.linalg.lstsq(AMQ, B[:, i], rcond=None)
+        rmin = np.linalg.norm(B[:, i] - AMQ @ y) / np.linalg.norm(B[:, i])
+        r_block = np.linalg.norm(B[:, i] - A @ X[:, i]) / np.linalg.norm(B[:, i])
+        assert abs(r_block - rmin) <= 1e-9 * max(rmin, 1e-6), (k, i, r_block, rmin)
+        assert abs(rel[i] - r_block) <= 1e-12
+
+
+def test_block_fgmres_needs_no_more_steps_than_its_slowest_column():
+    """The block space contains each column's own Krylov space of the same step count, so
+    without restarts the block solve converges in at most as many steps as the slowest
+    single-column solve, and it solves every column."""
+    A, fa, fm, d, B = _block_problem(n=80, s=4, seed=3)
+    single = [krylov.fgmres(fa, fm, B[:, i], tol=1e-8, m=80)[1] for i in range(4)]
+    X, its, rel, ok = krylov.block_fgmres(fa, fm, B, tol=1e-8, m=80)
+    assert ok and its <= max(single), (its, single)
+    assert np.all(rel <= 1e-8)
+    assert np.linalg.norm(X - np.linalg.solve(A, B)) <= 1e-6 * np.linalg.norm(np.linalg.solve(A, B))
+
+
+def test_block_fgmres_restarts_and_zero_columns():
+    A, fa, fm, d, B = _block_problem(n=60, s=3, seed=11)
+    B[:, 1] = 0.0
+    X, its, rel, ok = krylov.block_fgmres(fa, fm, B, tol=1e-9, m=3)
+    assert ok and its > 3                                # several cycles
+    assert np.all(X[:, 1] == 0) and rel[1] == 0.0
+    for i in (0, 2):
+        assert np.linalg.norm(B[:, i] - A @ X[:, i]) <= 1e-9 * np.linalg.norm(B[:, i])
+
+
+def test_block_arnoldi_relation_and_orthonormal_basis():
+    """A Z = V H holds to rounding and V^H V = I on a problem whose Krylov vectors align
+    quickly (a few dominant eigenvalues), where one classical Gram-Schmidt pass would lose
+    orthogonality: the second pass and its coefficients are needed for both."""
+    rng = np.random.default_rng(5)
+    n, s = 120, 3
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    ev = np.concatenate([[1e4, 5e3, 2e3, 1e3], 1.0 + rng.uniform(0, 1, n - 4)])
+    A = (Q * ev) @ Q.conj().T
+    B = rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))
+    dg = {}
+    krylov.block_fgmres(lambda v: A @ v, lambda v: v, B, tol=1e-300, m=12, maxit=12, diagnostics=dg)
+    V, Z, H = dg["V"], dg["Z"], dg["H"]
+    assert np.linalg.norm(V.conj().T @ V - np.eye(V.shape[1])) <= 1e-12
+    rel = np.linalg.norm(A @ Z - V @ H) / np.linalg.norm(A @ Z)
+    assert rel <= 1e-13, rel
