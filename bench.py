@@ -568,6 +568,8 @@ def main():
     ap.add_argument("--coarse-maxit", type=int, default=0, help="inner coarse iterations at most (0: default)")
     ap.add_argument("--recycle", type=int, default=0,
                     help="GCRO-DR: recycled-space dimension kept across the step's right-hand sides (0: FGMRES)")
+    ap.add_argument("--tune-sweeps", type=int, default=1,
+                    help="1: autotune the sweep task shapes at the first factorisation (0: library default shapes)")
     ap.add_argument("--block-sizes", type=int, nargs="+", default=[4, 8, 16],
                     help="block sizes of the block-against-pseudo-block comparison (--workload block)")
     ap.add_argument("--one-level-steps", type=int, default=3,
@@ -656,7 +658,7 @@ def main():
                       coarse_solver=hz.HZ_COARSE_ORAS if coarse == "oras" else hz.HZ_COARSE_DIRECT,
                       coarse_tol=args.coarse_tol or spec.get("coarse_tol", 0.0), coarse_maxit=args.coarse_maxit,
                       recycle=args.recycle,
-                      factor_group=spec.get("factor_group", 0))
+                      factor_group=spec.get("factor_group", 0), tune_sweeps=args.tune_sweeps)
         tf = time.time()
         G.factor()
         torch.cuda.synchronize()
@@ -804,7 +806,7 @@ def main():
                    "part_jitter": spec.get("part_jitter", 0.0),
                    "coarse_solver": coarse, "recycle": args.recycle,
                    "coarse_tol": args.coarse_tol or spec.get("coarse_tol", 0.0),
-                   "factor_group": spec.get("factor_group", 0),
+                   "factor_group": spec.get("factor_group", 0), "tune_sweeps": args.tune_sweeps,
                    "l2": "inputs larger than L2 (factors >> 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "iterations": R["iterations"][-1], "rel_residual": R["rel"],
@@ -819,6 +821,7 @@ def main():
         "phases_gbytes": {k: round(v["bytes"] / 1e9, 4) for k, v in prof.items()},
         "phases_gflops": {k: round(v["flops"] / 1e9, 4) for k, v in prof.items()},
         "stats": {k: R["stats"][k] for k in ("nnz", "n_coarse", "sum_ni", "nnz_factor", "nnz_factor_coarse",
+                                             "sweep_chunk", "sweep_scale",
                                              "nsupernodes", "nlevels", "front_bytes", "device_bytes",
                                              "setup_seconds", "coarse_solves", "coarse_iterations")},
         "generate_seconds": t_gen,

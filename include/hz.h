@@ -157,6 +157,15 @@ typedef struct {
                                count is the number of block steps).  The multi-source
                                remark of the experiments section sets block GMRES
                                beside pseudo-block GMRES.                             */
+  int32_t tune_sweeps;      /* 1: at the first hz_factor, time the triangular sweeps of
+                               the local factors and of the direct coarse factor under
+                               eight task-shape schedules each (the task count below
+                               which a tree level gets narrow tasks scaled by 1/4, 1/2,
+                               1 or 2; wide backward chunks of 256 or 512 rows, 128 or
+                               256 in complex128) and keep the fastest; only with
+                               sweep_tasks == 0 and bwd_chunk == 0.  0: the default
+                               schedule.  The choice sets summation orders, so
+                               contexts that must agree bitwise leave it off.          */
 } hz_options;
 
 typedef struct {
@@ -200,6 +209,9 @@ typedef struct {
   int64_t tc_multi_fronts;  /* complex64: fronts whose update spans several tiles       */
   int32_t tc_max_kstages;   /* complex64: most 32-deep K stages of one tile (2k / 32)   */
   int32_t max_snode_width;  /* widest local supernode (pivot columns)                   */
+  int32_t sweep_chunk;      /* rows of a wide backward chunk in use (hz_setup_mesh or
+                               the sweep autotuner)                                   */
+  double sweep_scale;       /* scale of the narrow-level task threshold in use          */
 } hz_stats;
 
 /* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */

@@ -71,6 +71,7 @@ struct hz_ctx {
   hz_small::EigSolver eig;
   bool graphs = true;
   int spmv_lanes = 0;                      // autotuned at the first hz_factor (0: not yet)
+  bool sweeps_tuned = false;               // sweep task shapes chosen (tune_sweeps)
   int* brk = nullptr;
   hz::DevStatus* status = nullptr;
   double* h_pin = nullptr;                 // pinned: est, invh, invbeta, beta, brk, norm
@@ -193,7 +194,18 @@ struct SweepPlan {
   int32_t tc_kstages = 0, max_k = 0;
 };
 
-SweepPlan plan_sweeps(const hz::SymbolicSet& S, int precision, int bwd_rows, int sweep_tasks) {
+// The assembly-tree view the sweep schedule needs (host arrays).
+struct TreeView {
+  int nlev;
+  const int32_t *lev_ptr, *lev_sn, *sn_k, *sn_m;
+};
+TreeView view_of(const hz::SymbolicSet& S) {
+  return TreeView{S.nlev, S.lev_ptr.data(), S.lev_sn.data(), S.sn_k.data(), S.sn_m.data()};
+}
+
+// sparse_scale multiplies the task count below which a level gets narrow tasks (the
+// sweep autotuner's knob; 1 = the defaults above).
+SweepPlan plan_sweeps(const TreeView& S, int precision, int bwd_rows, int sweep_tasks, double sparse_scale = 1.0) {
   SweepPlan sp;
   const int nlev = S.nlev;
   const int wide = precision == 0 ? 64 : 256;
@@ -206,7 +218,7 @@ SweepPlan plan_sweeps(const hz::SymbolicSet& S, int precision, int bwd_rows, int
       nf += (S.sn_m[s] + wide - 1) / wide;
       nbk += int64_t((S.sn_k[s] + 31) / 32) * ((S.sn_m[s] + bwd_rows - 1) / bwd_rows);
     }
-    const int64_t sparse = precision == 0 ? 2 * 152 : 8 * 152;
+    const int64_t sparse = int64_t((precision == 0 ? 2 * 152 : 8 * 152) * sparse_scale);
     const bool narrow_f = sweep_tasks == 2 || (sweep_tasks == 0 && nf < sparse);
     const bool narrow_b = sweep_tasks == 2 || (sweep_tasks == 0 && nbk < sparse);
     if (narrow_f) sp.fwd_rt[l] = precision == 0 ? 16 : 64;
@@ -229,6 +241,142 @@ SweepPlan plan_sweeps(const hz::SymbolicSet& S, int precision, int bwd_rows, int
     }
   }
   return sp;
+}
+
+// (Re)builds the triangular-sweep task lists of F from its kept tree for the schedule sp:
+// forward (supernode, row block) tasks, backward (supernode, column block, row chunk,
+// finish record) tasks and their finish records, per-level offsets and shapes, the
+// partial-sum buffer, and the variant counts.  Replaces any previous lists.
+hz_status build_sweep_tasks(hz_ctx* c, hz::FactorDev& F, const SweepPlan& sp) {
+  const int nlev = int(F.t_lev_ptr.size()) - 1;
+  const int32_t *lev_ptr = F.t_lev_ptr.data(), *lev_sn = F.t_lev_sn.data();
+  const int32_t *sn_k = F.t_sn_k.data(), *sn_m = F.t_sn_m.data();
+  std::vector<int2> fwd;
+  std::vector<int4> bwd, bfin;
+  std::vector<int64_t> fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1);
+  int64_t max_bwd_level = 0;
+  for (int l = 0; l < nlev; l++) {
+    fwd_ptr[l] = int64_t(fwd.size());
+    bwd_ptr[l] = int64_t(bwd.size());
+    bfin_ptr[l] = int64_t(bfin.size());
+    for (int32_t q = lev_ptr[l]; q < lev_ptr[l + 1]; q++) {
+      const int s = lev_sn[q];
+      const int k = sn_k[s], m = sn_m[s];
+      const int frows = sp.fwd_rt[l];                  // forward task rows (k_fwd / k_fwd_c64)
+      for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
+      const int nch = (m + sp.bwd_rows[l] - 1) / sp.bwd_rows[l];
+      for (int cb = 0; cb * 32 < k; cb++) {
+        const int fin = int(bfin.size());          // global index: its counter and its record
+        bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
+        for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, fin));
+      }
+    }
+    max_bwd_level = std::max(max_bwd_level, int64_t(bwd.size()) - bwd_ptr[l]);
+  }
+  fwd_ptr[nlev] = int64_t(fwd.size());
+  bwd_ptr[nlev] = int64_t(bwd.size());
+  bfin_ptr[nlev] = int64_t(bfin.size());
+  if (const char* vb = std::getenv("HZ_VERBOSE"); vb && std::atoi(vb) >= 2) {
+    // per tree level: supernodes, panel entries and sweep tasks (for reading launch lists)
+    for (int l = 0; l < nlev; l++) {
+      int64_t pe = 0;
+      for (int32_t q = lev_ptr[l]; q < lev_ptr[l + 1]; q++) {
+        const int s = lev_sn[q];
+        pe += int64_t(sn_k[s]) * (2 * sn_m[s] - sn_k[s] + 1) / 2;
+      }
+      std::fprintf(stderr, "[hz] level %3d: %6d supernodes %12lld panel entries %6lld fwd %6lld bwd tasks\n", l,
+                   lev_ptr[l + 1] - lev_ptr[l], (long long)pe, (long long)(fwd_ptr[l + 1] - fwd_ptr[l]),
+                   (long long)(bwd_ptr[l + 1] - bwd_ptr[l]));
+    }
+  }
+  dfree(c, F.fwd_tasks);
+  dfree(c, F.bwd_tasks);
+  dfree(c, F.bfin_tasks);
+  dfree(c, F.bwd_counters);
+  dfree(c, F.bwd_partial);
+  F.fwd_tasks = nullptr;
+  F.bwd_tasks = nullptr;
+  F.bfin_tasks = nullptr;
+  F.bwd_counters = nullptr;
+  F.bwd_partial = nullptr;
+  TRY(upload(c, &F.fwd_tasks, fwd));
+  TRY(upload(c, &F.bwd_tasks, bwd));
+  TRY(upload(c, &F.bfin_tasks, bfin));
+  TRY(upload(c, &F.bwd_counters, std::vector<unsigned int>(std::max<size_t>(bfin.size(), 1), 0u)));
+  void* bp = nullptr;
+  TRY(dalloc(c, (char**)&bp, std::max<int64_t>(max_bwd_level, 1) * 32 * int64_t(F.precision == 0 ? 16 : 8)));
+  F.bwd_partial = bp;
+  auto hcopy = [](const std::vector<int64_t>& v) {
+    int64_t* p = new int64_t[v.size()];
+    std::copy(v.begin(), v.end(), p);
+    return p;
+  };
+  delete[] F.h_fwd_ptr;
+  delete[] F.h_bwd_ptr;
+  delete[] F.h_bfin_ptr;
+  delete[] F.h_fwd_rt;
+  delete[] F.h_bwd_rows;
+  F.h_fwd_ptr = hcopy(fwd_ptr);
+  F.h_bwd_ptr = hcopy(bwd_ptr);
+  F.h_bfin_ptr = hcopy(bfin_ptr);
+  F.h_fwd_rt = new int[nlev];
+  F.h_bwd_rows = new int[nlev];
+  std::copy(sp.fwd_rt.begin(), sp.fwd_rt.end(), F.h_fwd_rt);
+  std::copy(sp.bwd_rows.begin(), sp.bwd_rows.end(), F.h_bwd_rows);
+  F.v_fwd_wide = sp.fwd_wide;
+  F.v_fwd_narrow = sp.fwd_narrow;
+  F.v_bwd_wide = sp.bwd_wide;
+  F.v_bwd_narrow = sp.bwd_narrow;
+  F.v_bwd_split = sp.bwd_split;
+  return HZ_OK;
+}
+
+// Sweep autotuner (hz_options.tune_sweeps): times the triangular sweeps of a factor
+// (A_i^{-1} on every subdomain, or the coarse E^{-1}; forward and backward) under the
+// schedules that scale the task count below which a level gets narrow tasks by 1/4, 1/2,
+// 1 and 2 and cut wide backward
+// chunks of 256 or 512 rows (complex64; 128 or 256 for complex128): one warm-up and three
+// timed runs each, CUDA events on the context stream; the fastest is kept.  It runs at
+// the first hz_factor, on the factor just computed and before any iteration graph holds
+// the task lists.
+hz_status tune_sweeps(hz_ctx* c, hz::FactorDev& F) {
+  if (F.nsn == 0) return HZ_OK;
+  const TreeView T{int(F.t_lev_ptr.size()) - 1, F.t_lev_ptr.data(), F.t_lev_sn.data(), F.t_sn_k.data(),
+                   F.t_sn_m.data()};
+  const int prec = F.precision;
+  const int chunks[2] = {prec == 1 ? 256 : 128, prec == 1 ? 512 : 256};
+  const double scales[4] = {0.25, 0.5, 1.0, 2.0};
+  CU(cudaMemsetAsync(F.t_loc, 0, size_t(F.ntot) * (prec == 0 ? 16 : 8), c->st));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_chunk = chunks[1];
+  double best_scale = 1.0;
+  static const bool verbose = std::getenv("HZ_VERBOSE") != nullptr;
+  for (int ch : chunks)
+    for (double sc : scales) {
+      TRY(build_sweep_tasks(c, F, plan_sweeps(T, prec, ch, 0, sc)));
+      hz::launch_solve(F, c->st);
+      CU(cudaEventRecord(e0, c->st));
+      for (int r = 0; r < 3; r++) hz::launch_solve(F, c->st);
+      CU(cudaEventRecord(e1, c->st));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (verbose) std::fprintf(stderr, "[hz] sweep tuning: chunk %3d scale %.2f: %.3f ms\n", ch, sc, ms / 3);
+      if (ms < best) {
+        best = ms;
+        best_chunk = ch;
+        best_scale = sc;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TRY(build_sweep_tasks(c, F, plan_sweeps(T, prec, best_chunk, 0, best_scale)));
+  F.sweep_chunk = best_chunk;
+  F.sweep_scale = best_scale;
+  return HZ_OK;
 }
 
 // sweep_tasks / bwd_chunk: hz_options fields of the same names (task shapes per level).
@@ -327,9 +475,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   }
   // task lists
   const int nlev = S.nlev;
-  std::vector<int2> fwd, wg, ea;
-  std::vector<int4> bwd, bfin;
-  int64_t max_bwd_level = 0;
+  std::vector<int2> wg, ea;
   std::vector<int4> cbt, tct;
   std::vector<int64_t> scr_off(ns, 0);
   std::vector<std::vector<int32_t>> children(ns);
@@ -338,8 +484,8 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   int max_slot = 1;
   for (int s = 0; s < ns; s++) max_slot = std::max(max_slot, int(children[s].size()));
   F.max_slot = max_slot;
-  std::vector<int64_t> lev_ptr(nlev + 1), fwd_ptr(nlev + 1), bwd_ptr(nlev + 1), bfin_ptr(nlev + 1), wg_ptr(nlev + 1),
-      cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1), tc_ptr(nlev + 1);
+  std::vector<int64_t> lev_ptr(nlev + 1), wg_ptr(nlev + 1), cb_ptr(nlev + 1), ea_ptr(int64_t(nlev) * max_slot + 1),
+      tc_ptr(nlev + 1);
   int64_t scratch = 0;
   // factorisation groups: per level (and extend-add slot) the start of each group's
   // tasks; every list is ordered by supernode within a level, hence by group
@@ -355,9 +501,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     void enter(int g, int64_t size) { while (next <= g) out[base + next++] = size; }
     void finish(int64_t size) { while (next <= G) out[base + next++] = size; }
   };
-  const SweepPlan sp = plan_sweeps(S, precision, bwd_rows, sweep_tasks);
-  const std::vector<int>& fwd_rt = sp.fwd_rt;
-  const std::vector<int>& lev_bwd_rows = sp.bwd_rows;
+  const SweepPlan sp = plan_sweeps(view_of(S), precision, bwd_rows, sweep_tasks);
   F.v_fwd_wide = sp.fwd_wide;
   F.v_fwd_narrow = sp.fwd_narrow;
   F.v_bwd_wide = sp.bwd_wide;
@@ -369,9 +513,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.v_max_k = sp.max_k;
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
-    fwd_ptr[l] = int64_t(fwd.size());
-    bwd_ptr[l] = int64_t(bwd.size());
-    bfin_ptr[l] = int64_t(bfin.size());
     wg_ptr[l] = int64_t(wg.size());
     cb_ptr[l] = int64_t(cbt.size());
     tc_ptr[l] = int64_t(tct.size());
@@ -391,14 +532,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
         sc.enter(gs, int64_t(cbt.size()));
         st.enter(gs, int64_t(tct.size()));
       }
-      const int frows = fwd_rt[l];                     // forward task rows (k_fwd / k_fwd_c64)
-      for (int rb = 0; rb * frows < m; rb++) fwd.push_back(make_int2(s, rb));
-      const int nch = (m + lev_bwd_rows[l] - 1) / lev_bwd_rows[l];
-      for (int cb = 0; cb * 32 < k; cb++) {
-        const int fin = int(bfin.size());          // global index: its counter and its record
-        bfin.push_back(make_int4(s, cb, int(int64_t(bwd.size()) - bwd_ptr[l]), nch));
-        for (int ch = 0; ch < nch; ch++) bwd.push_back(make_int4(s, cb, ch, fin));
-      }
       for (int rb = 0; rb * 32 < r; rb++) wg.push_back(make_int2(s, rb));
       if (precision == 0) {
         const int T = (r + 31) / 32;
@@ -417,7 +550,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     sw.finish(int64_t(wg.size()));
     sc.finish(int64_t(cbt.size()));
     st.finish(int64_t(tct.size()));
-    max_bwd_level = std::max(max_bwd_level, int64_t(bwd.size()) - bwd_ptr[l]);
     for (int q = 0; q < max_slot; q++) {
       ea_ptr[int64_t(l) * max_slot + q] = int64_t(ea.size());
       Split se{ea_g, (size_t(l) * max_slot + q) * (G + 1), G, 0};
@@ -434,32 +566,11 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     }
   }
   lev_ptr[nlev] = S.lev_ptr[nlev];
-  if (const char* vb = std::getenv("HZ_VERBOSE"); vb && std::atoi(vb) >= 2) {
-    // per tree level: supernodes, panel entries and sweep tasks (for reading launch lists)
-    for (int l = 0; l < nlev; l++) {
-      int64_t pe = 0;
-      for (int32_t q = S.lev_ptr[l]; q < S.lev_ptr[l + 1]; q++) {
-        const int s = S.lev_sn[q];
-        pe += int64_t(S.sn_k[s]) * (2 * S.sn_m[s] - S.sn_k[s] + 1) / 2;
-      }
-      std::fprintf(stderr, "[hz] level %3d: %6d supernodes %12lld panel entries %6lld fwd %6lld bwd tasks\n", l,
-                   S.lev_ptr[l + 1] - S.lev_ptr[l], (long long)pe,
-                   (long long)((l + 1 < nlev ? fwd_ptr[l + 1] : int64_t(fwd.size())) - fwd_ptr[l]),
-                   (long long)((l + 1 < nlev ? bwd_ptr[l + 1] : int64_t(bwd.size())) - bwd_ptr[l]));
-    }
-  }
-  fwd_ptr[nlev] = int64_t(fwd.size());
-  bwd_ptr[nlev] = int64_t(bwd.size());
-  bfin_ptr[nlev] = int64_t(bfin.size());
   wg_ptr[nlev] = int64_t(wg.size());
   cb_ptr[nlev] = int64_t(cbt.size());
   tc_ptr[nlev] = int64_t(tct.size());
   ea_ptr[int64_t(nlev) * max_slot] = int64_t(ea.size());
   F.scratch_elems = scratch;
-  TRY(upload(c, &F.fwd_tasks, fwd));
-  TRY(upload(c, &F.bwd_tasks, bwd));
-  TRY(upload(c, &F.bfin_tasks, bfin));
-  TRY(upload(c, &F.bwd_counters, std::vector<unsigned int>(std::max<size_t>(bfin.size(), 1), 0u)));
   TRY(upload(c, &F.wg_tasks, wg));
   TRY(upload(c, &F.cb_tasks, cbt));
   TRY(upload(c, &F.tc_tasks, tct));
@@ -472,9 +583,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     return p;
   };
   F.h_lev_ptr = hcopy(lev_ptr);
-  F.h_fwd_ptr = hcopy(fwd_ptr);
-  F.h_bwd_ptr = hcopy(bwd_ptr);
-  F.h_bfin_ptr = hcopy(bfin_ptr);
   F.h_wg_ptr = hcopy(wg_ptr);
   F.h_cb_ptr = hcopy(cb_ptr);
   F.h_tc_ptr = hcopy(tc_ptr);
@@ -494,10 +602,14 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     }
     return v;
   }());
-  F.h_fwd_rt = new int[nlev];
-  F.h_bwd_rows = new int[nlev];
-  std::copy(fwd_rt.begin(), fwd_rt.end(), F.h_fwd_rt);
-  std::copy(lev_bwd_rows.begin(), lev_bwd_rows.end(), F.h_bwd_rows);
+  // the tree as the sweep schedule sees it, kept for the sweep autotuner
+  F.t_lev_ptr = S.lev_ptr;
+  F.t_lev_sn = S.lev_sn;
+  F.t_sn_k = S.sn_k;
+  F.t_sn_m = S.sn_m;
+  TRY(build_sweep_tasks(c, F, sp));
+  F.sweep_chunk = bwd_rows;
+  F.sweep_scale = 1.0;
   // batched sweeps for nrhs_block right-hand sides (pseudo-block FGMRES)
   if (nrhs_block > 1) {
     F.mS = nrhs_block;
@@ -552,9 +664,6 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   TRY(dalloc(c, (char**)&zl, F.ntot * int64_t(vs)));
   TRY(dalloc(c, (char**)&xl, F.ntot * int64_t(vs)));
   TRY(dalloc(c, (char**)&uw, std::max<int64_t>(F.u_elems, 1) * int64_t(vs)));
-  void* bp = nullptr;
-  TRY(dalloc(c, (char**)&bp, std::max<int64_t>(max_bwd_level, 1) * 32 * int64_t(vs)));
-  F.bwd_partial = bp;
   F.panels = pan;
   F.t_loc = tl;
   F.z_loc = zl;
@@ -1923,7 +2032,7 @@ extern "C" hz_status hz_plan(const hz_mesh_desc* md, const hz_options* op, hz_st
   {
     const int prec = op->precision == HZ_MIXED ? 1 : 0;
     const int rows = op->bwd_chunk > 0 ? op->bwd_chunk : (prec == 1 ? 512 : 256);
-    const SweepPlan sp = plan_sweeps(P.local, prec, rows, op->sweep_tasks);
+    const SweepPlan sp = plan_sweeps(view_of(P.local), prec, rows, op->sweep_tasks);
     hz_stats& st = tmp.stats;
     st.fwd_levels_wide = sp.fwd_wide;
     st.fwd_levels_narrow = sp.fwd_narrow;
@@ -2177,13 +2286,27 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
   hz::set_spmv_lanes(c->spmv_lanes);
   double minp = 1e300;
   TRY(factor_one(c, c->loc, w, c->loc_max, minp));
+  const bool tune = c->opt.tune_sweeps && !c->sweeps_tuned && c->opt.sweep_tasks == 0 && c->opt.bwd_chunk == 0;
+  if (tune) {
+    TRY(tune_sweeps(c, c->loc));
+    hz_stats& st = c->stats;
+    st.fwd_levels_wide = c->loc.v_fwd_wide;
+    st.fwd_levels_narrow = c->loc.v_fwd_narrow;
+    st.bwd_levels_wide = c->loc.v_bwd_wide;
+    st.bwd_levels_narrow = c->loc.v_bwd_narrow;
+    st.bwd_split_blocks = c->loc.v_bwd_split;
+  }
+  c->stats.sweep_chunk = c->loc.sweep_chunk;
+  c->stats.sweep_scale = c->loc.sweep_scale;
   if (c->levels == 2 && c->coarse_oras) {
     hz::launch_fill_values(c->nnzH, c->d_EK, c->d_EM, c->d_EB, w, c->d_E, c->st);
     TRY(factor_one(c, c->cloc, w, c->cloc_max, minp));
     c->stats.coarse_solves = c->stats.coarse_iterations = 0;
   } else if (c->levels == 2) {
     TRY(factor_one(c, c->crs, w, c->crs_max, minp));
+    if (tune) TRY(tune_sweeps(c, c->crs));
   }
+  if (tune) c->sweeps_tuned = true;
   CU(cudaStreamSynchronize(c->st));
   c->stats.min_pivot = minp;
   c->rdim = 0;                              // a recycled space belongs to one operator

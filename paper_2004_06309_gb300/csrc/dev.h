@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace hz {
 
 // One supernode of a batched multifrontal factorisation (56 bytes).
@@ -73,6 +75,11 @@ struct FactorDev {
   int64_t v_bwd_split = 0, v_tc_tiles = 0, v_tc_multi = 0;
   int32_t v_tc_kstages = 0, v_max_k = 0;
   int32_t tc_wait = 1 << 22;          // polls of the first wait on a tensor-core completion barrier
+  // the assembly tree on the host (levels, supernode widths and heights), from which the
+  // sweep task lists can be rebuilt (sweep autotuner)
+  std::vector<int32_t> t_lev_ptr, t_lev_sn, t_sn_k, t_sn_m;
+  int32_t sweep_chunk = 0;            // rows of a wide backward chunk in use
+  double sweep_scale = 1.0;           // scale of the narrow-level task threshold in use
   int64_t scratch_elems = 0;          // max over levels of sum (m-k) k
   // algorithmic cost of one forward+backward sweep (host-side)
   double solve_bytes = 0, solve_flops = 0;

@@ -53,7 +53,7 @@ class Options(C.Structure):
         ("block_size", C.c_int32), ("spmv_lanes", C.c_int32), ("coarse_solver", C.c_int32),
         ("coarse_maxit", C.c_int32), ("coarse_tol", C.c_double), ("recycle", C.c_int32),
         ("sweep_tasks", C.c_int32), ("bwd_chunk", C.c_int32), ("tc_wait_limit", C.c_int32),
-        ("factor_group", C.c_int32), ("krylov", C.c_int32),
+        ("factor_group", C.c_int32), ("krylov", C.c_int32), ("tune_sweeps", C.c_int32),
     ]
 
 
@@ -73,6 +73,7 @@ class Stats(C.Structure):
         ("fwd_levels_wide", C.c_int32), ("fwd_levels_narrow", C.c_int32), ("bwd_levels_wide", C.c_int32),
         ("bwd_levels_narrow", C.c_int32), ("bwd_split_blocks", C.c_int64), ("tc_tiles", C.c_int64),
         ("tc_multi_fronts", C.c_int64), ("tc_max_kstages", C.c_int32), ("max_snode_width", C.c_int32),
+        ("sweep_chunk", C.c_int32), ("sweep_scale", C.c_double),
     ]
 
     def as_dict(self):
@@ -217,7 +218,7 @@ class _MeshArrays:
 def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=2000, leaf_size=0,
                  max_snode=0, hbm_budget=0, elem_part=None, stream=0, block_size=0, spmv_lanes=0,
                  coarse_solver=0, coarse_maxit=0, coarse_tol=0.0, recycle=0, sweep_tasks=0, bwd_chunk=0,
-                 tc_wait_limit=0, factor_group=0, krylov=0):
+                 tc_wait_limit=0, factor_group=0, krylov=0, tune_sweeps=0):
     o = Options()
     o.nsub, o.overlap, o.levels, o.restart = int(nsub), int(overlap), int(levels), int(restart)
     o.precision, o.max_iter = int(precision), int(max_iter)
@@ -233,6 +234,7 @@ def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=200
     o.sweep_tasks, o.bwd_chunk, o.tc_wait_limit = int(sweep_tasks), int(bwd_chunk), int(tc_wait_limit)
     o.factor_group = int(factor_group)
     o.krylov = int(krylov)
+    o.tune_sweeps = int(tune_sweeps)
     return o, part
 
 

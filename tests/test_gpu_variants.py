@@ -172,3 +172,26 @@ def test_grouped_factorisation_is_bitwise_identical(hzmod, case, prec):
             G.close()
     assert out[1][0] < out[0][0]                       # a smaller workspace
     assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sweep_autotuner_keeps_parity(hzmod, case, prec):
+    """tune_sweeps times six task-shape schedules of the local sweeps at the first hz_factor
+    and keeps the fastest; whichever it keeps, M^{-1} v still matches the oracle, and solves
+    (whose iterations are then captured as graphs on the tuned task lists) converge."""
+    import torch
+    p, S, kappa, v, ref = case
+    G = hzmod.Solver(p, precision=hzmod.HZ_MIXED if prec == "mixed" else hzmod.HZ_FP64, tune_sweeps=1)
+    try:
+        G.factor()
+        st = G.stats()
+        z = G.apply_M(torch.from_numpy(v).cuda()).cpu().numpy()
+        b = S.rhs()[:, 0]
+        x, info = G.solve(b)
+    finally:
+        G.close()
+    assert st["sweep_chunk"] in ((256, 512) if prec == "mixed" else (128, 256))
+    assert st["sweep_scale"] in (0.5, 1.0, 2.0)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= (1e-10 if prec == "fp64" else kappa * U32), err
+    assert info[0][1] == 0 and np.linalg.norm(b - S.A @ x) / np.linalg.norm(b) <= p.tol
