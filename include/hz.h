@@ -310,6 +310,15 @@ hz_status hz_cgs2(hz_ctx* ctx, const void* V, int64_t ldv, int32_t ncols, void* 
 hz_status hz_cgs2_noalloc(const void* V, int64_t n, int64_t ldv, int32_t ncols, void* w, void* h,
                           void* wnorm, uintptr_t stream);
 
+/* Host utility of the GCRO-DR cycle end (exported so that callers and tests can check
+   it; it has no counterpart in the paper): eigenvalues w and right eigenvectors V (unit
+   columns) of a general complex n x n matrix A.  A, V: complex128 n x n column-major,
+   w: complex128 n; host pointers, caller-owned.  Householder reduction to Hessenberg
+   form, the shifted QR algorithm to the complex Schur form, back substitution for the
+   eigenvectors.  HZ_ERR_ARG for n outside [1, 1024] or null pointers; HZ_ERR_BREAKDOWN
+   for a non-finite input or if the iteration does not converge. */
+hz_status hz_dense_eig(int32_t n, const double* A, double* w, double* V);
+
 /* Time each phase of one inner iteration (reps runs each, after one warm-up run)
    with CUDA events on the context's stream, on the current factors; fills
    algorithmic bytes and flops per run.  Overwrites the Krylov workspace.

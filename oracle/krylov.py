@@ -374,6 +374,19 @@ def gcrodr(apply_A, apply_M, b, tol=1e-6, m=50, k=10, recycle=None, maxit=1000, 
             return x, its, rel, rel <= tol, (Ux, Uh, C)
 
 
+def rebase_recycle(apply_A, recycle):
+    """Carry a recycled space (Ux, Uh, C) over to a new operator (Parks et al. 2006, for a
+    sequence of matrices): C' = A_new Ux is orthonormalised column by column (CGS2),
+    C' = Q R, and the space becomes (Ux R^{-1}, Uh R^{-1}, Q), so that C = A_new Ux and
+    C^H C = I hold again.  Uh keeps the old preconditioned side; it only steers the choice
+    of the next recycled space."""
+    Ux, Uh, C = recycle
+    AU = np.column_stack([apply_A(Ux[:, i]) for i in range(Ux.shape[1])])
+    Q, R, _ = _block_orthonormalise(AU, np.linalg.norm(AU, axis=0))
+    Rinv = np.linalg.inv(R)
+    return Ux @ Rinv, Uh @ Rinv, Q
+
+
 def _first_recycle(V, Zs, H, kc, k):
     """Recycled space from a plain GMRES cycle: harmonic Ritz vectors of H_m."""
     Hm = H[:kc, :kc]

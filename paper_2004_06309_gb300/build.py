@@ -65,7 +65,7 @@ def build(force=False, verbose=False):
             if verbose and out:
                 print(out)
     tmp = LIB + ".tmp"
-    run([_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lpthread", "-lcusolver"])
+    run([_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

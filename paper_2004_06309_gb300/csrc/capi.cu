@@ -68,7 +68,6 @@ struct hz_ctx {
   int rk = 0, rdim = 0, ckk = 0;
   double2 *Vx = nullptr, *Ux = nullptr, *Uh = nullptr, *Ctmp = nullptr, *Uxt = nullptr, *Uht = nullptr;
   double2 *Hraw = nullptr, *Braw = nullptr, *dcoef = nullptr;
-  hz_small::EigSolver eig;
   bool graphs = true;
   int spmv_lanes = 0;                      // autotuned at the first hz_factor (0: not yet)
   bool sweeps_tuned = false;               // sweep task shapes chosen (tune_sweeps)
@@ -1076,7 +1075,7 @@ hz_status recycle_update(hz_ctx* c, int kk, int kc) {
     Mg = Ag;
     if (!hz_small::lu_solve(nt, Bg, Mg, nt)) return HZ_OK;
   }
-  if (!hz_small::eig(c->eig, st, nt, Mg, w, VR, err)) {
+  if (!hz_small::eig(nt, Mg, w, VR, err)) {
     c->err = err;
     return HZ_OK;
   }
@@ -2569,6 +2568,23 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
   out->flops[HZ_PH_PRECOND] = pf;
   out->bytes[HZ_PH_ITERATION] = pb + out->bytes[HZ_PH_SPMV] + out->bytes[HZ_PH_CGS2] + 2 * dn * nt;
   out->flops[HZ_PH_ITERATION] = pf + out->flops[HZ_PH_SPMV] + out->flops[HZ_PH_CGS2];
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_dense_eig(int32_t n, const double* A, double* w, double* V) {
+  if (n < 1 || n > 1024 || !A || !w || !V) return HZ_ERR_ARG;
+  std::vector<cplx> M(size_t(n) * n), ev, vec;
+  for (size_t q = 0; q < M.size(); q++) M[q] = cplx(A[2 * q], A[2 * q + 1]);
+  std::string err;
+  if (!hz_small::eig(n, M, ev, vec, err)) return HZ_ERR_BREAKDOWN;
+  for (int i = 0; i < n; i++) {
+    w[2 * i] = ev[size_t(i)].real();
+    w[2 * i + 1] = ev[size_t(i)].imag();
+  }
+  for (size_t q = 0; q < vec.size(); q++) {
+    V[2 * q] = vec[q].real();
+    V[2 * q + 1] = vec[q].imag();
+  }
   return HZ_OK;
 }
 

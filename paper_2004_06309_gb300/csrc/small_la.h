@@ -2,9 +2,6 @@
 // order <= restart + 1, column-major std::complex<double>).
 #pragma once
 
-#include <cuda_runtime.h>
-#include <cusolverDn.h>
-
 #include <complex>
 #include <string>
 #include <vector>
@@ -23,19 +20,13 @@ void qr_thin(int rows, int cols, const std::vector<cplx>& A, std::vector<cplx>& 
 // R <- R^{-1} for an upper-triangular k x k R; false on a zero diagonal entry.
 bool tri_inv_upper(int k, std::vector<cplx>& R);
 
-// Eigenvalues w and right eigenvectors VR (columns) of a general n x n matrix, by
-// cuSOLVER on `st`; device buffers are kept in the solver between calls.
-struct EigSolver {
-  cusolverDnHandle_t handle = nullptr;
-  cusolverDnParams_t params = nullptr;
-  void *dA = nullptr, *dW = nullptr, *dVR = nullptr, *dwork = nullptr;
-  int* dinfo = nullptr;
-  size_t dbytes = 0;
-  std::vector<char> hwork;
-  int cap = 0;
-  ~EigSolver();
-};
-bool eig(EigSolver& E, cudaStream_t st, int n, const std::vector<cplx>& A, std::vector<cplx>& w,
-         std::vector<cplx>& VR, std::string& err);
+// Eigenvalues w and right eigenvectors V (unit columns) of a general complex n x n
+// matrix A, on the host: Householder reduction to upper Hessenberg form, the shifted QR
+// algorithm (Wilkinson shifts, bulge chased by Givens rotations, deflation of negligible
+// subdiagonal entries, an exceptional shift every 11 steps without deflation) to the
+// complex Schur form A = Q T Q^H, then the eigenvectors of T by back substitution and
+// V = Q X (Golub and Van Loan, Matrix Computations, chapter 7).  False (with err) on a
+// non-finite input or if the iteration does not converge within 60 n steps.
+bool eig(int n, const std::vector<cplx>& A, std::vector<cplx>& w, std::vector<cplx>& V, std::string& err);
 
 }  // namespace hz_small

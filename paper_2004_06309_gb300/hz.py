@@ -130,6 +130,7 @@ SIGNATURES = {
                           C.POINTER(C.c_double)]),
     "hz_cgs2_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    "hz_dense_eig": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hz_ndofs": (C.c_int64, [C.c_void_p]),
     "hz_status_string": (C.c_char_p, [C.c_int]),
     "hz_last_error": (C.c_char_p, [C.c_void_p]),
@@ -366,6 +367,18 @@ class Solver:
         z = self.torch.empty_like(v)
         self._check(lib().hz_apply_M(self.h, C.c_void_p(v.data_ptr()), C.c_void_p(z.data_ptr())), "hz_apply_M")
         return z
+
+
+def dense_eig(A):
+    """Eigenvalues and unit right eigenvectors of a complex square matrix (hz_dense_eig)."""
+    A = np.asfortranarray(np.asarray(A, np.complex128))
+    n = A.shape[0]
+    w = np.zeros(n, np.complex128)
+    V = np.zeros((n, n), np.complex128, order="F")
+    s = lib().hz_dense_eig(n, _ptr(A), _ptr(w), _ptr(V))
+    if s != HZ_OK:
+        raise HzError(s, "hz_dense_eig failed")
+    return w, V
 
 
 def select_evictions(bytes_, last_use, evictable, resident, need, budget):

@@ -115,3 +115,36 @@ def test_factor_groups_shrink_the_frontal_workspace(hzmod):
         assert a[key] == b[key], key
     with pytest.raises(hzmod.HzError):
         hzmod.plan(p, factor_group=-1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 33, 66])
+def test_dense_eig_against_known_spectra(hzmod, n):
+    """The host eigen-solver of the GCRO-DR cycle end (Hessenberg reduction, shifted QR,
+    back substitution): eigenpairs satisfy A v = w v to rounding and match numpy's
+    eigenvalues; a matrix built as Q T Q^H returns the diagonal of T."""
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    w, V = hzmod.dense_eig(A)
+    assert np.linalg.norm(A @ V - V * w) <= 1e-13 * np.linalg.norm(A) * max(1, n)
+    assert np.allclose(np.linalg.norm(V, axis=0), 1.0)
+    ref = np.linalg.eigvals(A)
+    assert max(np.min(np.abs(x - ref)) for x in w) <= 1e-11 * np.abs(ref).max()
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    lam = np.arange(1, n + 1) * (1 + 0.5j)
+    T = np.triu(rng.standard_normal((n, n)), 1) + np.diag(lam)
+    w2, V2 = hzmod.dense_eig(Q @ T @ Q.conj().T)
+    assert np.allclose(np.sort_complex(w2), np.sort_complex(lam), atol=1e-10 * n)
+
+
+def test_dense_eig_real_pairs_diagonal_and_bad_input(hzmod):
+    rng = np.random.default_rng(4)
+    R = rng.standard_normal((20, 20))                 # real: conjugate eigenvalue pairs
+    w, V = hzmod.dense_eig(R)
+    assert np.linalg.norm(R @ V - V * w) <= 1e-13 * np.linalg.norm(R) * 20
+    D = np.diag(np.arange(1.0, 7.0))                  # already triangular: deflates at once
+    w, V = hzmod.dense_eig(D)
+    assert np.allclose(np.sort(w.real), np.arange(1.0, 7.0)) and np.allclose(w.imag, 0)
+    bad = np.full((3, 3), np.nan + 0j)
+    with pytest.raises(hzmod.HzError) as e:
+        hzmod.dense_eig(bad)
+    assert e.value.status == hzmod.HZ_ERR_BREAKDOWN

@@ -1,8 +1,8 @@
 """GPU parity of GCRO-DR (options.recycle = k) against the oracle's gcrodr, through the
 C ABI, on a sequence of right-hand sides that share the recycled space.
 
-The recycled space is chosen from harmonic Ritz vectors (cuSOLVER on the device side,
-LAPACK through scipy in the oracle); both pick the same eigenvectors unless two
+The recycled space is chosen from harmonic Ritz vectors (the library's host shifted-QR
+eigen-solver, LAPACK through scipy in the oracle); both pick the same eigenvectors unless two
 harmonic Ritz values tie in modulus to rounding, so iteration counts are compared to
 +-1 and solutions to the solver tolerance, and every solution is checked against the
 tolerance with the oracle's FP64 operator."""
