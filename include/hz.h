@@ -123,8 +123,9 @@ typedef struct {
                                across right-hand sides of hz_solve, renewed from
                                harmonic Ritz vectors at every cycle end; cycles then
                                add restart - k Arnoldi vectors.  hz_factor drops the
-                               space.  0 = off (FGMRES); 1 <= k <= min(16, restart/2);
-                               one right-hand side at a time (block_size <= 1).      */
+                               space unless recycle_keep is set.  0 = off (FGMRES);
+                               1 <= k <= min(16, restart/2); one right-hand side at a
+                               time (block_size <= 1).                               */
   /* Task shapes of the batched triangular sweeps (A_i^{-1} of Eq. 4 and the coarse
      E^{-1} of Eq. 3).  Results differ only by the rounding of the summation order.  */
   int32_t sweep_tasks;      /* 0: chosen per assembly-tree level from its task count
@@ -166,6 +167,11 @@ typedef struct {
                                sweep_tasks == 0 and bwd_chunk == 0.  0: the default
                                schedule.  The choice sets summation orders, so
                                contexts that must agree bitwise leave it off.          */
+  int32_t recycle_keep;     /* with recycle > 0: 1 keeps the recycled space across
+                               hz_factor (recycling across frequencies); the first solve
+                               on the new factors re-bases it: C = A_new Ux is
+                               orthonormalised, C = Q R, and Ux, Uh are scaled by
+                               R^{-1}.  0: hz_factor drops the space.                 */
 } hz_options;
 
 typedef struct {

@@ -71,6 +71,7 @@ struct hz_ctx {
   bool graphs = true;
   int spmv_lanes = 0;                      // autotuned at the first hz_factor (0: not yet)
   bool sweeps_tuned = false;               // sweep task shapes chosen (tune_sweeps)
+  bool recycle_stale = false;              // recycled space kept across hz_factor, not yet re-based
   int* brk = nullptr;
   hz::DevStatus* status = nullptr;
   double* h_pin = nullptr;                 // pinned: est, invh, invbeta, beta, brk, norm
@@ -1116,6 +1117,37 @@ hz_status recycle_update(hz_ctx* c, int kk, int kc) {
 // One right-hand side by GCRO-DR (x0 = 0), with the stopping and counting rules of
 // fgmres_one; the recycled space left by the previous right-hand side is used from the
 // first cycle on.
+hz_status block_orthonormalise(hz_ctx* c, double2* W, int s, double2* Q, std::vector<cplx>& R, const double* w0,
+                               bool& brk);
+
+// Carries the recycled space over to a new operator (options.recycle_keep, after a new
+// hz_factor): C' = A Ux is orthonormalised column by column (CGS2), C' = Q R, and the space
+// becomes (Ux R^{-1}, Uh R^{-1}, Q), so that C = A Ux and C^H C = I hold for the new A
+// (Parks et al. 2006, for a sequence of matrices).  A numerically dependent C' drops the
+// space.
+hz_status recycle_rebase(hz_ctx* c) {
+  const int64_t n = c->n;
+  const int kk = c->rdim;
+  cudaStream_t st = c->st;
+  for (int i = 0; i < kk; i++)
+    hz::launch_spmv(n, c->d_rp, c->d_ci, c->d_A, c->Ux + int64_t(i) * n, nullptr, c->Ctmp + int64_t(i) * n, st);
+  std::vector<double> w0(kk);
+  for (int i = 0; i < kk; i++) TRY(norm2(c, c->Ctmp + int64_t(i) * n, w0[i]));
+  std::vector<cplx> R;
+  bool brk = false;
+  TRY(block_orthonormalise(c, c->Ctmp, kk, c->V - int64_t(kk) * n, R, w0.data(), brk));
+  if (brk || !hz_small::tri_inv_upper(kk, R)) {
+    c->rdim = 0;
+    return HZ_OK;
+  }
+  combo(c, kk, c->Ux, 0, nullptr, R, kk, c->Uxt, 1.0, false);      // Ux R^{-1}
+  combo(c, kk, c->Uh, 0, nullptr, R, kk, c->Uht, 1.0, false);      // Uh R^{-1}
+  std::swap(c->Ux, c->Uxt);
+  std::swap(c->Uh, c->Uht);
+  CU(cudaStreamSynchronize(st));
+  return HZ_OK;
+}
+
 hz_status gcrodr_one(hz_ctx* c, double tol, hz_rhs_info* info) {
   const int64_t n = c->n;
   const int m = c->restart;
@@ -1131,6 +1163,10 @@ hz_status gcrodr_one(hz_ctx* c, double tol, hz_rhs_info* info) {
   if (!std::isfinite(bnorm)) {
     info->status = HZ_ERR_BREAKDOWN;
     return HZ_OK;
+  }
+  if (c->recycle_stale) {                   // the space was built for the previous operator
+    c->recycle_stale = false;
+    if (c->rdim > 0) TRY(recycle_rebase(c));
   }
   c->h_pin[6] = bnorm;
   CU(cudaMemcpyAsync(c->scal + 4, c->h_pin + 6, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -2308,7 +2344,10 @@ extern "C" hz_status hz_factor(hz_ctx* c, double freq_hz) {
   if (tune) c->sweeps_tuned = true;
   CU(cudaStreamSynchronize(c->st));
   c->stats.min_pivot = minp;
-  c->rdim = 0;                              // a recycled space belongs to one operator
+  if (c->opt.recycle_keep && c->rdim > 0)
+    c->recycle_stale = true;                // re-based on the new operator at the next solve
+  else
+    c->rdim = 0;                            // a recycled space belongs to one operator
   c->stats.factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->factored = true;
   return HZ_OK;

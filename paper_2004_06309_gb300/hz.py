@@ -54,6 +54,7 @@ class Options(C.Structure):
         ("coarse_maxit", C.c_int32), ("coarse_tol", C.c_double), ("recycle", C.c_int32),
         ("sweep_tasks", C.c_int32), ("bwd_chunk", C.c_int32), ("tc_wait_limit", C.c_int32),
         ("factor_group", C.c_int32), ("krylov", C.c_int32), ("tune_sweeps", C.c_int32),
+        ("recycle_keep", C.c_int32),
     ]
 
 
@@ -219,7 +220,7 @@ class _MeshArrays:
 def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=2000, leaf_size=0,
                  max_snode=0, hbm_budget=0, elem_part=None, stream=0, block_size=0, spmv_lanes=0,
                  coarse_solver=0, coarse_maxit=0, coarse_tol=0.0, recycle=0, sweep_tasks=0, bwd_chunk=0,
-                 tc_wait_limit=0, factor_group=0, krylov=0, tune_sweeps=0):
+                 tc_wait_limit=0, factor_group=0, krylov=0, tune_sweeps=0, recycle_keep=0):
     o = Options()
     o.nsub, o.overlap, o.levels, o.restart = int(nsub), int(overlap), int(levels), int(restart)
     o.precision, o.max_iter = int(precision), int(max_iter)
@@ -236,6 +237,7 @@ def make_options(nsub, overlap, levels, restart, precision=HZ_FP64, max_iter=200
     o.factor_group = int(factor_group)
     o.krylov = int(krylov)
     o.tune_sweeps = int(tune_sweeps)
+    o.recycle_keep = int(recycle_keep)
     return o, part
 
 
