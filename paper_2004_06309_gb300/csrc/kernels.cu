@@ -312,23 +312,30 @@ __global__ void __launch_bounds__(256) k_cb(const int4* tasks, const SnDev* sn, 
 
 // ---------------------------------------------------------------------------
 // Tensor-core (tcgen05) Schur update of complex64 fronts, one 128 x 128 lower
-// tile of the contribution block per CTA (4 warps):
+// tile of the contribution block per CTA (8 warps):
 //   F22[a][b] -= sum_i W[a][i] d_i^{-1} W[b][i]      (complex, i < k)
-// as two real products over K' = 2k:
-//   Re = [Wr | Wi] [Br | -Bi]^T,  Im = [Wr | Wi] [Bi | Br]^T,   B = W diag(d^{-1}),
+// as two real products over K' = 2k, K' interleaved by complex column (2i: real parts,
+// 2i + 1: imaginary parts):
+//   Re = A B1^T,  Im = A B2^T,  A = (Wr, Wi),  B1 = (Br, -Bi),  B2 = (Bi, Br),  B = W diag(d^{-1}),
 // each in 3xTF32 (hi*hi + hi*lo + lo*hi, hi = TF32 rounding, lo = the remainder),
 // accumulated in FP32 in tensor memory (Re: columns 0-127, Im: 128-255).
 // Operands are staged K-major in shared memory as 8-row x 16-byte core matrices
-// (no swizzle), 32 K-elements per stage.  Every wait on the MMA-completion
-// barrier is bounded.  The per-stage wait polls at most first_wait times; when it
-// runs out the CTA raises status->timeout (bit 0), skips its epilogue and drains
-// the MMAs it issued with a second wait of kTcDrainPolls polls before it frees
-// its tensor memory.  The MMAs read only this CTA's shared memory and write only
-// its tensor memory, so they finish in bounded time and the drain ends; should it
-// run out as well (a faulty tensor pipe), bit 1 is raised and the memory is still
-// freed, because a CTA that exits holding tensor memory would leave later
-// allocations on its SM waiting forever.  Either bit makes hz_factor return
-// HZ_ERR_TIMEOUT and leaves the context unfactored.
+// (no swizzle), kTcCols complex columns (2 kTcCols K' values) per stage, in two stages
+// (96 KB, two CTAs per SM): while one stage's MMAs run the 256 threads fill the other
+// (thread = tile row, half of the stage's columns; every W element is read once per
+// tile; a thread's loads of the next stage are issued together, right after the current
+// stage's MMAs).  One elected thread issues the MMAs
+// and commits each stage to that stage's mbarrier.  Every wait is bounded: a stage
+// buffer is refilled only after the commit of the stage that last used it; the polls of
+// these waits and of the final one are first_wait.  When one runs out the CTA raises
+// status->timeout (bit 0), skips its epilogue and drains the MMAs it issued with a
+// second wait of kTcDrainPolls polls on the last commit before it frees its tensor
+// memory.  The MMAs read only this CTA's shared memory and write only its tensor
+// memory, so they finish in bounded time and the drain ends; should it run out as well
+// (a faulty tensor pipe), bit 1 is raised and the memory is still freed, because a CTA
+// that exits holding tensor memory would leave later allocations on its SM waiting
+// forever.  Either bit makes hz_factor return HZ_ERR_TIMEOUT and leaves the context
+// unfactored.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -337,10 +344,16 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(y);
 }
 // float offset of element (row r, k) in a 128 x 32 K-major tile of core matrices
-__device__ __forceinline__ int tc_off(int r, int kk) { return ((r >> 3) * 8 + (kk >> 2)) * 32 + (r & 7) * 4 + (kk & 3); }
+constexpr int kTcCols = 8;                      // complex columns per stage
+constexpr int kTcK = 2 * kTcCols;               // real K' values per stage
+constexpr int kTcTile = 128 * kTcK;             // floats of one 128-row operand tile
+__device__ __forceinline__ int tc_off(int r, int kk) {
+  return ((r >> 3) * (kTcK / 4) + (kk >> 2)) * 32 + (r & 7) * 4 + (kk & 3);
+}
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  // LBO = 128 B (next core matrix along K), SBO = 1024 B (next 8-row group), version 1, no swizzle
-  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) |
+  // LBO = 128 B (next core matrix along K), SBO = 8 rows x kTcK x 4 B (next 8-row group),
+  // version 1, no swizzle
+  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t((32 * kTcK) >> 4) << 32) |
          (uint64_t(1) << 46);
 }
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
@@ -373,23 +386,21 @@ __device__ __forceinline__ void tc_ld32(uint32_t ta, float* out) {
   for (int j = 0; j < 32; j++) out[j] = __uint_as_float(v[j]);
 }
 
-constexpr int kTcSmemFloats = 6 * 128 * 32;   // Ah, Al, B1h, B1l, B2h, B2l: 96 KB
-__global__ void __launch_bounds__(128) k_cb_tc(const int4* tasks, const SnDev* sn, const int64_t* scr_off,
+// Two stages of 16 complex columns (32 real K values each): Ah, Al, B1h, B1l, B2h, B2l
+// per stage, 96 KB; the MMAs of one stage run while the other is refilled.
+constexpr int kTcStage = 6 * kTcTile;
+constexpr int kTcSmemFloats = 2 * kTcStage;     // 96 KB: two CTAs per SM
+__global__ void __launch_bounds__(256) k_cb_tc(const int4* tasks, const SnDev* sn, const int64_t* scr_off,
                                                float2* fronts, const float2* scratch, DevStatus* status,
                                                int first_wait) {
   extern __shared__ __align__(1024) float tsm[];
-  float* Ah = tsm;
-  float* Al = Ah + 4096;
-  float* B1h = Al + 4096;
-  float* B1l = B1h + 4096;
-  float* B2h = B1l + 4096;
-  float* B2l = B2h + 4096;
   __shared__ float2 dinv[kMaxK];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const int4 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, r = m - k, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & 127, half = tid >> 7;        // staging: tile row, and which 8 of 16 columns
   const int a0 = t.y * 128, b0 = t.z * 128;
   const float2* W = scratch + scr_off[t.x];          // r x k, column-major (ld r)
   float2* F = fronts + S.frontoff;
@@ -399,48 +410,75 @@ __global__ void __launch_bounds__(128) k_cb_tc(const int4* tasks, const SnDev* s
                  :: "r"(smem_addr(&tmem_base)), "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar)), "r"(1));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(&mbar[1])), "r"(1));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int K2 = 2 * k;
+  // K is interleaved by complex column: K' = 2i holds the real parts, 2i + 1 the imaginary
+  // ones, so Re = sum A B1^T, Im = sum A B2^T with A = (Wr, Wi), B1 = (Br, -Bi), B2 = (Bi, Br)
+  const int nst = (k + kTcCols - 1) / kTcCols;
+  constexpr int QH = kTcCols / 2;                   // complex columns per thread per stage
+  const int ra = a0 + row, rb = b0 + row;
+  // a stage's 16 operand values per thread are loaded into registers in one go, the next
+  // stage's right after this stage's MMAs are issued, so the loads overlap the MMAs
+  float2 av[QH], bw[QH];
+  auto load_stage = [&](int st) {
+#pragma unroll
+    for (int q = 0; q < QH; q++) {
+      const int i = kTcCols * st + QH * half + q;
+      av[q] = (i < k && ra < r) ? W[ra + int64_t(i) * r] : make_float2(0.f, 0.f);
+      bw[q] = (i < k && rb < r) ? W[rb + int64_t(i) * r] : make_float2(0.f, 0.f);
+    }
+  };
+  load_stage(0);
   bool ok = true;
-  uint32_t phase = 0;
-  for (int kc = 0; kc < K2 && ok; kc += 32) {
-    // stage: thread = row of the A tile (a0 + tid) and of the B tile (b0 + tid)
-    const int ra = a0 + tid, rb = b0 + tid;
-    for (int q = 0; q < 32; q++) {
-      const int kap = kc + q;
-      float a = 0.f, b1 = 0.f, b2 = 0.f;
-      if (kap < K2) {
-        const int i = kap < k ? kap : kap - k;
-        if (ra < r) {
-          const float2 w = W[ra + int64_t(i) * r];
-          a = kap < k ? w.x : w.y;
-        }
-        if (rb < r) {
-          const float2 bw = cmul(W[rb + int64_t(i) * r], dinv[i]);
-          b1 = kap < k ? bw.x : -bw.y;
-          b2 = kap < k ? bw.y : bw.x;
-        }
-      }
-      const int o = tc_off(tid, q);
-      const float ah = tf32_rna(a), b1h = tf32_rna(b1), b2h = tf32_rna(b2);
-      Ah[o] = ah;
-      Al[o] = tf32_rna(a - ah);
-      B1h[o] = b1h;
-      B1l[o] = tf32_rna(b1 - b1h);
-      B2h[o] = b2h;
-      B2l[o] = tf32_rna(b2 - b2h);
+  int issued = 0;                                    // stages whose MMAs were committed
+  for (int st = 0; st < nst; st++) {
+    const int b = st & 1;
+    if (st >= 2) {                                   // buffer b: stage st - 2's MMAs must be done
+      const bool mine = tc_wait(&mbar[b], uint32_t((st - 2) >> 1) & 1u, first_wait);
+      ok = __syncthreads_and(mine) != 0;             // block-uniform
+      if (!ok) break;
+    }
+    float* Ah = tsm + b * kTcStage;
+    float* Al = Ah + kTcTile;
+    float* B1h = Al + kTcTile;
+    float* B1l = B1h + kTcTile;
+    float* B2h = B1l + kTcTile;
+    float* B2l = B2h + kTcTile;
+#pragma unroll
+    for (int q = 0; q < QH; q++) {
+      const int i = kTcCols * st + QH * half + q;
+      const float2 a = av[q];
+      const float2 bv = i < k ? cmul(bw[q], dinv[i]) : make_float2(0.f, 0.f);
+      const int kk = 2 * (QH * half + q);
+      const int o0 = tc_off(row, kk), o1 = tc_off(row, kk + 1);
+      const float arh = tf32_rna(a.x), aih = tf32_rna(a.y);
+      const float brh = tf32_rna(bv.x), bih = tf32_rna(bv.y), nbih = tf32_rna(-bv.y);
+      Ah[o0] = arh;
+      Al[o0] = tf32_rna(a.x - arh);
+      Ah[o1] = aih;
+      Al[o1] = tf32_rna(a.y - aih);
+      B1h[o0] = brh;
+      B1l[o0] = tf32_rna(bv.x - brh);
+      B1h[o1] = nbih;
+      B1l[o1] = tf32_rna(-bv.y - nbih);
+      B2h[o0] = bih;
+      B2l[o0] = tf32_rna(bv.y - bih);
+      B2h[o1] = brh;
+      B2l[o1] = tf32_rna(bv.x - brh);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
-      for (int kk = 0; kk < 4; kk++) {
-        const uint32_t off = kk * 256;                  // two core matrices (8 K-elements) per MMA
-        const uint32_t acc0 = (kc > 0 || kk > 0) ? 1u : 0u;
+      for (int kk = 0; kk < kTcK / 8; kk++) {
+        const uint32_t off = kk * 256;                // two core matrices (8 K values) per MMA
+        const uint32_t acc0 = (st > 0 || kk > 0) ? 1u : 0u;
         const uint64_t dah = tc_desc(smem_addr(Ah) + off), dal = tc_desc(smem_addr(Al) + off);
         tc_mma(tmem, dah, tc_desc(smem_addr(B1h) + off), acc0);
         tc_mma(tmem, dah, tc_desc(smem_addr(B1l) + off), 1u);
@@ -450,30 +488,38 @@ __global__ void __launch_bounds__(128) k_cb_tc(const int4* tasks, const SnDev* s
         tc_mma(tmem + 128, dal, tc_desc(smem_addr(B2h) + off), 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_addr(&mbar)));
+                   :: "r"(smem_addr(&mbar[b])));
     }
-    const bool mine = tc_wait(&mbar, phase, first_wait);
-    ok = __syncthreads_and(mine) != 0;                 // block-uniform; the stage may be overwritten
-    if (ok) phase ^= 1u;
+    issued = st + 1;
+    if (st + 1 < nst) load_stage(st + 1);
+  }
+  // the last stage's commit covers every MMA before it (they complete in order)
+  const int L = issued - 1;
+  uint64_t* lbar = &mbar[L & 1];
+  const uint32_t lpar = uint32_t(L >> 1) & 1u;
+  if (ok) {
+    const bool mine = tc_wait(lbar, lpar, first_wait);
+    ok = __syncthreads_and(mine) != 0;
   }
   if (!ok) {
-    const bool drained = tc_wait(&mbar, phase, kTcDrainPolls);   // MMAs of the last stage still in flight
+    const bool drained = tc_wait(lbar, lpar, kTcDrainPolls);   // MMAs still in flight
     const bool all = __syncthreads_and(drained) != 0;
     if (tid == 0) atomicOr(&status->timeout, all ? 1u : 3u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    const int a = a0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < 128; c0 += 32) {
+    const int q4 = warp & 3, ch = warp >> 2;           // TMEM lanes 32 q4.., columns 64 ch..
+    const int a = a0 + q4 * 32 + lane;
+    for (int c0 = ch * 64; c0 < ch * 64 + 64; c0 += 32) {
       float re[32], im[32];
-      const uint32_t ta = tmem + (uint32_t(warp * 32) << 16) + c0;
+      const uint32_t ta = tmem + (uint32_t(q4 * 32) << 16) + c0;
       tc_ld32(ta, re);
       tc_ld32(ta + 128, im);
       if (a < r) {
         for (int j = 0; j < 32; j++) {
-          const int b = b0 + c0 + j;
-          if (b < r && a >= b) {
-            const int64_t pos = (k + a) + int64_t(k + b) * m;
+          const int bb = b0 + c0 + j;
+          if (bb < r && a >= bb) {
+            const int64_t pos = (k + a) + int64_t(k + bb) * m;
             float2 f = F[pos];
             f.x -= re[j];
             f.y -= im[j];
@@ -561,7 +607,7 @@ static void factor_level_t(const FactorDev& F, int lev, int grp, double w, V* fr
     range(F.h_tc_g, lev, tb, te);
     if (te > tb) {
       HZ_COUNT();
-      k_cb_tc<<<unsigned(te - tb), 128, kTcSmemFloats * sizeof(float), st>>>(F.tc_tasks + tb, F.sn, F.scr_off,
+      k_cb_tc<<<unsigned(te - tb), 256, kTcSmemFloats * sizeof(float), st>>>(F.tc_tasks + tb, F.sn, F.scr_off,
                                                                             fronts, scratch, status, F.tc_wait);
     }
   } else {
