@@ -278,19 +278,21 @@ SERVE_FREQS = (1.0, 1.25, 1.5, 2.0, 2.5)
 
 
 def serve_problem(seed, f):
+    """A served problem: the seeded model meshed for frequency f like the 5 Hz workload,
+    with about 37k dofs per subdomain at and above 4.5 Hz (fewer, larger-share parts below)."""
     import synth
-    nsub = 8 if f < 1.5 else 16
+    nsub = 8 if f < 1.5 else (16 if f < 3.0 else (32 if f < 4.5 else 64))
     return synth.overthrust_problem(seed=seed, freq=f, nsub=nsub, overlap=2, restart=50, levels=2)
 
 
-def serve_requests(rng, nreq, rate, max_batch):
+def serve_requests(rng, nreq, rate, max_batch, nprob):
     """Poisson arrivals (exponential gaps at `rate` per second); each request names a
     problem uniformly, and 1..max_batch sources at uniform surface positions, 50 m deep."""
     import numpy as np
     gaps = rng.exponential(1.0 / rate, nreq)
     out = []
     for k in range(nreq):
-        pid = int(rng.integers(0, len(SERVE_SEEDS) * len(SERVE_FREQS)))
+        pid = int(rng.integers(0, nprob))
         nb = int(rng.integers(1, max_batch + 1))
         xy = rng.uniform(0.5, 19.5, (nb, 2))
         pts = np.column_stack([xy, np.full(nb, 0.05)])
@@ -309,37 +311,48 @@ def serve_bench(args):
     torch.cuda.set_device(0)
     build.build()
     t0 = time.time()
-    probs = [serve_problem(sd, f) for sd in SERVE_SEEDS for f in SERVE_FREQS]
+    freqs = tuple(args.serve_freqs) if args.serve_freqs else SERVE_FREQS
+    probs = [serve_problem(sd, f) for sd in SERVE_SEEDS for f in freqs]
     t_gen = time.time() - t0
     budget = 150 * 10**9
     res = {}
     for pname in ({"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]):
-        srv = hz.Server(slots=16, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64, hbm_budget=budget)
+        srv = hz.Server(slots=args.serve_slots, precision=hz.HZ_MIXED if pname == "mixed" else hz.HZ_FP64,
+                        hbm_budget=budget)
+        deadline = time.time() + args.serve_max_s
+
+        def left():
+            return max(1.0, deadline - time.time())
+
+        def log(msg):
+            print(f"[serve {pname} {time.time() - t0:7.1f} s] {msg}", file=sys.stderr, flush=True)
         ids = [srv.add_problem(p) for p in probs]
         # cold start: one single-source request per problem loads every factorisation
         tc = time.time()
         warm = [srv.submit(i, [[10.0, 10.0, 0.05]], 1e-6) for i in ids]
         for r in warm:
-            srv.wait(r)
+            srv.wait(r, timeout=left())
         t_cold = time.time() - tc
+        log(f"cold start of {len(ids)} problems in {t_cold:.1f} s")
         dofs = [srv.ndofs(i) for i in ids]
         # capacity: a closed burst of requests with the stream's batch mix
         rng = np.random.default_rng(11)
-        burst = serve_requests(rng, max(args.warmup, 3) * 8, 1.0, args.serve_batch)
+        burst = serve_requests(rng, args.serve_burst or max(args.warmup, 3) * 8, 1.0, args.serve_batch, len(probs))
         tb = time.time()
         reqs = [srv.submit(pid, pts, 1e-6) for _, pid, pts in burst]
         for r in reqs:
-            srv.wait(r)
+            srv.wait(r, timeout=left())
         cap = sum(len(p) for _, _, p in burst) / (time.time() - tb)
+        log(f"capacity burst: {len(burst)} requests, {cap:.2f} RHS/s")
         rate = 0.7 * cap / ((1 + args.serve_batch) / 2.0)        # ~70 % of the measured capacity
-        stream = serve_requests(np.random.default_rng(12), args.steps, rate, args.serve_batch)
+        stream = serve_requests(np.random.default_rng(12), args.steps, rate, args.serve_batch, len(probs))
         s0 = srv.stats()
         clocks = Clocks(0, os.path.join(clocks_dir(args), f"clocks_serve_{pname}.csv"))
         done = []
         lock = threading.Lock()
 
         def collect(r, n_src, n_dof):
-            X, inf, t = srv.wait(r)
+            X, inf, t = srv.wait(r, timeout=left())
             with lock:
                 done.append((t["latency_s"], n_src, max(i for i, _, _ in inf), all(st == 0 for _, st, _ in inf),
                              n_src * n_dof * 16))
@@ -384,9 +397,9 @@ def serve_bench(args):
         else "complex128",
         "data": "synthetic",
         "config": {"workload": "serving: Poisson stream over 3 Overthrust-shaped models x 5 frequencies",
-                   "seeds": list(SERVE_SEEDS), "freqs_hz": list(SERVE_FREQS),
+                   "seeds": list(SERVE_SEEDS), "freqs_hz": list(freqs),
                    "dofs": R["dofs"],
-                   "batch_sources": [1, args.serve_batch], "slots": 16, "hbm_budget_gb": budget / 1e9,
+                   "batch_sources": [1, args.serve_batch], "slots": args.serve_slots, "hbm_budget_gb": budget / 1e9,
                    "tol": 1e-6, "arrival": "Poisson at 70% of the measured closed-loop capacity",
                    "l2": "factors and Krylov bases >> 129 MB", "parallelism": "replicas x1"},
         "latency_ms": {"p50": 1e3 * R["p50"], "p99": 1e3 * R["p99"]},
@@ -552,6 +565,13 @@ def main():
     ap.add_argument("--workload", default="overthrust-5hz",
                     choices=list(WORKLOADS) + ["serving", "trends", "crossover", "block"])
     ap.add_argument("--serve-batch", type=int, default=16, help="largest sources per request (serving)")
+    ap.add_argument("--serve-freqs", type=float, nargs="+", default=None,
+                    help="frequencies of the served problems (default: 1.0 1.25 1.5 2.0 2.5)")
+    ap.add_argument("--serve-slots", type=int, default=16, help="slots per served problem")
+    ap.add_argument("--serve-max-s", type=float, default=1500.0,
+                    help="wall-clock limit of the serving run; a request still open then raises")
+    ap.add_argument("--serve-burst", type=int, default=0,
+                    help="requests of the closed capacity burst (0: 8 x max(warmup, 3))")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default="",

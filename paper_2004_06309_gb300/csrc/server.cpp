@@ -182,9 +182,21 @@ void hz_server::loader_loop() {
       hz_engine::plan_bytes(*p->host, p->opt, p->est_persistent, p->est_transient);
       st.analyses++;
     }
-    // room under the budget: evict idle problems, least recently used first
+    // room under the budget: evict idle problems, least recently used first.  A problem
+    // that needs more than the whole budget can never be admitted, whatever else is
+    // resident: its requests fail at once (waiting for others to leave would never end
+    // when they stay resident and idle).
     const int64_t need = p->est_persistent + p->est_transient;
     std::vector<Problem*> evict;
+    if (budget > 0 && need > budget) {
+      std::lock_guard<std::mutex> lk(mu);
+      err = "problem " + std::to_string(p->id) + " needs " + std::to_string(need) + " bytes, over the budget of " +
+            std::to_string(budget);
+      p->state = P_IDLE;
+      fail_queued(*p, HZ_ERR_OOM);
+      cv_done.notify_all();
+      continue;
+    }
     {
       std::unique_lock<std::mutex> lk(mu);
       for (;;) {

@@ -158,3 +158,58 @@ def test_problem_over_budget_and_bad_requests(hzmod, probs):
     X, inf, t = srv.wait(srv.submit(a, np.zeros((0, 3))), timeout=60)   # empty request
     assert X.shape[1] == 0 and inf == []
     srv.close()
+
+
+def test_same_alone_and_in_the_mix_at_55k_dofs(hzmod):
+    """The alone-against-mix property on two 54,925-dof Overthrust-shaped problems (1.25 Hz,
+    coarse (16, 16, 3) cells, 8 subdomains) with 8 slots: a 5-source request solved alone,
+    then again among 4 other requests on both problems, gives bitwise the same solutions
+    and iteration counts; both meet the tolerance with the oracle's operator."""
+    pa = synth.overthrust_problem(seed=0, freq=1.25, nsub=8, overlap=2, restart=50, levels=2)
+    pb = synth.overthrust_problem(seed=1, freq=1.25, nsub=8, overlap=2, restart=50, levels=2)
+    srv = hzmod.Server(slots=8, precision=hzmod.HZ_MIXED)
+    try:
+        a = srv.add_problem(pa)
+        b = srv.add_problem(pb)
+        R = _pts(pa, [[0.2, 0.3, 0.1], [0.6, 0.5, 0.3], [0.45, 0.7, 0.2], [0.8, 0.2, 0.4], [0.3, 0.9, 0.1]])
+        X_alone, inf_alone, _ = srv.wait(srv.submit(a, R, TOL), timeout=900)
+        assert all(s == 0 for _, s, _ in inf_alone)
+        rng = np.random.default_rng(3)
+        others = [srv.submit(b, _pts(pb, rng.uniform(0.1, 0.9, (4, 3))), TOL),
+                  srv.submit(a, _pts(pa, rng.uniform(0.1, 0.9, (3, 3))), TOL)]
+        again = srv.submit(a, R, TOL)
+        others += [srv.submit(a, _pts(pa, rng.uniform(0.1, 0.9, (6, 3))), TOL),
+                   srv.submit(b, _pts(pb, rng.uniform(0.1, 0.9, (2, 3))), TOL)]
+        X_mix, inf_mix, _ = srv.wait(again, timeout=900)
+        assert [i for i, _, _ in inf_mix] == [i for i, _, _ in inf_alone]
+        assert np.array_equal(X_alone, X_mix)
+        for req in others:
+            X, inf, t = srv.wait(req, timeout=900)
+            assert all(s == 0 for _, s, _ in inf)
+    finally:
+        srv.close()
+    _check_residuals(OracleSolver(pa), R, X_mix)
+
+
+def test_problem_over_the_budget_fails_while_others_stay_resident(hzmod):
+    """A problem that needs more than the whole HBM budget ends its requests with
+    HZ_ERR_OOM at once, even while another problem stays resident and idle (that one is
+    never evicted for it, since evicting it could not make room); the resident problem
+    keeps serving afterwards."""
+    small = synth.small_overthrust(seed=0, levels=2, cells=(5, 5, 3), freq=0.6, nsub=16)
+    big = synth.overthrust_problem(seed=0, freq=1.25, nsub=8, overlap=2, restart=50, levels=2)
+    srv = hzmod.Server(slots=4, precision=hzmod.HZ_MIXED, hbm_budget=800 * 10**6)
+    try:
+        a = srv.add_problem(small)
+        b = srv.add_problem(big)
+        X, inf, _ = srv.wait(srv.submit(a, _pts(small, [[0.3, 0.4, 0.3]]), TOL), timeout=300)
+        assert inf[0][1] == 0
+        X, inf, _ = srv.wait(srv.submit(b, _pts(big, [[0.3, 0.4, 0.1], [0.6, 0.5, 0.2]]), TOL), timeout=300)
+        assert [s for _, s, _ in inf] == [hzmod.HZ_ERR_OOM] * 2
+        assert "over the budget" in srv.last_error()
+        X, inf, _ = srv.wait(srv.submit(a, _pts(small, [[0.5, 0.5, 0.5]]), TOL), timeout=300)
+        assert inf[0][1] == 0
+        st = srv.stats()
+        assert st["evictions"] == 0 and st["factorisations"] == 1
+    finally:
+        srv.close()
