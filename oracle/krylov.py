@@ -374,6 +374,132 @@ def gcrodr(apply_A, apply_M, b, tol=1e-6, m=50, k=10, recycle=None, maxit=1000, 
             return x, its, rel, rel <= tol, (Ux, Uh, C)
 
 
+def block_gcrodr(apply_A, apply_M, B, tol=1e-6, m=30, k=8, recycle=None, maxit=1000):
+    """Block GCRO-DR: block FGMRES (block_fgmres's steps) with a recycled space (gcrodr's),
+    for the s columns of B together.  Returns (X, iterations, true relative residuals,
+    converged, recycle) with recycle = (Ux, Uh, C) for the next block at the same A and M.
+
+    Per cycle: R is made orthogonal to C (X += Ux C^H R, R -= C C^H R) and factored R = V_0 beta;
+    each block step orthogonalises A M^{-1} V_j against [C, V_0..V_j] by CGS2 (the C
+    coefficients form B, the V ones the block Hessenberg H), then the new block column by
+    column; p = m - ceil(k_now / s) block steps at most.  The least-squares problem splits as
+    in gcrodr: Y2 from the band Hessenberg by the Givens rotations of block_fgmres, Y1 = -D^{-1} B
+    Y2, so X += Z Y2 - Ux (B Y2).  At the cycle end the k harmonic Ritz vectors of smallest
+    |theta| form the new space:
+      first cycle:  (H_m + H_m^{-H} E (H_{+}^H H_{+}) E^H) z = theta z, H_{+} the s x s block below
+                    H_m and E its last s columns of the identity;
+      later:        G^H G z = theta G^H (Vh^H Wh) z as in gcrodr, with block matrices.
+    The iteration count is the number of block steps."""
+    B = np.asarray(B, np.complex128)
+    n, s = B.shape
+    bn = np.linalg.norm(B, axis=0)
+    assert np.all(bn > 0.0)
+    X = np.zeros_like(B)
+    Ux = Uh = C = None
+    if recycle is not None:
+        Ux, Uh, C = recycle
+    R0 = B.copy()
+    its = 0
+    while True:
+        kk = 0 if C is None else C.shape[1]
+        if kk:
+            c = C.conj().T @ R0
+            X = X + Ux @ c
+            R0 = R0 - C @ c
+        V0, beta, _ = _block_orthonormalise(R0, np.linalg.norm(R0, axis=0))
+        p = max(1, m - (kk + s - 1) // s)
+        V, Zs = [V0], []
+        H = np.zeros(((p + 1) * s, p * s), np.complex128)
+        Bc = np.zeros((kk, p * s), np.complex128)
+        Hr = np.zeros_like(H)                               # Givens-rotated copy
+        G = np.zeros(((p + 1) * s, s), np.complex128)
+        G[:s, :] = beta
+        rots = []
+        ks = 0
+        for j in range(p):
+            Zj = np.column_stack([apply_M(V[j][:, c]) for c in range(s)])
+            Zs.append(Zj)
+            W = np.column_stack([apply_A(Zj[:, c]) for c in range(s)])
+            w0 = np.linalg.norm(W, axis=0)
+            Q = np.hstack(([C] if kk else []) + V)
+            h1 = Q.conj().T @ W
+            W = W - Q @ h1
+            h2 = Q.conj().T @ W
+            W = W - Q @ h2
+            h = h1 + h2
+            Qn, Rn, brk = _block_orthonormalise(W, w0)
+            V.append(Qn)
+            c0 = j * s
+            Bc[:, c0: c0 + s] = h[:kk]
+            H[: (j + 1) * s, c0: c0 + s] = h[kk:]
+            H[(j + 1) * s: (j + 2) * s, c0: c0 + s] = Rn
+            Hr[:, c0: c0 + s] = H[:, c0: c0 + s]
+            for q in range(s):
+                col = c0 + q
+                for (i, r, cs, sn) in rots:
+                    t = cs * Hr[i, col] + sn * Hr[r, col]
+                    Hr[r, col] = -np.conj(sn) * Hr[i, col] + cs * Hr[r, col]
+                    Hr[i, col] = t
+                for r in range(col + s, col, -1):
+                    cs, sn = givens(Hr[col, col], Hr[r, col])
+                    t = cs * Hr[col, col] + sn * Hr[r, col]
+                    Hr[r, col] = 0.0
+                    Hr[col, col] = t
+                    gi = cs * G[col, :] + sn * G[r, :]
+                    G[r, :] = -np.conj(sn) * G[col, :] + cs * G[r, :]
+                    G[col, :] = gi
+                    rots.append((col, r, cs, sn))
+            its += 1
+            ks = j + 1
+            est = np.linalg.norm(G[ks * s: (ks + 1) * s, :], axis=0) / bn
+            if brk or np.all(est <= tol) or its >= maxit:
+                break
+        kc = ks * s
+        Y = np.zeros((kc, s), np.complex128)
+        for i in range(kc - 1, -1, -1):
+            Y[i, :] = (G[i, :] - Hr[i, i + 1: kc] @ Y[i + 1: kc, :]) / Hr[i, i]
+        Zb = np.hstack(Zs)
+        Vb = np.hstack(V)                                   # kc + s columns
+        X = X + Zb @ Y
+        if kk:
+            X = X - Ux @ (Bc[:, :kc] @ Y)
+        R0 = B - np.column_stack([apply_A(X[:, c]) for c in range(s)])
+        rel = np.linalg.norm(R0, axis=0) / bn
+        Hm = H[: kc + s, :kc]
+        if k > 0:
+            if not kk:
+                Hsq = Hm[:kc, :kc]
+                Hp = Hm[kc: kc + s, kc - s: kc]
+                E = np.zeros((kc, s), np.complex128)
+                E[kc - s:, :] = np.eye(s)
+                F = np.linalg.solve(Hsq.conj().T, E)
+                Mh = Hsq + F @ (Hp.conj().T @ Hp) @ E.conj().T
+                P = _smallest_harmonic(Mh, np.eye(kc), min(k, kc))
+                Qg, Rq = np.linalg.qr(Hm @ P)
+                Rinv = np.linalg.inv(Rq)
+                C = Vb @ Qg
+                Uh = Vb[:, :kc] @ P @ Rinv
+                Ux = Zb @ P @ Rinv
+            else:
+                dn = 1.0 / np.linalg.norm(Uh, axis=0)
+                Gm = np.zeros((kk + kc + s, kk + kc), np.complex128)
+                Gm[:kk, :kk] = np.diag(dn)
+                Gm[:kk, kk:] = Bc[:, :kc]
+                Gm[kk:, kk:] = Hm
+                Vh = np.hstack([C, Vb])
+                Wh = np.hstack([Uh * dn, Vb[:, :kc]])
+                Wx = np.hstack([Ux * dn, Zb])
+                P = _smallest_harmonic(Gm.conj().T @ Gm, Gm.conj().T @ (Vh.conj().T @ Wh), min(k, kk + kc))
+                Qg, Rq = np.linalg.qr(Gm @ P)
+                Rinv = np.linalg.inv(Rq)
+                C = Vh @ Qg
+                Uh = Wh @ P @ Rinv
+                Ux = Wx @ P @ Rinv
+        if np.all(rel <= tol) or its >= maxit:
+            rec = None if C is None else (Ux, Uh, C)
+            return X, its, rel, bool(np.all(rel <= tol)), rec
+
+
 def rebase_recycle(apply_A, recycle):
     """Carry a recycled space (Ux, Uh, C) over to a new operator (Parks et al. 2006, for a
     sequence of matrices): C' = A_new Ux is orthonormalised column by column (CGS2),

@@ -284,3 +284,129 @@ def test_rebased_space_helps_at_a_nearby_frequency():
     _, it_rec, rel, ok, _ = krylov.gcrodr(S2.apply_A, S2.apply_M, b, tol=1e-6, m=20, k=8, recycle=rb)
     _, it_new, _, _, _ = krylov.gcrodr(S2.apply_A, S2.apply_M, b, tol=1e-6, m=20, k=8)
     assert ok and it_rec < it_new, (it_rec, it_new)
+
+
+# --- block GCRO-DR ---------------------------------------------------------------------
+
+def _orth_block_krylov(op, R, p):
+    """An orthonormal basis of the block Krylov space span[R, op R, ..., op^{p-1} R], built
+    by repeated application and a full QR (independent of the Arnoldi recurrences)."""
+    blocks = [np.linalg.qr(R)[0]]
+    for _ in range(p - 1):
+        blocks.append(np.linalg.qr(op(blocks[-1]))[0])
+    return np.linalg.qr(np.hstack(blocks))[0]
+
+
+def _harmonic_ritz_span(A, W, k):
+    """Span of the k harmonic Ritz vectors of A over span(W) with the smallest |theta|, from
+    the definition: u = W z with (A u - theta u) orthogonal to A W, i.e.
+    (AW)^H (AW) z = theta (AW)^H W z."""
+    import scipy.linalg as sla
+    AW = A @ W
+    th, Z = sla.eig(AW.conj().T @ AW, AW.conj().T @ W)
+    return np.linalg.qr(W @ Z[:, np.argsort(np.abs(th))[:k]])[0]
+
+
+def _same_span(Q1, U):
+    Q2 = np.linalg.qr(U)[0]
+    sv = np.linalg.svd(Q1.conj().T @ Q2, compute_uv=False)
+    return np.abs(sv - 1.0).max()
+
+
+def test_block_gcrodr_with_one_column_is_gcrodr():
+    rng = np.random.default_rng(11)
+    n = 100
+    A = _dense(n, 12, spread=2.0)
+    d = 1.0 + rng.uniform(0, 1, n)
+    fa, fm = (lambda v: A @ v), (lambda v: v / d)
+    r1 = r2 = None
+    for _ in range(3):                                   # fresh, then two solves that recycle
+        b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        x1, i1, _, ok1, r1 = krylov.gcrodr(fa, fm, b, tol=1e-9, m=12, k=4, recycle=r1)
+        X2, i2, _, ok2, r2 = krylov.block_gcrodr(fa, fm, b[:, None], tol=1e-9, m=12, k=4, recycle=r2)
+        assert ok1 and ok2 and i1 == i2
+        assert np.linalg.norm(x1 - X2[:, 0]) <= 1e-12 * np.linalg.norm(x1)
+        # the same recycled space (its basis is the eigenvectors' up to rounding in the
+        # harmonic Ritz problem, which the two forms of the first-cycle matrix round differently)
+        assert _same_span(np.linalg.qr(r1[0])[0], r2[0]) <= 1e-9
+        assert _same_span(r1[2], r2[2]) <= 1e-9
+
+
+def test_block_gcrodr_without_recycling_is_block_fgmres():
+    A, fa, fm, d, B = _block_problem()
+    X1, i1, _, ok1 = krylov.block_fgmres(fa, fm, B, tol=1e-10, m=5)
+    X2, i2, _, ok2, rec = krylov.block_gcrodr(fa, fm, B, tol=1e-10, m=5, k=0)
+    assert ok1 and ok2 and i1 == i2 and rec is None
+    assert np.linalg.norm(X1 - X2) <= 1e-13 * np.linalg.norm(X1)
+
+
+def test_block_gcrodr_first_cycle_recycles_the_block_harmonic_ritz_space():
+    """One cycle of p = 4 block steps (M = I, s = 3): every column's residual is the
+    minimum over the block Krylov space, and span(Ux) is that of the k harmonic Ritz
+    vectors of A over the space with the smallest |theta| (the block first-cycle formula
+    with H_{+} in place of h_{m+1,m}); C = A Ux, C^H C = I."""
+    rng = np.random.default_rng(13)
+    n, s, p, k = 70, 3, 4, 5
+    A = _dense(n, 14, spread=1.5)
+    B = rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))
+    X, it, rel, ok, (Ux, Uh, C) = krylov.block_gcrodr(lambda v: A @ v, lambda v: v, B, tol=1e-15, m=p, k=k,
+                                                      maxit=p)
+    assert it == p and Ux.shape == (n, k)
+    K = _orth_block_krylov(lambda V: A @ V, B, p)
+    for j in range(s):
+        y = np.linalg.lstsq(A @ K, B[:, j], rcond=None)[0]
+        rmin = np.linalg.norm(B[:, j] - A @ K @ y) / np.linalg.norm(B[:, j])
+        assert abs(rel[j] - rmin) <= 1e-10 * rmin, (j, rel[j], rmin)
+    assert _same_span(_harmonic_ritz_span(A, K, k), Ux) <= 1e-8
+    assert np.linalg.norm(A @ Ux - C) <= 1e-12 * np.linalg.norm(C)
+    assert np.linalg.norm(C.conj().T @ C - np.eye(k)) <= 1e-13
+
+
+def test_block_gcrodr_recycled_cycle_minimises_and_updates_the_space():
+    """A second block (M = I) with the first block's space: one cycle of p = m - ceil(k/s)
+    block steps.  Each column's residual is the minimum over span(Ux_old) + the block
+    Krylov space of (I - C C^H) A started at (I - C C^H) B; the new space is the k harmonic
+    Ritz vectors of A over span[Ux_old, that Krylov space]."""
+    rng = np.random.default_rng(15)
+    n, s, m, k = 70, 3, 6, 5
+    A = _dense(n, 16, spread=1.5)
+    fa = lambda v: A @ v
+    B1 = rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))
+    _, _, _, ok, rec = krylov.block_gcrodr(fa, lambda v: v, B1, tol=1e-8, m=m, k=k)
+    assert ok
+    Ux0, Uh0, C0 = rec
+    p = m - (k + s - 1) // s
+    B2 = rng.standard_normal((n, s)) + 1j * rng.standard_normal((n, s))
+    X, it, rel, ok, (Ux, Uh, C) = krylov.block_gcrodr(fa, lambda v: v, B2, tol=1e-15, m=m, k=k, recycle=rec,
+                                                      maxit=p)
+    assert it == p
+    Pc = lambda V: V - C0 @ (C0.conj().T @ V)
+    K = _orth_block_krylov(lambda V: Pc(A @ V), Pc(B2), p)
+    W = np.linalg.qr(np.hstack([Ux0, K]))[0]
+    for j in range(s):
+        y = np.linalg.lstsq(A @ W, B2[:, j], rcond=None)[0]
+        rmin = np.linalg.norm(B2[:, j] - A @ W @ y) / np.linalg.norm(B2[:, j])
+        assert abs(rel[j] - rmin) <= 1e-9 * rmin, (j, rel[j], rmin)
+    assert _same_span(_harmonic_ritz_span(A, W, k), Ux) <= 1e-8
+    assert np.linalg.norm(A @ Ux - C) <= 1e-12 * np.linalg.norm(C)
+    assert np.linalg.norm(C.conj().T @ C - np.eye(k)) <= 1e-13
+
+
+def test_block_gcrodr_recycling_cuts_the_next_blocks_steps():
+    """Tiny configuration, three sources per block: a block that reuses the previous
+    block's space needs fewer block steps than block FGMRES on it."""
+    import synth
+    from oracle.solver import OracleSolver
+    p = synth.tiny_problem()
+    S = OracleSolver(p)
+    S.factor()
+    ext = p.mesh.xyz.max(axis=0)
+    pts = np.array([[0.2, 0.3, 0.3], [0.7, 0.2, 0.5], [0.5, 0.5, 0.2],
+                    [0.3, 0.8, 0.6], [0.8, 0.7, 0.4], [0.45, 0.55, 0.75]]) * ext
+    B = S.rhs(pts)
+    _, it1, _, ok, rec = krylov.block_gcrodr(S.apply_A, S.apply_M, B[:, :3], tol=1e-6, m=10, k=8)
+    assert ok
+    X, it2, rel, ok, _ = krylov.block_gcrodr(S.apply_A, S.apply_M, B[:, 3:], tol=1e-6, m=10, k=8, recycle=rec)
+    _, it_plain, _, _ = krylov.block_fgmres(S.apply_A, S.apply_M, B[:, 3:], tol=1e-6, m=10)
+    assert ok and np.all(np.linalg.norm(B[:, 3:] - S.A @ X, axis=0) <= 1e-6 * np.linalg.norm(B[:, 3:], axis=0))
+    assert it2 < it_plain, (it2, it_plain)
