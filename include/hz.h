@@ -124,8 +124,15 @@ typedef struct {
                                harmonic Ritz vectors at every cycle end; cycles then
                                add restart - k Arnoldi vectors.  hz_factor drops the
                                space unless recycle_keep is set.  0 = off (FGMRES);
-                               1 <= k <= min(16, restart/2); one right-hand side at a
-                               time (block_size <= 1).                               */
+                               1 <= k <= min(16, restart/2).  One right-hand side at
+                               a time (block_size <= 1), or with krylov =
+                               HZ_KRYLOV_BLOCK block GCRO-DR: each batch of up to
+                               block_size right-hand sides is one block Krylov space
+                               of at most restart - ceil(k / batch) block steps per
+                               cycle, and the space is renewed from the cycle's block
+                               harmonic Ritz vectors and kept for the next batch (a
+                               single right-hand side then runs as a batch of one).
+                               block_size > 1 with pseudo-block Krylov: HZ_ERR_ARG.    */
   /* Task shapes of the batched triangular sweeps (A_i^{-1} of Eq. 4 and the coarse
      E^{-1} of Eq. 3).  Results differ only by the rounding of the summation order.  */
   int32_t sweep_tasks;      /* 0: chosen per assembly-tree level from its task count

@@ -1010,65 +1010,120 @@ std::vector<int> smallest(const std::vector<cplx>& w, int kn) {
   return idx;
 }
 
-// New recycled space from the cycle that just ended (kk recycled vectors in it, kc
-// Arnoldi steps).  On a numerical failure the previous space is kept.
-hz_status recycle_update(hz_ctx* c, int kk, int kc) {
-  const int m = c->restart, rk = c->rk;
+// out (+)= sign * [B_1, B_2, ...] coef for any number of columns (coef: total columns x
+// nout, column-major, host).  The columns go to the combination kernel in pieces of at
+// most kComboMaxCols; the first piece writes out (or adds to it, acc), the others add.
+hz_status combo_cols(hz_ctx* c, const std::vector<std::pair<const double2*, int>>& blocks,
+                     const std::vector<cplx>& coef, int nout, double2* out, double sign, bool acc) {
+  int total = 0;
+  for (const auto& b : blocks) total += b.second;
+  bool first = true;
+  int col = 0;
+  for (const auto& b : blocks) {
+    for (int a = 0; a < b.second; a += hz::kComboMaxCols) {
+      const int w = std::min(hz::kComboMaxCols, b.second - a);
+      std::vector<cplx> piece(size_t(w) * nout);
+      for (int q = 0; q < nout; q++)
+        for (int i = 0; i < w; i++) piece[size_t(q) * w + i] = coef[size_t(q) * total + col + a + i];
+      combo(c, w, b.first + int64_t(a) * c->n, 0, nullptr, piece, nout, out, sign, acc || !first);
+      first = false;
+    }
+    col += b.second;
+  }
+  if (first && !acc) CU(cudaMemsetAsync(out, 0, size_t(nout) * c->n * 16, c->st));
+  CU(cudaGetLastError());
+  return HZ_OK;
+}
+
+// The basis whose columns the recycled space C precedes in memory: C sits in the kk
+// columns right before it, so that [C, V] is one column-major block.
+double2* recycle_basis(hz_ctx* c) { return c->krylov == HZ_KRYLOV_BLOCK ? c->Vb : c->V; }
+
+// New recycled space from the cycle that just ended, for one right-hand side (s = 1) or a
+// block of s: kk recycled vectors at the cycle start, kc basis columns in the cycle (Arnoldi
+// steps times s).  Hm ((kc + s) x kc) is the unrotated (block) Hessenberg matrix and Bm
+// (kk x kc) the coefficients of the orthogonalisation against C, both column-major on the
+// host; V (with C before it) and Z are the cycle's bases.  The k harmonic Ritz vectors of
+// smallest |theta| over the search space become the new space:
+//   kk = 0:  (H + H^{-H} E (H_+^H H_+) E^H) z = theta z, H the square top of Hm, H_+ the
+//            s x s block below it, E the last s columns of the identity;
+//   kk > 0:  G^H G z = theta G^H (Vh^H Wh) z, G = [[D, B], [0, Hm]], Vh = [C, V],
+//            Wh = [Uh D, V_kc], D = diag(1 / |Uh_i|).
+// With P the chosen vectors and G P = Q R: C = Vh Q, Uh = Wh P R^{-1}, Ux = [Ux D, Z] P R^{-1}
+// (Parks et al. 2006, GCRO-DR; the block form replaces h_{m+1,m} by H_+).  On a numerical
+// failure the previous space is kept.
+hz_status recycle_space(hz_ctx* c, int kk, int kc, int s, const std::vector<cplx>& Hm, const std::vector<cplx>& Bm,
+                        double2* V, const double2* Z) {
+  const int rk = c->rk;
   const int64_t n = c->n;
   const int nb = hz::cgs_blocks();
   cudaStream_t st = c->st;
   if (kc < 1) return HZ_OK;
   CU(cudaStreamSynchronize(st));
-  const std::vector<cplx> Hr = to_host(c->Hraw, size_t(m + 1) * kc);     // column j at j (m + 1)
-  auto H = [&](int i, int j) { return Hr[size_t(j) * (m + 1) + i]; };
+  const int lh = kc + s;                                                 // rows of Hm
+  auto H = [&](int i, int j) { return Hm[size_t(j) * lh + i]; };
   const int nt = kk + kc;                                                // columns of G
+  const int ng = nt + s;                                                 // rows of G
   const int kn = std::min(rk, nt);
-  std::vector<cplx> G(size_t(nt + 1) * nt, 0.0), P, w, VR, Mg;
+  std::vector<cplx> G(size_t(ng) * nt, 0.0), P, w, VR, Mg;
   std::vector<double> dsc(size_t(kk), 1.0);
   std::string err;
+  double2* Cb = V - int64_t(kk) * n;
   if (kk == 0) {
-    // harmonic Ritz pairs of H_m: (H_m + |h|^2 H_m^{-H} e_m e_m^H) z = theta z
-    std::vector<cplx> Hm(size_t(kc) * kc), HmH(size_t(kc) * kc), f(size_t(kc), 0.0);
+    std::vector<cplx> Hq(size_t(kc) * kc), HqH(size_t(kc) * kc), F(size_t(kc) * s, 0.0), HpHp(size_t(s) * s, 0.0);
     for (int j = 0; j < kc; j++)
-      for (int i = 0; i < kc; i++) Hm[size_t(j) * kc + i] = H(i, j);
+      for (int i = 0; i < kc; i++) Hq[size_t(j) * kc + i] = H(i, j);
     for (int j = 0; j < kc; j++)
-      for (int i = 0; i < kc; i++) HmH[size_t(j) * kc + i] = std::conj(Hm[size_t(i) * kc + j]);
-    f[size_t(kc - 1)] = 1.0;
-    if (!hz_small::lu_solve(kc, HmH, f, 1)) return HZ_OK;
-    const double hl2 = std::norm(H(kc, kc - 1));
-    Mg = Hm;
-    for (int i = 0; i < kc; i++) Mg[size_t(kc - 1) * kc + i] += hl2 * f[size_t(i)];
+      for (int i = 0; i < kc; i++) HqH[size_t(j) * kc + i] = std::conj(Hq[size_t(i) * kc + j]);
+    for (int q = 0; q < s; q++) F[size_t(q) * kc + kc - s + q] = 1.0;              // E
+    if (!hz_small::lu_solve(kc, HqH, F, s)) return HZ_OK;                         // H^{-H} E
+    for (int a = 0; a < s; a++)                                                    // H_+^H H_+
+      for (int b = 0; b < s; b++) {
+        cplx acc = 0;
+        for (int r = 0; r < s; r++) acc += std::conj(H(kc + r, kc - s + a)) * H(kc + r, kc - s + b);
+        HpHp[size_t(b) * s + a] = acc;
+      }
+    Mg = Hq;
+    for (int b = 0; b < s; b++)
+      for (int i = 0; i < kc; i++) {
+        cplx acc = 0;
+        for (int a = 0; a < s; a++) acc += F[size_t(a) * kc + i] * HpHp[size_t(b) * s + a];
+        Mg[size_t(kc - s + b) * kc + i] += acc;
+      }
     for (int j = 0; j < kc; j++)
-      for (int i = 0; i <= kc; i++) G[size_t(j) * (nt + 1) + i] = H(i, j);
+      for (int i = 0; i < lh; i++) G[size_t(j) * ng + i] = H(i, j);
   } else {
-    // G = [[D, B], [0, H]], Vh^H Wh = [[C^H Uh D, 0], [V^H Uh D, I]]:
-    // harmonic Ritz pairs of G^H G z = theta G^H (Vh^H Wh) z
-    const std::vector<cplx> Bh = to_host(c->Braw, size_t(rk) * kc);        // column j at j rk
-    const double2* Cb = c->V - int64_t(kk) * n;
-    std::vector<cplx> VW(size_t(nt + 1) * nt, 0.0);
+    // Vh^H Wh = [[C^H Uh D, 0], [V^H Uh D, I_kc; 0]]: the Uh columns against [C, V], 64 at a time
+    std::vector<cplx> VW(size_t(ng) * nt, 0.0);
     for (int i = 0; i < kk; i++) {
       double2* ui = c->Uh + int64_t(i) * n;
-      hz::launch_cgs(n, kk + kc + 1, Cb, n, nullptr, ui, kk + kc + 1, c->partial, st);
-      hz::launch_reduce(c->partial, nb, kk + kc + 1, c->h1, st);
-      CU(cudaStreamSynchronize(st));
-      const std::vector<cplx> hv = to_host(c->h1, 65);
-      dsc[size_t(i)] = 1.0 / std::sqrt(hv[64].real());
-      for (int a = 0; a <= nt; a++) VW[size_t(i) * (nt + 1) + a] = hv[size_t(a)] * dsc[size_t(i)];
+      double unorm2 = 0.0;
+      for (int a = 0; a < ng; a += 64) {
+        const int wc = std::min(64, ng - a);
+        hz::launch_cgs(n, wc, Cb + int64_t(a) * n, n, nullptr, ui, wc, c->partial, st);
+        hz::launch_reduce(c->partial, nb, wc, c->h1, st);
+        CU(cudaStreamSynchronize(st));
+        const std::vector<cplx> hv = to_host(c->h1, 65);
+        for (int q = 0; q < wc; q++) VW[size_t(i) * ng + a + q] = hv[size_t(q)];
+        unorm2 = hv[64].real();
+      }
+      dsc[size_t(i)] = 1.0 / std::sqrt(unorm2);
+      for (int a = 0; a < ng; a++) VW[size_t(i) * ng + a] *= dsc[size_t(i)];
     }
-    for (int j = 0; j < kc; j++) VW[size_t(kk + j) * (nt + 1) + kk + j] = 1.0;
-    for (int i = 0; i < kk; i++) G[size_t(i) * (nt + 1) + i] = dsc[size_t(i)];
+    for (int j = 0; j < kc; j++) VW[size_t(kk + j) * ng + kk + j] = 1.0;
+    for (int i = 0; i < kk; i++) G[size_t(i) * ng + i] = dsc[size_t(i)];
     for (int j = 0; j < kc; j++) {
-      for (int i = 0; i < kk; i++) G[size_t(kk + j) * (nt + 1) + i] = Bh[size_t(j) * rk + i];
-      for (int i = 0; i <= kc; i++) G[size_t(kk + j) * (nt + 1) + kk + i] = H(i, j);
+      for (int i = 0; i < kk; i++) G[size_t(kk + j) * ng + i] = Bm[size_t(j) * kk + i];
+      for (int i = 0; i < lh; i++) G[size_t(kk + j) * ng + kk + i] = H(i, j);
     }
     std::vector<cplx> Ag(size_t(nt) * nt, 0.0), Bg(size_t(nt) * nt, 0.0);
     for (int a = 0; a < nt; a++)
       for (int b = 0; b < nt; b++) {
         cplx sa = 0, sb = 0;
-        for (int r = 0; r <= nt; r++) {
-          const cplx gra = std::conj(G[size_t(a) * (nt + 1) + r]);
-          sa += gra * G[size_t(b) * (nt + 1) + r];
-          sb += gra * VW[size_t(b) * (nt + 1) + r];
+        for (int r = 0; r < ng; r++) {
+          const cplx gra = std::conj(G[size_t(a) * ng + r]);
+          sa += gra * G[size_t(b) * ng + r];
+          sb += gra * VW[size_t(b) * ng + r];
         }
         Ag[size_t(b) * nt + a] = sa;
         Bg[size_t(b) * nt + a] = sb;
@@ -1084,14 +1139,14 @@ hz_status recycle_update(hz_ctx* c, int kk, int kc) {
   P.assign(size_t(nt) * kn, 0.0);
   for (int q = 0; q < kn; q++)
     for (int i = 0; i < nt; i++) P[size_t(q) * nt + i] = VR[size_t(pick[size_t(q)]) * nt + i];
-  std::vector<cplx> GP(size_t(nt + 1) * kn, 0.0), Q, R;
+  std::vector<cplx> GP(size_t(ng) * kn, 0.0), Q, R;
   for (int q = 0; q < kn; q++)
-    for (int i = 0; i <= nt; i++) {
+    for (int i = 0; i < ng; i++) {
       cplx sacc = 0;
-      for (int j = 0; j < nt; j++) sacc += G[size_t(j) * (nt + 1) + i] * P[size_t(q) * nt + j];
-      GP[size_t(q) * (nt + 1) + i] = sacc;
+      for (int j = 0; j < nt; j++) sacc += G[size_t(j) * ng + i] * P[size_t(q) * nt + j];
+      GP[size_t(q) * ng + i] = sacc;
     }
-  hz_small::qr_thin(nt + 1, kn, GP, Q, R);
+  hz_small::qr_thin(ng, kn, GP, Q, R);
   if (!hz_small::tri_inv_upper(kn, R)) return HZ_OK;
   // U coefficients: P R^{-1}, recycled rows scaled by D
   std::vector<cplx> PU(size_t(nt) * kn, 0.0);
@@ -1101,17 +1156,34 @@ hz_status recycle_update(hz_ctx* c, int kk, int kc) {
       for (int r = 0; r <= q; r++) sacc += P[size_t(r) * nt + i] * R[size_t(q) * kn + r];
       PU[size_t(q) * nt + i] = (i < kk ? dsc[size_t(i)] : 1.0) * sacc;
     }
-  const double2* Cb = c->V - int64_t(kk) * n;
-  combo(c, kk, Cb, kc + 1, c->V, Q, kn, c->Ctmp, 1.0, false);       // C = [C, V] Q
-  combo(c, kk, c->Uh, kc, c->V, PU, kn, c->Uht, 1.0, false);        // Uh = [Uh D, V] P R^-1
-  combo(c, kk, c->Ux, kc, c->Zs, PU, kn, c->Uxt, 1.0, false);       // Ux = [Ux D, Z] P R^-1
-  CU(cudaMemcpyAsync(c->V - int64_t(kn) * n, c->Ctmp, size_t(kn) * n * 16, cudaMemcpyDeviceToDevice, st));
+  TRY(combo_cols(c, {{Cb, ng}}, Q, kn, c->Ctmp, 1.0, false));                   // C = [C, V] Q
+  TRY(combo_cols(c, {{c->Uh, kk}, {V, kc}}, PU, kn, c->Uht, 1.0, false));      // Uh = [Uh D, V] P R^-1
+  TRY(combo_cols(c, {{c->Ux, kk}, {Z, kc}}, PU, kn, c->Uxt, 1.0, false));      // Ux = [Ux D, Z] P R^-1
+  CU(cudaMemcpyAsync(V - int64_t(kn) * n, c->Ctmp, size_t(kn) * n * 16, cudaMemcpyDeviceToDevice, st));
   std::swap(c->Uh, c->Uht);
   std::swap(c->Ux, c->Uxt);
   c->rdim = kn;
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
   return HZ_OK;
+}
+
+// The single right-hand side's cycle end: its Hessenberg and B columns from the device
+// (Hraw: column j at j (m + 1); Braw: column j at j rk).
+hz_status recycle_update(hz_ctx* c, int kk, int kc) {
+  const int m = c->restart, rk = c->rk;
+  if (kc < 1) return HZ_OK;
+  CU(cudaStreamSynchronize(c->st));
+  const std::vector<cplx> Hr = to_host(c->Hraw, size_t(m + 1) * kc);
+  std::vector<cplx> Hm(size_t(kc + 1) * kc), Bm(size_t(kk) * kc);
+  for (int j = 0; j < kc; j++)
+    for (int i = 0; i <= kc; i++) Hm[size_t(j) * (kc + 1) + i] = Hr[size_t(j) * (m + 1) + i];
+  if (kk > 0) {
+    const std::vector<cplx> Bh = to_host(c->Braw, size_t(rk) * kc);
+    for (int j = 0; j < kc; j++)
+      for (int i = 0; i < kk; i++) Bm[size_t(j) * kk + i] = Bh[size_t(j) * rk + i];
+  }
+  return recycle_space(c, kk, kc, 1, Hm, Bm, c->V, c->Zs);
 }
 
 // One right-hand side by GCRO-DR (x0 = 0), with the stopping and counting rules of
@@ -1135,7 +1207,7 @@ hz_status recycle_rebase(hz_ctx* c) {
   for (int i = 0; i < kk; i++) TRY(norm2(c, c->Ctmp + int64_t(i) * n, w0[i]));
   std::vector<cplx> R;
   bool brk = false;
-  TRY(block_orthonormalise(c, c->Ctmp, kk, c->V - int64_t(kk) * n, R, w0.data(), brk));
+  TRY(block_orthonormalise(c, c->Ctmp, kk, recycle_basis(c) - int64_t(kk) * n, R, w0.data(), brk));
   if (brk || !hz_small::tri_inv_upper(kk, R)) {
     c->rdim = 0;
     return HZ_OK;
@@ -1577,9 +1649,11 @@ hz_status block_orthonormalise(hz_ctx* c, double2* W, int s, double2* Q, std::ve
   return HZ_OK;
 }
 
-// Block step j: Z_j = M^{-1} V_j, W = A Z_j, block CGS2 against V_0..V_j and the new block.
-// hcol ((j + 2) s x s, column-major, host): the step's column of the block Hessenberg matrix.
-hz_status block_step(hz_ctx* c, int j, int s, std::vector<cplx>& hcol, bool& brk) {
+// Block step j: Z_j = M^{-1} V_j, W = A Z_j, block CGS2 against [C, V_0..V_j] (C: the kk
+// recycled columns stored right before V; kk = 0 without recycling) and the new block.
+// hcol ((kk + (j + 2) s) x s, column-major, host): rows [0, kk) the coefficients against C,
+// then the step's column of the block Hessenberg matrix.
+hz_status block_step(hz_ctx* c, int j, int s, int kk, std::vector<cplx>& hcol, bool& brk) {
   const int S = c->S;
   const int64_t n = c->n;
   cudaStream_t st = c->st;
@@ -1597,14 +1671,15 @@ hz_status block_step(hz_ctx* c, int j, int s, std::vector<cplx>& hcol, bool& brk
   hz::launch_deinterleave(n, S, wout, c->Wi, c->Wc, st);
   std::vector<double> w0(s);
   for (int i = 0; i < s; i++) TRY(norm2(c, c->Wc + int64_t(i) * n, w0[i]));
-  const int p = (j + 1) * s;
+  const double2* base = c->Vb - int64_t(kk) * n;
+  const int p = kk + (j + 1) * s;
   const int nch = (p + 63) / 64;
   hz::SlotCgs pc{};
   for (int pass = 0; pass < 2; pass++) {
     for (int k = 0; k < nch; k++) {
       for (int i = 0; i < 16; i++) {
         const bool on = i < s;
-        pc.V[i] = on ? c->Vb + int64_t(64) * k * n : nullptr;
+        pc.V[i] = on ? base + int64_t(64) * k * n : nullptr;
         pc.w[i] = on ? c->Wc + int64_t(i) * n : nullptr;
         pc.h[i] = nullptr;
         pc.ncols[i] = on ? std::min(64, p - 64 * k) : -1;
@@ -1614,7 +1689,7 @@ hz_status block_step(hz_ctx* c, int j, int s, std::vector<cplx>& hcol, bool& brk
     for (int k = 0; k < nch; k++) {
       for (int i = 0; i < 16; i++) {
         const bool on = i < s;
-        pc.V[i] = on ? c->Vb + int64_t(64) * k * n : nullptr;
+        pc.V[i] = on ? base + int64_t(64) * k * n : nullptr;
         pc.w[i] = on ? c->Wc + int64_t(i) * n : nullptr;
         pc.h[i] = on ? c->hblk + ((int64_t(pass) * nch + k) * S + i) * 65 : nullptr;
         pc.ncols[i] = on ? std::min(64, p - 64 * k) : -1;
@@ -1635,16 +1710,21 @@ hz_status block_step(hz_ctx* c, int j, int s, std::vector<cplx>& hcol, bool& brk
       hcol[r + size_t(i) * ld] = cplx(a.x + b.x, a.y + b.y);
     }
   std::vector<cplx> R;
-  TRY(block_orthonormalise(c, c->Wc, s, c->Vb + int64_t(p) * n, R, w0.data(), brk));
+  TRY(block_orthonormalise(c, c->Wc, s, c->Vb + int64_t(p - kk) * n, R, w0.data(), brk));
   for (int i = 0; i < s; i++)
     for (int r = 0; r < s; r++) hcol[p + r + size_t(i) * ld] = R[r + size_t(i) * s];
   return HZ_OK;
 }
 
-// Solves the s right-hand sides in Bc[0..s) (all nonzero) into Xc[0..s).
+// Solves the s right-hand sides in Bc[0..s) (all nonzero) into Xc[0..s).  With recycling
+// (options.recycle = rk > 0) this is block GCRO-DR: each cycle first makes the residual
+// block orthogonal to C (X += Ux C^H R, R -= C C^H R), runs at most m - ceil(kk / s) block
+// steps against [C, V], adds X += Z Y - Ux (B Y), and replaces the recycled space by the
+// cycle's block harmonic Ritz vectors; the space is kept for the next batch.
 hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
   const int64_t n = c->n;
   const int m = c->restart;
+  const int nb = hz::cgs_blocks();
   cudaStream_t st = c->st;
   for (int i = 0; i < c->S; i++) c->slots[i].state = i < s ? hz_ctx::SLOT_RUN : hz_ctx::SLOT_FREE;
   std::vector<double> bn(s), rel(s, 0.0);
@@ -1652,7 +1732,7 @@ hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
   CU(cudaMemsetAsync(c->Xc, 0, size_t(s) * n * 16, st));
   CU(cudaMemcpyAsync(c->Wc, c->Bc, size_t(s) * n * 16, cudaMemcpyDeviceToDevice, st));
   const int ldh = (m + 1) * s;
-  std::vector<cplx> H, G, hcol, beta;
+  std::vector<cplx> H, Hr, Bm, G, hcol, beta;
   struct Rot { int i, r; double cs; cplx sn; };
   std::vector<Rot> rots;
   auto givens = [](cplx a, cplx b, double& cs, cplx& sn) {
@@ -1665,22 +1745,39 @@ hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
   int its = 0;
   bool nonfinite = false;
   for (;;) {
+    const int kk = c->rk > 0 ? c->rdim : 0;
+    if (kk > 0) {
+      const double2* Cb = c->Vb - int64_t(kk) * n;
+      for (int i = 0; i < s; i++) {
+        double2* wi = c->Wc + int64_t(i) * n;
+        hz::launch_cgs(n, kk, Cb, n, nullptr, wi, kk, c->partial, st);
+        hz::launch_reduce(c->partial, nb, kk, c->h1, st);
+        hz::launch_cgs(n, kk, Cb, n, c->h1, wi, 0, c->partial, st);
+        hz::launch_combo(n, kk, c->Ux, n, 0, nullptr, n, c->h1, 1, c->Xc + int64_t(i) * n, n, 1.0, true, st);
+      }
+    }
     std::vector<double> rn(s);
     for (int i = 0; i < s; i++) TRY(norm2(c, c->Wc + int64_t(i) * n, rn[i]));
     bool brk0 = false;
     TRY(block_orthonormalise(c, c->Wc, s, c->Vb, beta, rn.data(), brk0));
+    const int psteps = std::max(1, m - (kk + s - 1) / s);
     H.assign(size_t(ldh) * m * s, cplx(0.0, 0.0));
+    Hr.assign(H.size(), cplx(0.0, 0.0));                       // unrotated copy
+    Bm.assign(size_t(kk) * m * s, cplx(0.0, 0.0));
     G.assign(size_t(ldh) * s, cplx(0.0, 0.0));
     for (int i = 0; i < s; i++)
       for (int r = 0; r <= i; r++) G[r + size_t(i) * ldh] = beta[r + size_t(i) * s];
     rots.clear();
     int k = 0;
-    for (int j = 0; j < m; j++) {
+    for (int j = 0; j < psteps; j++) {
       bool brk = false;
-      TRY(block_step(c, j, s, hcol, brk));
-      const int lc = (j + 2) * s;
-      for (int q = 0; q < s; q++)
-        for (int r = 0; r < lc; r++) H[r + size_t(j * s + q) * ldh] = hcol[r + size_t(q) * lc];
+      TRY(block_step(c, j, s, kk, hcol, brk));
+      const int lc = kk + (j + 2) * s;
+      for (int q = 0; q < s; q++) {
+        for (int r = 0; r < kk; r++) Bm[r + size_t(j * s + q) * kk] = hcol[r + size_t(q) * lc];
+        for (int r = 0; r < (j + 2) * s; r++)
+          H[r + size_t(j * s + q) * ldh] = Hr[r + size_t(j * s + q) * ldh] = hcol[kk + r + size_t(q) * lc];
+      }
       for (int q = 0; q < s; q++) {
         const int col = j * s + q;
         cplx* hc = H.data() + size_t(col) * ldh;
@@ -1730,6 +1827,13 @@ hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
       for (int q0 = 0; q0 < p; q0 += 64)
         hz::launch_gemv_add(n, std::min(64, p - q0), c->yblk + size_t(i) * p + q0, c->Zb + int64_t(q0) * n, n,
                             c->Xc + int64_t(i) * n, st);
+    if (kk > 0) {                                              // X -= Ux (B Y)
+      std::vector<cplx> T(size_t(kk) * s, 0.0);
+      for (int i = 0; i < s; i++)
+        for (int l = 0; l < p; l++)
+          for (int r = 0; r < kk; r++) T[r + size_t(i) * kk] += Bm[r + size_t(l) * kk] * Y[l + size_t(i) * p];
+      combo(c, kk, c->Ux, 0, nullptr, T, s, c->Xc, -1.0, true);
+    }
     // true residuals (into W, the next cycle's residual block)
     bool done = true;
     for (int i = 0; i < s; i++) {
@@ -1740,6 +1844,14 @@ hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
       rel[i] = r / bn[i];
       if (!std::isfinite(rel[i])) nonfinite = true;
       done = done && rel[i] <= tol;
+    }
+    if (c->rk > 0 && !nonfinite) {                             // the cycle's block harmonic Ritz space
+      std::vector<cplx> Hm(size_t(p + s) * p), Bp(size_t(kk) * p);
+      for (int l = 0; l < p; l++) {
+        for (int r = 0; r < p + s; r++) Hm[r + size_t(l) * (p + s)] = Hr[r + size_t(l) * ldh];
+        for (int r = 0; r < kk; r++) Bp[r + size_t(l) * kk] = Bm[r + size_t(l) * kk];
+      }
+      TRY(recycle_space(c, kk, p, s, Hm, Bp, c->Vb, c->Zb));
     }
     if (done || nonfinite || its >= c->max_iter) break;
   }
@@ -1752,12 +1864,17 @@ hz_status block_batch(hz_ctx* c, int s, double tol, hz_rhs_info* info) {
   return HZ_OK;
 }
 
-// Block FGMRES over nrhs right-hand sides in batches of S; zero columns get x = 0.
+// Block FGMRES (block GCRO-DR with recycling) over nrhs right-hand sides in batches of S;
+// zero columns get x = 0.
 hz_status solve_block(hz_ctx* c, const double2* rhs, int nrhs, double tol, double2* x, bool on_device,
                       hz_rhs_info* info, hz_status& worst) {
   const int64_t n = c->n;
   const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (c->recycle_stale) {                   // the space was built for the previous operator
+    c->recycle_stale = false;
+    if (c->rdim > 0) TRY(recycle_rebase(c));
+  }
   int next = 0;
   while (next < nrhs) {
     std::vector<int> cols;
@@ -1918,8 +2035,8 @@ static hz_status analyse(hz_ctx* c, const hz_mesh_desc* md, const hz_options* op
     return fail(c, HZ_ERR_ARG, "coarse_maxit must be in [0, 63] and coarse_tol >= 0");
   if (op->recycle < 0 || op->recycle > 16 || 2 * op->recycle > op->restart)
     return fail(c, HZ_ERR_ARG, "recycle must be in [0, min(16, restart / 2)]");
-  if (op->recycle > 0 && op->block_size > 1)
-    return fail(c, HZ_ERR_ARG, "recycle and block_size > 1 are exclusive");
+  if (op->recycle > 0 && op->block_size > 1 && op->krylov != HZ_KRYLOV_BLOCK)
+    return fail(c, HZ_ERR_ARG, "recycle with block_size > 1 needs krylov = HZ_KRYLOV_BLOCK");
   if (op->sweep_tasks < 0 || op->sweep_tasks > 2) return fail(c, HZ_ERR_ARG, "sweep_tasks must be 0, 1 or 2");
   if (op->bwd_chunk != 0 && (op->bwd_chunk < 32 || op->bwd_chunk > 512 || op->bwd_chunk % 2 != 0))
     return fail(c, HZ_ERR_ARG, "bwd_chunk must be 0 or even in [32, 512]");
@@ -2222,7 +2339,10 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
   SETUP_TRY(dalloc(c, &c->status, 1));
   if (c->S) {
     const int S = c->S;
-    SETUP_TRY(dalloc(c, &c->Vb, int64_t(S) * n * (m + 1)));
+    // block GCRO-DR keeps its recycled space C in the rk columns right before Vb
+    const int64_t vb_extra = op->krylov == HZ_KRYLOV_BLOCK ? c->rk : 0;
+    SETUP_TRY(dalloc(c, &c->Vb, int64_t(S) * n * (m + 1) + vb_extra * n));
+    if (c->Vb) c->Vb += vb_extra * n;
     SETUP_TRY(dalloc(c, &c->Zb, int64_t(S) * n * m));
     SETUP_TRY(dalloc(c, &c->Wc, int64_t(S) * n));
     SETUP_TRY(dalloc(c, &c->Bc, int64_t(S) * n));
@@ -2250,7 +2370,7 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
     c->slots.assign(S, hz_ctx::Slot{});
     c->krylov = op->krylov;
     if (c->krylov == HZ_KRYLOV_BLOCK) {
-      const int64_t nch = (int64_t(m) * S + 63) / 64;
+      const int64_t nch = (int64_t(m) * S + c->rk + 63) / 64;
       SETUP_TRY(dalloc(c, &c->hblk, 2 * nch * S * 65));
       SETUP_TRY(dalloc(c, &c->yblk, int64_t(m) * S * S));
     }
@@ -2381,7 +2501,7 @@ extern "C" hz_status hz_solve(hz_ctx* c, const void* rhs, int32_t nrhs, double t
   if (!c->factored) return fail(c, HZ_ERR_STATE, "hz_factor must run before hz_solve");
   const int64_t n = c->n;
   hz_status worst = HZ_OK;
-  if (c->S && nrhs > 1 && c->krylov == HZ_KRYLOV_BLOCK) {
+  if (c->S && c->krylov == HZ_KRYLOV_BLOCK && (nrhs > 1 || c->rk > 0)) {
     TRY(solve_block(c, (const double2*)rhs, nrhs, tol, (double2*)x, on_device != 0, info, worst));
     CU(cudaStreamSynchronize(c->st));
     return worst;
