@@ -523,8 +523,9 @@ def block_bench(args):
     """Block FGMRES against pseudo-block FGMRES on the 5 Hz workload: 16 sources from the
     16 x 8 surface grid at 50 m depth, solved with block sizes 4, 8 and 16 (16 / S batches
     of one block Krylov space each, against 16 / S rounds of S independent slots), mixed
-    precision, tol 1e-6.  One warm-up solve of the first batch, then one timed solve of
-    all 16 sources per configuration."""
+    precision, tol 1e-6.  With --recycle k a third row per block size runs block GCRO-DR
+    (the block batches share a recycled space of dimension k).  One warm-up solve of S other
+    sources of the grid, then one timed solve of the 16 sources per configuration."""
     import numpy as np
     import torch
     import synth
@@ -534,14 +535,18 @@ def block_bench(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     p = make_problem(WORKLOADS["overthrust-5hz"])
+    grid = synth.surface_source_grid()
     rows = []
+    kinds = ("pseudo", "block") + (("block-gcrodr",) if args.recycle else ())
     for S in args.block_sizes:
-        for kind in ("pseudo", "block"):
+        for kind in kinds:
             G = hz.Solver(p, precision=hz.HZ_MIXED, stream=stream, block_size=S,
-                          krylov=hz.HZ_KRYLOV_BLOCK if kind == "block" else hz.HZ_KRYLOV_PSEUDO_BLOCK)
+                          krylov=hz.HZ_KRYLOV_PSEUDO_BLOCK if kind == "pseudo" else hz.HZ_KRYLOV_BLOCK,
+                          recycle=args.recycle if kind == "block-gcrodr" else 0)
             G.factor()
-            B = torch.from_numpy(np.asfortranarray(G.point_sources(synth.surface_source_grid()[:16]))).cuda()
-            G.solve(B[:, :S].contiguous())
+            B = torch.from_numpy(np.asfortranarray(G.point_sources(grid[:16]))).cuda()
+            W = torch.from_numpy(np.asfortranarray(G.point_sources(grid[16:16 + S]))).cuda()
+            G.solve(W)
             torch.cuda.synchronize()
             t = time.perf_counter()
             X, info = G.solve(B)
@@ -550,6 +555,8 @@ def block_bench(args):
             rows.append({"block_size": S, "krylov": kind, "rhs_per_s": 16 / dt, "seconds": dt,
                          "iterations": [int(i[0]) for i in info], "ok": all(i[1] == 0 for i in info),
                          "max_rel_residual": max(i[2] for i in info)})
+            if kind == "block-gcrodr":
+                rows[-1]["recycle"] = args.recycle
             G.close()
             torch.cuda.empty_cache()
             print(json.dumps(rows[-1]), flush=True)
