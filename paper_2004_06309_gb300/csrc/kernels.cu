@@ -338,6 +338,14 @@ __global__ void __launch_bounds__(256) k_cb(const int4* tasks, const SnDev* sn, 
 // unfactored.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+// Programmatic dependent launch (the triangular sweeps, one launch per tree level): a level's
+// kernel lets the next level's grid start as soon as all of its CTAs are running
+// (launch_dependents), and the next level reads nothing of the previous levels' results
+// before griddepcontrol.wait, which returns once the previous grid has completed and its
+// writes are visible.  Loads issued before the wait touch only the factor panels and the
+// task descriptors, which no sweep writes.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t y;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
@@ -693,6 +701,7 @@ __device__ __forceinline__ void fwd_item(const int2 t, const SnDev* sn, const in
       const int j = cg + CG * q;
       pv[q] = (r < m && j < jmax) ? P[r + int64_t(j) * S.ld] : czero<V>();
     }
+    pdl_wait();
     for (int j = tid; j < k; j += blockDim.x) {
       V a = ldv(tin + S.first + j);
       for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, ldv(u + cidx[c]));
@@ -710,6 +719,7 @@ __device__ __forceinline__ void fwd_item(const int2 t, const SnDev* sn, const in
       }
     }
   } else {
+    pdl_wait();
     for (int j = tid; j < k; j += blockDim.x) {
       V a = ldv(tin + S.first + j);
       for (int64_t c = cp[j]; c < cp[j + 1]; c++) a = cadd(a, ldv(u + cidx[c]));
@@ -747,6 +757,7 @@ template <typename V, int RT>
 __global__ void __launch_bounds__(256) k_fwd(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                              const int64_t* cidx, const V* panels, const V* tin, V* zout,
                                              V* u) {
+  pdl_trigger();
   fwd_item<V, RT>(tasks[blockIdx.x], sn, cptr, cidx, panels, tin, zout, u);
 }
 
@@ -807,6 +818,7 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
                                                           const int32_t* rowlist, const double2* panels,
                                                           const double2* zin, double2* x, double2* partial,
                                                           int rows, const int4* fins, unsigned int* counters) {
+  pdl_trigger();
   __shared__ double2 vec[kBwdRows];
   __shared__ double2 red[8][33];
   const int4 t = tasks[blockIdx.x];
@@ -826,6 +838,7 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
       pre[q] = (j < k && r < rb) ? col[r] : make_double2(0.0, 0.0);
     }
   }
+  pdl_wait();
   for (int r = r0 + tid; r < r1; r += blockDim.x) vec[r - r0] = (r < k) ? zin[S.first + r] : cneg(x[rl[r]]);
   __syncthreads();
   double2 a0 = make_double2(0.0, 0.0), a1 = a0;
@@ -897,6 +910,7 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
       const int j = cg + CG * q;
       pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    pdl_wait();
     for (int jj = tid; jj < k; jj += blockDim.x) {
       float2 acc = ldv(tin + S.first + jj);
       for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, ldv(u + cidx[c]));
@@ -933,6 +947,7 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
       const int j = cg + CG * q;
       pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    pdl_wait();
     for (int jj = tid; jj < k; jj += blockDim.x) {
       float2 acc = ldv(tin + S.first + jj);
       for (int64_t c = cp[jj]; c < cp[jj + 1]; c++) acc = cadd(acc, ldv(u + cidx[c]));
@@ -994,27 +1009,47 @@ template <int CG>
 __global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnDev* sn, const int64_t* cptr,
                                                  const int64_t* cidx, const float2* panels, const float2* tin,
                                                  float2* zout, float2* u) {
+  pdl_trigger();
   fwd_c64_item<CG>(tasks[blockIdx.x], sn, cptr, cidx, panels, tin, zout, u);
 }
 
-// complex64 backward partial sums with 16-byte loads (two rows per lane).  PF (narrow
-// chunks of at most 128 rows, sparse levels): each lane's <= 2 row pairs of its 4 columns
-// are loaded before the chunk's right-hand side is gathered; the sums keep their order.
-// A supernode that fits in one chunk is finished by its own CTA (lane 0 of each column's
-// warp), with the same sums, without the partial-sum round trip and ticket of bwd_finish.
-template <bool PF>
-__global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, const SnDev* sn,
-                                                         const int32_t* rowlist, const float2* panels,
-                                                         const float2* zin, float2* x, float2* partial,
-                                                         int rows, const int4* fins, unsigned int* counters) {
+// complex64 backward partial sums with 16-byte loads (two rows per lane), two forms:
+//   kBwdAsync  (wide chunks): the first kBwdAsyncIt row pairs per lane and column are copied
+//              into shared memory by asynchronous copies (cp.async, no registers held)
+//              issued before the gather, so the panel stream starts while the gather's
+//              dependent loads are in flight; the rest of each column is loaded in the loop;
+//   kBwdPrefetch (narrow chunks of at most 128 rows, sparse levels): each lane's <= 2 row
+//              pairs of its 4 columns are loaded into registers before the gather.
+// Both keep the column loop's sums in its order.  The panel loads issued before the gather
+// do not depend on earlier levels; the kernel waits for the previous level
+// (griddepcontrol.wait, a no-op without programmatic dependent launch) only after them,
+// before its first read of x.  A supernode that fits in one chunk is finished by
+// its own CTA (lane 0 of each column's warp), with the same sums, without the partial-sum
+// round trip and ticket of bwd_finish.
+enum { kBwdAsync = 1, kBwdPrefetch = 2 };
+constexpr int kBwdAsyncIt = 2;
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == kBwdPrefetch ? 4 : 6)
+    k_bwd_partial_c64(const int4* tasks, const SnDev* sn, const int32_t* rowlist, const float2* panels,
+                      const float2* zin, float2* x, float2* partial, int rows, const int4* fins,
+                      unsigned int* counters) {
+  pdl_trigger();
   __shared__ __align__(16) float2 vec[kBwdRows + 2];
+  __shared__ __align__(16) float4 apf[MODE == kBwdAsync ? 4 * kBwdAsyncIt * 256 : 1];
   const int4 t = tasks[blockIdx.x];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = t.z * rows, r1 = min(m, r0 + rows);
   const int32_t* rl = rowlist + S.rowoff;
   float4 pre[4][2];
-  if constexpr (PF) {
+  if constexpr (MODE == kBwdPrefetch) {
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int j = t.y * 32 + wid + 8 * q;
@@ -1026,9 +1061,23 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
         pre[q][it] = (j < k && r < r1) ? col[r >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+  } else if constexpr (MODE == kBwdAsync) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int j = t.y * 32 + wid + 8 * q;
+      const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j < k ? j : 0) * S.ld);
+      const int rs = max(r0, (j + 1) & ~1);
+#pragma unroll
+      for (int it = 0; it < kBwdAsyncIt; it++) {
+        const int r = rs + 2 * lane + 64 * it;
+        if (j < k && r < r1) cp_async16(&apf[(q * kBwdAsyncIt + it) * 256 + tid], col + (r >> 1));
+      }
+    }
   }
+  pdl_wait();
   for (int r = r0 + tid; r < r0 + rows + 2; r += blockDim.x)
     vec[r - r0] = (r < r1) ? ((r < k) ? zin[S.first + r] : cneg(x[rl[r]])) : make_float2(0.f, 0.f);
+  if constexpr (MODE == kBwdAsync) cp_async_wait_all();     // each thread reads back only its own copies
   __syncthreads();
   float2* out = partial + int64_t(blockIdx.x) * 32;
   const bool single = m <= rows;                     // the only chunk: finish here, no ticket
@@ -1040,7 +1089,7 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
     float2 acc = make_float2(0.f, 0.f);
     if (j < k) {
       const int rs = max(r0, (j + 1) & ~1);          // first even row of the pair holding row j + 1
-      if constexpr (PF) {
+      if constexpr (MODE == kBwdPrefetch) {
 #pragma unroll
         for (int it = 0; it < 2; it++) {
           const int r = rs + 2 * lane + 64 * it;
@@ -1053,8 +1102,20 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c64(const int4* tasks, cons
         }
       } else {
         const float4* col = reinterpret_cast<const float4*>(panels + S.paneloff + int64_t(j) * S.ld);
+        int r = rs + 2 * lane;
+        if constexpr (MODE == kBwdAsync) {
+#pragma unroll
+          for (int it = 0; it < kBwdAsyncIt; it++, r += 64) {
+            if (r < r1) {
+              const float4 p = apf[(q * kBwdAsyncIt + it) * 256 + tid];
+              const float4 v = vec4[(r - r0) >> 1];
+              if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
+              acc = cmad(make_float2(p.z, p.w), make_float2(v.z, v.w), acc);
+            }
+          }
+        }
 #pragma unroll 4
-        for (int r = rs + 2 * lane; r < r1; r += 64) {
+        for (; r < r1; r += 64) {
           const float4 p = col[r >> 1];
           const float4 v = vec4[(r - r0) >> 1];
           if (r > j) acc = cmad(make_float2(p.x, p.y), make_float2(v.x, v.y), acc);
@@ -1087,6 +1148,31 @@ __global__ void k_prolong(int64_t n, const int64_t* pptr, const int32_t* pidx, c
   }
 }
 
+// One tree level of a sweep.  The complex64 sweeps launch with programmatic stream
+// serialisation (unless HZ_NO_PDL is set), so that a level's CTAs start their panel loads
+// while the previous level's grid drains; the kernels wait (pdl_wait) before they read any
+// result of that level.  The complex128 sweeps (FP64-bound) launch plainly: on the coarse
+// factor the early start measured slower (5.8 -> 6.2 ms per coarse solve on the 5 Hz
+// workload).
+static bool pdl_enabled(bool fp64) {
+  static const bool on = std::getenv("HZ_NO_PDL") == nullptr;
+  return on && !fp64;
+}
+template <typename... KArgs, typename... Args>
+static void launch_level(void (*kern)(KArgs...), int64_t grid, cudaStream_t st, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename V>
 static void solve_t(const FactorDev& F, cudaStream_t st) {
   const V* P = (const V*)F.panels;
@@ -1095,20 +1181,22 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
   V* x = (V*)F.x_loc;
   V* u = (V*)F.u_ws;
   V* part = (V*)F.bwd_partial;
+  const bool pdl = pdl_enabled(sizeof(V) == 16);
   if (F.level_events) cudaEventRecord(F.level_events[0], st);
   for (int l = 0; l < F.nlev; l++) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
+      const int2* tk = F.fwd_tasks + b;
       if constexpr (sizeof(V) == 8) {
         if (F.h_fwd_rt && F.h_fwd_rt[l] == 64)
-          k_fwd_c64<8><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+          launch_level(k_fwd_c64<8>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
         else
-          k_fwd_c64<2><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+          launch_level(k_fwd_c64<2>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
       } else if (F.h_fwd_rt && F.h_fwd_rt[l] == 16)
-        k_fwd<V, 16><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+        launch_level(k_fwd<V, 16>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
       else
-        k_fwd<V, 64><<<unsigned(e - b), 256, 0, st>>>(F.fwd_tasks + b, F.sn, F.cptr, F.cidx, P, t, z, u);
+        launch_level(k_fwd<V, 64>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
     }
     if (F.level_events) cudaEventRecord(F.level_events[1 + l], st);
   }
@@ -1116,25 +1204,22 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
-      if constexpr (sizeof(V) == 8)
-      {
-        const int rows = F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows;
+      const int4* tk = F.bwd_tasks + b;
+      const int rows = F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows;
+      if constexpr (sizeof(V) == 8) {
         if (rows <= 128)
-          k_bwd_partial_c64<true><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                                   rows, F.bfin_tasks, F.bwd_counters);
+          launch_level(k_bwd_partial_c64<kBwdPrefetch>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+                       F.bfin_tasks, F.bwd_counters);
         else
-          k_bwd_partial_c64<false><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x,
-                                                                    part, rows, F.bfin_tasks, F.bwd_counters);
-      }
-      else
-      {
-        const int rows = F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows;
+          launch_level(k_bwd_partial_c64<kBwdAsync>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+                       F.bfin_tasks, F.bwd_counters);
+      } else {
         if (rows <= 64)
-          k_bwd_partial_c128<true><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x, part,
-                                                                    rows, F.bfin_tasks, F.bwd_counters);
+          launch_level(k_bwd_partial_c128<true>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+                       F.bfin_tasks, F.bwd_counters);
         else
-          k_bwd_partial_c128<false><<<unsigned(e - b), 256, 0, st>>>(F.bwd_tasks + b, F.sn, F.rowlist, P, z, x,
-                                                                     part, rows, F.bfin_tasks, F.bwd_counters);
+          launch_level(k_bwd_partial_c128<false>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+                       F.bfin_tasks, F.bwd_counters);
       }
     }
     if (F.level_events) cudaEventRecord(F.level_events[1 + F.nlev + (F.nlev - 1 - l)], st);
