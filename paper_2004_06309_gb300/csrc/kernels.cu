@@ -346,6 +346,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(_
 // task descriptors, which no sweep writes.  Without the launch attribute both are no-ops.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// 16-byte asynchronous copy global -> shared (L2 only), and the wait for all of a thread's copies
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t y;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
@@ -882,8 +890,10 @@ __global__ void __launch_bounds__(256) k_bwd_partial_c128(const int4* tasks, con
 // group) on sparse levels, where a task's serial walk over its columns, not bandwidth,
 // sets the time.  In both, a thread's first 8 panel values are loaded, and the update
 // rows' child contributions b2 gathered, before the barrier that publishes b1, so the
-// load chains overlap; every sum keeps the order of the column loop (even q on one
-// chain, odd q on the other).
+// load chains overlap; with CG = 2 the next kFwdAsync values are also copied into shared
+// memory (cp.async) before the gather.  Every sum keeps the order of the column loop
+// (even q on one chain, odd q on the other).
+constexpr int kFwdAsync = 8, kFwdNarrowAsync = 8;
 template <int CG>
 __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, const int64_t* cptr,
                                              const int64_t* cidx, const float2* panels, const float2* tin,
@@ -900,7 +910,9 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
   const int rr = t.y * ROWS + tid;                   // update row finished by this thread
   float2 a0 = make_float2(0.f, 0.f), a1 = a0, c0 = a0, c1 = a0, b2 = a0;
   if constexpr (CG == 8) {
-    constexpr int MQ = kMaxK / CG, PF = 8;              // PF of the MQ columns are prefetched
+    constexpr int MQ = kMaxK / CG, PF = 8;              // PF of the MQ columns are prefetched,
+    constexpr int NA = kFwdNarrowAsync;                 // the next NA copied by cp.async
+    __shared__ __align__(16) float4 apf[NA > 0 ? NA * 256 : 1];
     float4 pv[MQ];
     const int j0 = min(r, k), j1 = min(r + 1, k);
     const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + (r < m ? r : 0));
@@ -910,6 +922,11 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
       const int j = cg + CG * q;
       pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+#pragma unroll
+    for (int q = PF; q < PF + NA; q++) {
+      const int j = cg + CG * q;
+      if (r < m && j < j1) cp_async16(&apf[(q - PF) * 256 + tid], P4 + int64_t(j) * ld4);
+    }
     pdl_wait();
     for (int jj = tid; jj < k; jj += blockDim.x) {
       float2 acc = ldv(tin + S.first + jj);
@@ -918,13 +935,15 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
     }
     if (tid < ROWS && rr >= k && rr < m)
       for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, ldv(u + cidx[c]));
+    if constexpr (NA > 0) cp_async_wait_all();        // each thread reads back only its own copies
     __syncthreads();
     if (r < m) {
 #pragma unroll
       for (int q = 0; q < MQ; q++) {
         const int j = cg + CG * q;
         if (j < j1) {
-          if (q >= PF) pv[q] = P4[int64_t(j) * ld4];
+          if (q >= PF && q < PF + NA) pv[q] = apf[(q - PF) * 256 + tid];
+          else if (q >= PF) pv[q] = P4[int64_t(j) * ld4];
           const float2 bj = b1[j];
           if (q % 2 == 0) {
             a1 = cmad(make_float2(pv[q].z, pv[q].w), bj, a1);
@@ -938,6 +957,8 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
     }
   } else {
     constexpr int PF = 8;                              // columns q < PF are prefetched
+    constexpr int NA = kFwdAsync;                      // columns PF <= q < PF + NA: cp.async
+    __shared__ __align__(16) float4 apf[NA > 0 ? NA * 256 : 1];
     float4 pv[PF];
     const int j0 = min(r, k), j1 = min(r + 1, k);
     const float4* P4 = reinterpret_cast<const float4*>(panels + S.paneloff + (r < m ? r : 0));
@@ -947,6 +968,11 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
       const int j = cg + CG * q;
       pv[q] = (r < m && j < j1) ? P4[int64_t(j) * ld4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+#pragma unroll
+    for (int q = 0; q < NA; q++) {
+      const int j = cg + CG * (PF + q);
+      if (r < m && j < j1) cp_async16(&apf[q * 256 + tid], P4 + int64_t(j) * ld4);
+    }
     pdl_wait();
     for (int jj = tid; jj < k; jj += blockDim.x) {
       float2 acc = ldv(tin + S.first + jj);
@@ -955,6 +981,7 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
     }
     if (tid < ROWS && rr >= k && rr < m)
       for (int64_t c = cp[rr]; c < cp[rr + 1]; c++) b2 = cadd(b2, ldv(u + cidx[c]));
+    if constexpr (NA > 0) cp_async_wait_all();        // each thread reads back only its own copies
     __syncthreads();
     if (r < m) {
 #pragma unroll
@@ -971,7 +998,22 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
           }
         }
       }
-      int j = cg + CG * PF;
+#pragma unroll
+      for (int q = 0; q < NA; q++) {
+        const int j = cg + CG * (PF + q);
+        if (j < j1) {
+          const float4 p = apf[q * 256 + tid];
+          const float2 bj = b1[j];
+          if ((PF + q) % 2 == 0) {
+            a1 = cmad(make_float2(p.z, p.w), bj, a1);
+            if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+          } else {
+            c1 = cmad(make_float2(p.z, p.w), bj, c1);
+            if (j < j0) c0 = cmad(make_float2(p.x, p.y), bj, c0);
+          }
+        }
+      }
+      int j = cg + CG * (PF + NA);
       for (; j + CG < j1; j += 2 * CG) {               // two independent chains
         const float4 p = P4[int64_t(j) * ld4];
         const float4 q = P4[int64_t(j + CG) * ld4];
@@ -1028,13 +1070,6 @@ __global__ void __launch_bounds__(256, 4) k_fwd_c64(const int2* tasks, const SnD
 // round trip and ticket of bwd_finish.
 enum { kBwdAsync = 1, kBwdPrefetch = 2 };
 constexpr int kBwdAsyncIt = 2;
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 template <int MODE>
 __global__ void __launch_bounds__(256, MODE == kBwdPrefetch ? 4 : 6)
     k_bwd_partial_c64(const int4* tasks, const SnDev* sn, const int32_t* rowlist, const float2* panels,
