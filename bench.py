@@ -72,7 +72,7 @@ PHASE_KERNELS = {
 }
 # DRAM traffic / panel bytes of the complex64 local sweeps (ncu, medium workload, three launches
 # each of the forward and backward sweep; an upper bound of traffic / algorithmic bytes)
-LOCAL_SWEEP_TRAFFIC_RATIO = 1.047
+LOCAL_SWEEP_TRAFFIC_RATIO = 1.055
 # Oracle samples for the CPU baseline / reference arm: same generator, 1/240 and 1/43 of the
 # 5 Hz workload's dofs.
 ORACLE_SAMPLES = {
