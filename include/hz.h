@@ -225,6 +225,14 @@ typedef struct {
   int32_t sweep_chunk;      /* rows of a wide backward chunk in use (hz_setup_mesh or
                                the sweep autotuner)                                   */
   double sweep_scale;       /* scale of the narrow-level task threshold in use          */
+  /* direct coarse factor (complex128): its triangular sweeps run on a solve tree in which
+     chains of supernodes (each the only child of the next, with nested row sets, as at
+     the top separators) are merged into solve supernodes up to 448 wide, whose panels
+     hold the inverse of the merged diagonal block; the sweeps then take one dependent
+     level per chain.  Same entries, stored beside the factor's panels.                */
+  int32_t coarse_solve_levels;   /* levels of that solve tree (nlevels_coarse: factor tree) */
+  int32_t coarse_merged_chains;  /* merged chains of two or more supernodes              */
+  int64_t coarse_merged_bytes;   /* device bytes of their panels                         */
 } hz_stats;
 
 /* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */

@@ -203,6 +203,76 @@ TreeView view_of(const hz::SymbolicSet& S) {
   return TreeView{S.nlev, S.lev_ptr.data(), S.lev_sn.data(), S.sn_k.data(), S.sn_m.data()};
 }
 
+// Solve tree of a complex128 factor: chains of supernodes in which each one is the only
+// child of the next and its rows below its pivots are exactly the next one's rows (same
+// order, checked on the row lists) merge, up to width merge_width, into one solve supernode
+// (the top separators of a nested-dissection tree form such chains).  The triangular sweeps
+// then take one dependent level per merged chain instead of one per supernode.  chain_of:
+// solve supernode of each supernode; chains: members bottom to top; the solve tree's levels
+// (a solve supernode one above its highest child) with its widths and heights.
+struct SolveTree {
+  std::vector<int32_t> chain_of;
+  std::vector<std::vector<int32_t>> chains;
+  std::vector<int32_t> k, m, lev_ptr, lev_sn;
+  int nlev = 0;
+  int64_t merged_elems = 0;           // entries of the merged panels (stored beside the factor's)
+  TreeView view() const { return TreeView{nlev, lev_ptr.data(), lev_sn.data(), k.data(), m.data()}; }
+};
+
+SolveTree plan_solve_tree(const hz::SymbolicSet& S, int precision, int merge_width) {
+  SolveTree T;
+  const int ns = int(S.sn_k.size());
+  static const bool off = std::getenv("HZ_NO_SOLVE_MERGE") != nullptr;
+  const bool merge = merge_width > 0 && precision == 0 && !off;
+  std::vector<int32_t> nchild(ns, 0), width;
+  for (int s = 0; s < ns; s++)
+    if (S.sn_parent[s] >= 0) nchild[S.sn_parent[s]]++;
+  T.chain_of.assign(ns, -1);
+  for (int s = 0; s < ns; s++) {                     // children before parents
+    if (T.chain_of[s] < 0) {
+      T.chain_of[s] = int32_t(T.chains.size());
+      T.chains.push_back({s});
+      width.push_back(S.sn_k[s]);
+    }
+    const int ch = T.chain_of[s], p = S.sn_parent[s];
+    if (!merge || p <= s || nchild[p] != 1 || T.chain_of[p] >= 0 || T.chains[ch].back() != s) continue;
+    if (S.sn_mat[p] != S.sn_mat[s] || S.sn_m[s] - S.sn_k[s] != S.sn_m[p] ||
+        S.sn_first[p] != S.sn_first[s] + S.sn_k[s] || width[size_t(ch)] + S.sn_k[p] > merge_width)
+      continue;
+    bool same = true;
+    for (int i = 0; i < S.sn_m[p] && same; i++)
+      same = S.rowlist[size_t(S.sn_rowoff[s] + S.sn_k[s] + i)] == S.rowlist[size_t(S.sn_rowoff[p] + i)];
+    if (!same) continue;
+    T.chain_of[p] = ch;
+    T.chains[size_t(ch)].push_back(p);
+    width[size_t(ch)] += S.sn_k[p];
+  }
+  const int nc = int(T.chains.size());
+  T.k.assign(nc, 0);
+  T.m.assign(nc, 0);
+  std::vector<int32_t> lev(nc, 0);
+  for (int c = 0; c < nc; c++) {                     // chains in order of their first member
+    const std::vector<int32_t>& ch = T.chains[size_t(c)];
+    T.k[size_t(c)] = width[size_t(c)];
+    T.m[size_t(c)] = S.sn_m[ch.front()];
+    if (ch.size() > 1) T.merged_elems += int64_t(T.m[size_t(c)]) * T.k[size_t(c)];
+    const int p = S.sn_parent[ch.back()];
+    if (p >= 0) {
+      const int pc = T.chain_of[p];
+      lev[size_t(pc)] = std::max(lev[size_t(pc)], lev[size_t(c)] + 1);
+    }
+  }
+  for (int c = 0; c < nc; c++) T.nlev = std::max(T.nlev, lev[size_t(c)] + 1);
+  if (nc == 0) T.nlev = 0;
+  T.lev_ptr.assign(T.nlev + 1, 0);
+  for (int c = 0; c < nc; c++) T.lev_ptr[size_t(lev[size_t(c)]) + 1]++;
+  for (int l = 0; l < T.nlev; l++) T.lev_ptr[size_t(l) + 1] += T.lev_ptr[size_t(l)];
+  T.lev_sn.assign(nc, 0);
+  std::vector<int32_t> fill(T.lev_ptr.begin(), T.lev_ptr.end() - (T.nlev > 0 ? 1 : 0));
+  for (int c = 0; c < nc; c++) T.lev_sn[size_t(fill[size_t(lev[size_t(c)])]++)] = c;
+  return T;
+}
+
 // sparse_scale multiplies the task count below which a level gets narrow tasks (the
 // sweep autotuner's knob; 1 = the defaults above).
 SweepPlan plan_sweeps(const TreeView& S, int precision, int bwd_rows, int sweep_tasks, double sparse_scale = 1.0) {
@@ -381,7 +451,8 @@ hz_status tune_sweeps(hz_ctx* c, hz::FactorDev& F) {
 
 // sweep_tasks / bwd_chunk: hz_options fields of the same names (task shapes per level).
 hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
-                        double maxabs[3], int bwd_rows, int nrhs_block, int sweep_tasks, int bwd_chunk) {
+                        double maxabs[3], int bwd_rows, int nrhs_block, int sweep_tasks, int bwd_chunk,
+                        int merge_width = 0) {
   F = hz::FactorDev();
   if (bwd_chunk > 0) bwd_rows = bwd_chunk;
   F.bwd_rows = bwd_rows;
@@ -417,6 +488,40 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   F.panel_elems = panel_off;
   const size_t vs = precision == 0 ? 16 : 8;
   TRY(upload(c, &F.sn, sn));
+  // the solve tree: merged chains get their own panels after the factor's, filled at the end
+  // of each factorisation (launch_merge_panels)
+  const SolveTree ST = plan_solve_tree(S, precision, merge_width);
+  {
+    std::vector<hz::SnDev> ssn(ST.chains.size());
+    int64_t off = panel_off;
+    F.merges.clear();
+    F.merge_tmp_elems = 0;
+    for (size_t ci = 0; ci < ST.chains.size(); ci++) {
+      const std::vector<int32_t>& ch = ST.chains[ci];
+      if (ch.size() == 1) {
+        ssn[ci] = sn[size_t(ch[0])];
+        continue;
+      }
+      hz::SnDev& d = ssn[ci];
+      d = sn[size_t(ch.front())];
+      d.k = ST.k[ci];
+      d.m = ST.m[ci];
+      d.ld = d.m;
+      d.parent = S.sn_parent[ch.back()];
+      d.uoff = S.sn_uoff[ch.back()];
+      d.paneloff = off;
+      int w = 0;
+      for (int32_t s : ch) {
+        F.merges.push_back({off, sn[size_t(s)].paneloff, d.m, w, sn[size_t(s)].ld, S.sn_k[s], S.sn_m[s]});
+        F.merge_tmp_elems = std::max(F.merge_tmp_elems, int64_t(S.sn_k[s]) * w);
+        w += S.sn_k[s];
+      }
+      off += int64_t(d.ld) * d.k;
+    }
+    F.solve_panel_elems = off;
+    F.snlev = ST.nlev;
+    TRY(upload(c, &F.ssn, ssn));
+  }
   TRY(upload(c, &F.rowlist, S.rowlist));
   TRY(upload(c, &F.cptr, S.cptr));
   TRY(upload(c, &F.cidx, S.cidx));
@@ -501,16 +606,17 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     void enter(int g, int64_t size) { while (next <= g) out[base + next++] = size; }
     void finish(int64_t size) { while (next <= G) out[base + next++] = size; }
   };
-  const SweepPlan sp = plan_sweeps(view_of(S), precision, bwd_rows, sweep_tasks);
+  const SweepPlan sp = plan_sweeps(ST.view(), precision, bwd_rows, sweep_tasks);
+  const SweepPlan spf = plan_sweeps(view_of(S), precision, bwd_rows, sweep_tasks);   // factor-side counts
   F.v_fwd_wide = sp.fwd_wide;
   F.v_fwd_narrow = sp.fwd_narrow;
   F.v_bwd_wide = sp.bwd_wide;
   F.v_bwd_narrow = sp.bwd_narrow;
   F.v_bwd_split = sp.bwd_split;
-  F.v_tc_tiles = sp.tc_tiles;
-  F.v_tc_multi = sp.tc_multi;
-  F.v_tc_kstages = sp.tc_kstages;
-  F.v_max_k = sp.max_k;
+  F.v_tc_tiles = spf.tc_tiles;
+  F.v_tc_multi = spf.tc_multi;
+  F.v_tc_kstages = spf.tc_kstages;
+  F.v_max_k = spf.max_k;
   for (int l = 0; l < nlev; l++) {
     lev_ptr[l] = S.lev_ptr[l];
     wg_ptr[l] = int64_t(wg.size());
@@ -602,11 +708,11 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
     }
     return v;
   }());
-  // the tree as the sweep schedule sees it, kept for the sweep autotuner
-  F.t_lev_ptr = S.lev_ptr;
-  F.t_lev_sn = S.lev_sn;
-  F.t_sn_k = S.sn_k;
-  F.t_sn_m = S.sn_m;
+  // the (solve) tree as the sweep schedule sees it, kept for the sweep autotuner
+  F.t_lev_ptr = ST.lev_ptr;
+  F.t_lev_sn = ST.lev_sn;
+  F.t_sn_k = ST.k;
+  F.t_sn_m = ST.m;
   TRY(build_sweep_tasks(c, F, sp));
   F.sweep_chunk = bwd_rows;
   F.sweep_scale = 1.0;
@@ -659,7 +765,8 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   }
   // numeric storage and solve workspaces
   void *pan = nullptr, *tl = nullptr, *zl = nullptr, *xl = nullptr, *uw = nullptr;
-  TRY(dalloc(c, (char**)&pan, F.panel_elems * int64_t(vs)));
+  TRY(dalloc(c, (char**)&pan, F.solve_panel_elems * int64_t(vs)));
+  if (F.merge_tmp_elems > 0) TRY(dalloc(c, (char**)&F.merge_tmp, F.merge_tmp_elems * int64_t(vs)));
   TRY(dalloc(c, (char**)&tl, F.ntot * int64_t(vs)));
   TRY(dalloc(c, (char**)&zl, F.ntot * int64_t(vs)));
   TRY(dalloc(c, (char**)&xl, F.ntot * int64_t(vs)));
@@ -726,6 +833,7 @@ hz_status factor_one(hz_ctx* c, hz::FactorDev& F, double w, const double maxabs[
   }
   for (int g = 0; g < F.ngrp; g++)                 // groups one after the other in one workspace
     for (int l = 0; l < F.nlev; l++) hz::launch_factor_level(F, l, g, w, fronts, scratch, c->status, tiny, c->st);
+  hz::launch_merge_panels(F, c->st);              // merged solve supernodes of the sweeps
   if (verbose) {
     cudaStreamSynchronize(c->st);
     std::fprintf(stderr, "[hz] factor: %d levels in %.3f s\n", F.nlev,
@@ -2167,6 +2275,15 @@ static void fill_stats(hz_ctx* c, const hz::HostProblem& P) {
   const int64_t vs = c->opt.precision == HZ_FP64 ? 16 : 8;
   s.front_bytes = std::max({P.local.front_elems * vs, P.coarse.front_elems * 16, P.clocal.front_elems * vs});
   s.factor_flops = P.local.flops;
+  s.coarse_solve_levels = s.nlevels_coarse;
+  s.coarse_merged_chains = 0;
+  s.coarse_merged_bytes = 0;
+  if (!it && !P.coarse.voff.empty()) {
+    const SolveTree T = plan_solve_tree(P.coarse, 0, hz::kMaxSolveK);
+    s.coarse_solve_levels = T.nlev;
+    for (const auto& ch : T.chains) s.coarse_merged_chains += ch.size() > 1;
+    s.coarse_merged_bytes = T.merged_elems * 16;
+  }
 }
 
 extern "C" hz_status hz_plan(const hz_mesh_desc* md, const hz_options* op, hz_stats* out) {
@@ -2292,7 +2409,7 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
       SETUP_TRY(dalloc(c, &c->brkH, 1));
     } else {
       SETUP_TRY(upload_factor(c, P.coarse, 0, c->nH, c->crs, c->crs_max, 256, c->S, op->sweep_tasks,
-                              op->bwd_chunk));
+                              op->bwd_chunk, hz::kMaxSolveK));
     }
     SETUP_TRY(dalloc(c, &c->rH, c->nH));
     SETUP_TRY(dalloc(c, &c->yH, c->nH));
@@ -2667,17 +2784,17 @@ extern "C" hz_status hz_profile(hz_ctx* c, int32_t reps, hz_profile_out* out) {
       hz::FactorDev& F = *Fp;
       if (F.nsn == 0) continue;
       const char* name = Fp == &c->loc ? "local" : "coarse";
-      std::vector<cudaEvent_t> ev(size_t(2 * F.nlev + 1));
+      std::vector<cudaEvent_t> ev(size_t(2 * F.snlev + 1));
       for (auto& e : ev) cudaEventCreate(&e);
       F.level_events = ev.data();
       hz::launch_solve(F, st);
       F.level_events = nullptr;
       cudaStreamSynchronize(st);
-      for (int q = 0; q < 2 * F.nlev; q++) {
+      for (int q = 0; q < 2 * F.snlev; q++) {
         float ms = 0;
         cudaEventElapsedTime(&ms, ev[size_t(q)], ev[size_t(q) + 1]);
-        const bool fw = q < F.nlev;
-        const int l = fw ? q : 2 * F.nlev - 1 - q;
+        const bool fw = q < F.snlev;
+        const int l = fw ? q : 2 * F.snlev - 1 - q;
         const int64_t nt = fw ? F.h_fwd_ptr[l + 1] - F.h_fwd_ptr[l] : F.h_bwd_ptr[l + 1] - F.h_bwd_ptr[l];
         std::fprintf(stderr, "[hz] %s %s level %3d: %6lld tasks %9.1f us\n", name, fw ? "fwd" : "bwd", l,
                      (long long)nt, 1e3 * ms);
@@ -2793,6 +2910,8 @@ void plan_bytes(const hz::HostProblem& P, const hz_options& op, int64_t& persist
   b += P.local.panel_elems * vs + (3 * P.local.voff.back() + P.local.u_elems) * vs;
   b += int64_t(P.local.rowlist.size()) * 4 + int64_t(P.local.cidx.size()) * 8 + int64_t(P.local.epos.size()) * 40;
   b += P.coarse.panel_elems * 16;
+  if (!P.coarse.voff.empty() && P.clocal.voff.empty())
+    b += plan_solve_tree(P.coarse, 0, hz::kMaxSolveK).merged_elems * 16;          // merged solve panels
   if (!P.coarse.voff.empty())
     b += (3 * P.coarse.voff.back() + P.coarse.u_elems) * 16 + int64_t(P.coarse.epos.size()) * 40;
   if (!P.clocal.voff.empty()) {

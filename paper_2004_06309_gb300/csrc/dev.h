@@ -8,6 +8,9 @@
 namespace hz {
 
 // One supernode of a batched multifrontal factorisation (56 bytes).
+// widest merged solve supernode of the complex128 sweeps (see FactorDev::ssn)
+constexpr int kMaxSolveK = 448;
+
 struct SnDev {
   int32_t k, m, first, parent;   // pivots, front order, first vector index, parent (-1 root)
   int32_t ld, pad_;              // panel leading dimension (m, or m rounded up to 4 for complex64)
@@ -24,6 +27,24 @@ struct FactorDev {
   int32_t bwd_rows = 512;        // rows per backward partial task (<= 512)
   int64_t ntot = 0, nrows = 0, panel_elems = 0, u_elems = 0, front_elems = 0, nentries = 0;
   SnDev* sn = nullptr;
+  // single-right-hand-side sweeps: supernodes of the solve tree, in which chains of
+  // supernodes (each the only child of the next, with nested row sets) are merged into one
+  // solve supernode whose panel (appended after the factor panels, panel_elems onwards)
+  // holds the inverse of the merged unit lower diagonal block and the matching off-diagonal
+  // block; equal to sn where nothing is merged.  snlev: levels of the solve tree.
+  SnDev* ssn = nullptr;
+  int snlev = 0;
+  int64_t solve_panel_elems = 0;      // panel_elems plus the merged solve panels
+  // merge steps, in order: the solve supernode's panel (offset, ld = its rows), its width
+  // so far w, and the appended original supernode's panel (offset, ld, k_s, m_s); and the
+  // scratch for one step's k_s x w block
+  struct MergeStep {
+    int64_t moff, soff;
+    int32_t ldm, w, lds, ks, ms;
+  };
+  std::vector<MergeStep> merges;
+  int64_t merge_tmp_elems = 0;
+  void* merge_tmp = nullptr;
   int32_t* rowlist = nullptr;
   int64_t* cptr = nullptr;
   int64_t* cidx = nullptr;
@@ -165,6 +186,8 @@ void launch_factor_level(const FactorDev& F, int lev, int grp, double w, void* f
 
 void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st);
 void launch_solve(const FactorDev& F, cudaStream_t st);
+// Builds the merged solve panels from the factor panels (after the last factor level).
+void launch_merge_panels(const FactorDev& F, cudaStream_t st);
 void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st);
 
 void launch_local_multi(const FactorDev& F, int S, const double2* src, const double2* y, double2* dst,

@@ -689,7 +689,7 @@ template <typename V, int RT>
 __device__ __forceinline__ void fwd_item(const int2 t, const SnDev* sn, const int64_t* cptr, const int64_t* cidx,
                                          const V* panels, const V* tin, V* zout, V* u) {
   constexpr int CG = 256 / RT;
-  __shared__ V b1[kMaxK];
+  __shared__ V b1[kMaxSolveK];
   __shared__ V part[CG][RT];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
@@ -725,6 +725,13 @@ __device__ __forceinline__ void fwd_item(const int2 t, const SnDev* sn, const in
           else acc2 = cmad(pv[q], b1[j], acc2);
         }
       }
+      // merged solve supernodes wider than kMaxK: the remaining columns, same chains
+      int j = cg + CG * MQ;
+      for (; j + CG < jmax; j += 2 * CG) {
+        acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
+        acc2 = cmad(P[r + int64_t(j + CG) * S.ld], b1[j + CG], acc2);
+      }
+      if (j < jmax) acc = cmad(P[r + int64_t(j) * S.ld], b1[j], acc);
     }
   } else {
     pdl_wait();
@@ -1216,26 +1223,27 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
   V* x = (V*)F.x_loc;
   V* u = (V*)F.u_ws;
   V* part = (V*)F.bwd_partial;
+  const SnDev* SN = F.ssn ? F.ssn : F.sn;
   const bool pdl = pdl_enabled(sizeof(V) == 16);
   if (F.level_events) cudaEventRecord(F.level_events[0], st);
-  for (int l = 0; l < F.nlev; l++) {
+  for (int l = 0; l < F.snlev; l++) {
     const int64_t b = F.h_fwd_ptr[l], e = F.h_fwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
       const int2* tk = F.fwd_tasks + b;
       if constexpr (sizeof(V) == 8) {
         if (F.h_fwd_rt && F.h_fwd_rt[l] == 64)
-          launch_level(k_fwd_c64<8>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
+          launch_level(k_fwd_c64<8>, e - b, st, pdl, tk, SN, F.cptr, F.cidx, P, t, z, u);
         else
-          launch_level(k_fwd_c64<2>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
+          launch_level(k_fwd_c64<2>, e - b, st, pdl, tk, SN, F.cptr, F.cidx, P, t, z, u);
       } else if (F.h_fwd_rt && F.h_fwd_rt[l] == 16)
-        launch_level(k_fwd<V, 16>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
+        launch_level(k_fwd<V, 16>, e - b, st, pdl, tk, SN, F.cptr, F.cidx, P, t, z, u);
       else
-        launch_level(k_fwd<V, 64>, e - b, st, pdl, tk, F.sn, F.cptr, F.cidx, P, t, z, u);
+        launch_level(k_fwd<V, 64>, e - b, st, pdl, tk, SN, F.cptr, F.cidx, P, t, z, u);
     }
     if (F.level_events) cudaEventRecord(F.level_events[1 + l], st);
   }
-  for (int l = F.nlev - 1; l >= 0; l--) {
+  for (int l = F.snlev - 1; l >= 0; l--) {
     const int64_t b = F.h_bwd_ptr[l], e = F.h_bwd_ptr[l + 1];
     if (e > b) {
       HZ_COUNT();
@@ -1243,21 +1251,21 @@ static void solve_t(const FactorDev& F, cudaStream_t st) {
       const int rows = F.h_bwd_rows ? F.h_bwd_rows[l] : F.bwd_rows;
       if constexpr (sizeof(V) == 8) {
         if (rows <= 128)
-          launch_level(k_bwd_partial_c64<kBwdPrefetch>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+          launch_level(k_bwd_partial_c64<kBwdPrefetch>, e - b, st, pdl, tk, SN, F.rowlist, P, z, x, part, rows,
                        F.bfin_tasks, F.bwd_counters);
         else
-          launch_level(k_bwd_partial_c64<kBwdAsync>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+          launch_level(k_bwd_partial_c64<kBwdAsync>, e - b, st, pdl, tk, SN, F.rowlist, P, z, x, part, rows,
                        F.bfin_tasks, F.bwd_counters);
       } else {
         if (rows <= 64)
-          launch_level(k_bwd_partial_c128<true>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+          launch_level(k_bwd_partial_c128<true>, e - b, st, pdl, tk, SN, F.rowlist, P, z, x, part, rows,
                        F.bfin_tasks, F.bwd_counters);
         else
-          launch_level(k_bwd_partial_c128<false>, e - b, st, pdl, tk, F.sn, F.rowlist, P, z, x, part, rows,
+          launch_level(k_bwd_partial_c128<false>, e - b, st, pdl, tk, SN, F.rowlist, P, z, x, part, rows,
                        F.bfin_tasks, F.bwd_counters);
       }
     }
-    if (F.level_events) cudaEventRecord(F.level_events[1 + F.nlev + (F.nlev - 1 - l)], st);
+    if (F.level_events) cudaEventRecord(F.level_events[1 + F.snlev + (F.snlev - 1 - l)], st);
   }
 }
 
@@ -1275,6 +1283,114 @@ void launch_gather(const FactorDev& F, const double2* src, cudaStream_t st) {
 void launch_solve(const FactorDev& F, cudaStream_t st) {
   if (F.precision == 0) solve_t<double2>(F, st);
   else solve_t<float2>(F, st);
+}
+
+// ---------------------------------------------------------------------------
+// merged solve supernodes (complex128 factors): a chain s_1 -> s_2 -> ... in which each
+// supernode is the only child of the next and its rows below its pivots are exactly the
+// next one's rows.  A supernode's panel holds T = L11^{-1} (strict lower part; D^{-1} on the
+// diagonal) over G = L21 L11^{-1}.  Appending s (T_s, G_s) to the merged M (T_M, G_M, width
+// w, rows P_M, P_s, R_s in that order) gives
+//   T' = [[T_M, 0], [-T_s A, T_s]],  G' = [G_M(R_s) - G_s A, G_s],  A = G_M(P_s rows),
+// from the block inverse of [[L11^M, 0], [L(P_s, P_M), L11^s]] (T_s taken with a unit
+// diagonal in the product).  Same entries, so the sweep reads the same bytes, in fewer
+// dependent levels.
+// ---------------------------------------------------------------------------
+// tmp (ks x w, column-major) = M[w .. w + ks, 0 .. w)
+__global__ void k_merge_save(const double2* M, int ldm, int w, int ks, double2* tmp) {
+  const int64_t n = int64_t(ks) * w;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    const int q = int(e % ks), c = int(e / ks);
+    tmp[e] = M[(w + q) + int64_t(ldm) * c];
+  }
+}
+
+// M[w + i, c] = (i >= ks ? M[w + i, c] : 0) - sum_q C(i, q) tmp[q, c] for i < ms, c < w, with
+// C = [T_s (unit diagonal, upper part 0); G_s] the appended panel.  64 x 32 output tiles,
+// 16-deep slices of q staged in shared memory; each thread owns 4 rows x 2 columns.
+__global__ void __launch_bounds__(256) k_merge_update(double2* M, int ldm, int w, const double2* Ps, int lds,
+                                                      int ks, int ms, const double2* tmp) {
+  __shared__ double2 Cs[16][64];
+  __shared__ double2 As[16][32];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int i0 = blockIdx.x * 64, c0 = blockIdx.y * 32;
+  double2 acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 2; b++) acc[a][b] = make_double2(0.0, 0.0);
+  for (int q0 = 0; q0 < ks; q0 += 16) {
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      const int e = tid + 256 * t, il = e & 63, ql = e >> 6;
+      const int i = i0 + il, q = q0 + ql;
+      double2 v = make_double2(0.0, 0.0);
+      if (i < ms && q < ks) {
+        if (i >= ks || i > q) v = Ps[i + int64_t(lds) * q];
+        else if (i == q) v = make_double2(1.0, 0.0);
+      }
+      Cs[ql][il] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+      const int e = tid + 256 * t, ql = e & 15, cl = e >> 4;
+      const int q = q0 + ql, c = c0 + cl;
+      As[ql][cl] = (q < ks && c < w) ? tmp[q + int64_t(ks) * c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ql = 0; ql < 16; ql++) {
+      double2 b0 = As[ql][2 * tx], b1 = As[ql][2 * tx + 1];
+#pragma unroll
+      for (int a = 0; a < 4; a++) {
+        const double2 cv = Cs[ql][4 * ty + a];
+        acc[a][0] = cmad(cv, b0, acc[a][0]);
+        acc[a][1] = cmad(cv, b1, acc[a][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int i = i0 + 4 * ty + a;
+    if (i >= ms) continue;
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+      const int c = c0 + 2 * tx + b;
+      if (c >= w) continue;
+      double2* o = M + (w + i) + int64_t(ldm) * c;
+      const double2 base = i >= ks ? *o : make_double2(0.0, 0.0);
+      *o = make_double2(base.x - acc[a][b].x, base.y - acc[a][b].y);
+    }
+  }
+}
+
+// M[w + i, w + q] = Ps[i, q] for i < ms, q < ks
+__global__ void k_merge_put(double2* M, int ldm, int w, const double2* Ps, int lds, int ks, int ms) {
+  const int64_t n = int64_t(ks) * ms;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(e % ms), q = int(e / ms);
+    M[(w + i) + int64_t(ldm) * (w + q)] = Ps[i + int64_t(lds) * q];
+  }
+}
+
+void launch_merge_panels(const FactorDev& F, cudaStream_t st) {
+  if (F.merges.empty() || F.precision != 0) return;
+  double2* P = (double2*)F.panels;
+  double2* tmp = (double2*)F.merge_tmp;
+  for (const FactorDev::MergeStep& m : F.merges) {
+    double2* M = P + m.moff;
+    const double2* Ps = P + m.soff;
+    if (m.w > 0) {
+      HZ_COUNT();
+      k_merge_save<<<grid_for(int64_t(m.ks) * m.w, 256), 256, 0, st>>>(M, m.ldm, m.w, m.ks, tmp);
+      HZ_COUNT();
+      k_merge_update<<<dim3(unsigned((m.ms + 63) / 64), unsigned((m.w + 31) / 32)), 256, 0, st>>>(
+          M, m.ldm, m.w, Ps, m.lds, m.ks, m.ms, tmp);
+    }
+    HZ_COUNT();
+    k_merge_put<<<grid_for(int64_t(m.ks) * m.ms, 256), 256, 0, st>>>(M, m.ldm, m.w, Ps, m.lds, m.ks, m.ms);
+  }
 }
 
 void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st) {

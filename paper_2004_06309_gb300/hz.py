@@ -75,6 +75,8 @@ class Stats(C.Structure):
         ("bwd_levels_narrow", C.c_int32), ("bwd_split_blocks", C.c_int64), ("tc_tiles", C.c_int64),
         ("tc_multi_fronts", C.c_int64), ("tc_max_kstages", C.c_int32), ("max_snode_width", C.c_int32),
         ("sweep_chunk", C.c_int32), ("sweep_scale", C.c_double),
+        ("coarse_solve_levels", C.c_int32), ("coarse_merged_chains", C.c_int32),
+        ("coarse_merged_bytes", C.c_int64),
     ]
 
     def as_dict(self):

@@ -148,3 +148,20 @@ def test_dense_eig_real_pairs_diagonal_and_bad_input(hzmod):
     with pytest.raises(hzmod.HzError) as e:
         hzmod.dense_eig(bad)
     assert e.value.status == hzmod.HZ_ERR_BREAKDOWN
+
+
+def test_coarse_solve_tree_merges_the_separator_chains(hzmod):
+    """The direct coarse factor's sweeps run on a solve tree with the supernode chains at the
+    top separators merged: fewer levels than the factor tree, merged widths within 448, the
+    merged panels counted in the planned device bytes; the iterative coarse solve has no
+    direct factor and merges nothing."""
+    import bench
+    p = bench.make_problem(bench.WORKLOADS["overthrust-small"])
+    st = hzmod.plan(p, precision=hzmod.HZ_MIXED)
+    assert st["coarse_merged_chains"] > 0
+    assert 0 < st["coarse_solve_levels"] < st["nlevels_coarse"], st
+    # a merged chain's panel holds at most 448 columns of n_coarse rows
+    assert 0 < st["coarse_merged_bytes"] <= st["coarse_merged_chains"] * 448 * st["n_coarse"] * 16
+    it = hzmod.plan(p, precision=hzmod.HZ_MIXED, coarse_solver=hzmod.HZ_COARSE_ORAS)
+    assert it["coarse_merged_chains"] == 0 and it["coarse_merged_bytes"] == 0
+    assert it["coarse_solve_levels"] == it["nlevels_coarse"]

@@ -191,7 +191,7 @@ def test_sweep_autotuner_keeps_parity(hzmod, case, prec):
     finally:
         G.close()
     assert st["sweep_chunk"] in ((256, 512) if prec == "mixed" else (128, 256))
-    assert st["sweep_scale"] in (0.5, 1.0, 2.0)
+    assert st["sweep_scale"] in (0.25, 0.5, 1.0, 2.0)
     err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
     assert err <= (1e-10 if prec == "fp64" else kappa * U32), err
     assert info[0][1] == 0 and np.linalg.norm(b - S.A @ x) / np.linalg.norm(b) <= p.tol
