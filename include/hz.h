@@ -233,6 +233,12 @@ typedef struct {
   int32_t coarse_solve_levels;   /* levels of that solve tree (nlevels_coarse: factor tree) */
   int32_t coarse_merged_chains;  /* merged chains of two or more supernodes              */
   int64_t coarse_merged_bytes;   /* device bytes of their panels                         */
+  /* the same for the subdomain factors, whose chains merge (up to 512 wide in complex64,
+     448 in complex128) on the sparse top levels of the batched trees, where each level
+     holds at most two supernodes per subdomain                                        */
+  int32_t solve_levels;          /* levels of the subdomains' solve tree (nlevels: factor) */
+  int32_t merged_chains;
+  int64_t merged_bytes;
 } hz_stats;
 
 /* Phases of one preconditioned FGMRES iteration, as timed by hz_profile. */

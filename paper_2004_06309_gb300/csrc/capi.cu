@@ -219,11 +219,18 @@ struct SolveTree {
   TreeView view() const { return TreeView{nlev, lev_ptr.data(), lev_sn.data(), k.data(), m.data()}; }
 };
 
-SolveTree plan_solve_tree(const hz::SymbolicSet& S, int precision, int merge_width) {
+// Merge parameters of the subdomain factors: width by precision; only the sparse top
+// levels (at most two supernodes per subdomain), which bounds the duplicated panel bytes.
+int local_merge_width(int precision) { return precision == 1 ? hz::kMaxSolveK64 : hz::kMaxSolveK; }
+int local_merge_sparse(const hz::SymbolicSet& S) { return 2 * S.nmat; }
+
+// sparse_max > 0: a supernode joins a chain only if its factor level holds at most that
+// many supernodes (the top of a batch of trees: about one separator chain per matrix).
+SolveTree plan_solve_tree(const hz::SymbolicSet& S, int merge_width, int sparse_max = 0) {
   SolveTree T;
   const int ns = int(S.sn_k.size());
   static const bool off = std::getenv("HZ_NO_SOLVE_MERGE") != nullptr;
-  const bool merge = merge_width > 0 && precision == 0 && !off;
+  const bool merge = merge_width > 0 && !off;
   std::vector<int32_t> nchild(ns, 0), width;
   for (int s = 0; s < ns; s++)
     if (S.sn_parent[s] >= 0) nchild[S.sn_parent[s]]++;
@@ -236,6 +243,9 @@ SolveTree plan_solve_tree(const hz::SymbolicSet& S, int precision, int merge_wid
     }
     const int ch = T.chain_of[s], p = S.sn_parent[s];
     if (!merge || p <= s || nchild[p] != 1 || T.chain_of[p] >= 0 || T.chains[ch].back() != s) continue;
+    if (sparse_max > 0 && (S.lev_ptr[size_t(S.sn_level[s]) + 1] - S.lev_ptr[size_t(S.sn_level[s])] > sparse_max ||
+                           S.lev_ptr[size_t(S.sn_level[p]) + 1] - S.lev_ptr[size_t(S.sn_level[p])] > sparse_max))
+      continue;
     if (S.sn_mat[p] != S.sn_mat[s] || S.sn_m[s] - S.sn_k[s] != S.sn_m[p] ||
         S.sn_first[p] != S.sn_first[s] + S.sn_k[s] || width[size_t(ch)] + S.sn_k[p] > merge_width)
       continue;
@@ -452,7 +462,7 @@ hz_status tune_sweeps(hz_ctx* c, hz::FactorDev& F) {
 // sweep_tasks / bwd_chunk: hz_options fields of the same names (task shapes per level).
 hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int64_t nglob, hz::FactorDev& F,
                         double maxabs[3], int bwd_rows, int nrhs_block, int sweep_tasks, int bwd_chunk,
-                        int merge_width = 0) {
+                        int merge_width = 0, int merge_sparse = 0) {
   F = hz::FactorDev();
   if (bwd_chunk > 0) bwd_rows = bwd_chunk;
   F.bwd_rows = bwd_rows;
@@ -490,7 +500,7 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
   TRY(upload(c, &F.sn, sn));
   // the solve tree: merged chains get their own panels after the factor's, filled at the end
   // of each factorisation (launch_merge_panels)
-  const SolveTree ST = plan_solve_tree(S, precision, merge_width);
+  const SolveTree ST = plan_solve_tree(S, merge_width, merge_sparse);
   {
     std::vector<hz::SnDev> ssn(ST.chains.size());
     int64_t off = panel_off;
@@ -506,13 +516,13 @@ hz_status upload_factor(hz_ctx* c, const hz::SymbolicSet& S, int precision, int6
       d = sn[size_t(ch.front())];
       d.k = ST.k[ci];
       d.m = ST.m[ci];
-      d.ld = d.m;
+      d.ld = precision == 0 ? d.m : (d.m + 3) / 4 * 4;     // complex64: 16-byte aligned row pairs
       d.parent = S.sn_parent[ch.back()];
       d.uoff = S.sn_uoff[ch.back()];
       d.paneloff = off;
       int w = 0;
       for (int32_t s : ch) {
-        F.merges.push_back({off, sn[size_t(s)].paneloff, d.m, w, sn[size_t(s)].ld, S.sn_k[s], S.sn_m[s]});
+        F.merges.push_back({off, sn[size_t(s)].paneloff, d.ld, w, sn[size_t(s)].ld, S.sn_k[s], S.sn_m[s]});
         F.merge_tmp_elems = std::max(F.merge_tmp_elems, int64_t(S.sn_k[s]) * w);
         w += S.sn_k[s];
       }
@@ -2278,8 +2288,16 @@ static void fill_stats(hz_ctx* c, const hz::HostProblem& P) {
   s.coarse_solve_levels = s.nlevels_coarse;
   s.coarse_merged_chains = 0;
   s.coarse_merged_bytes = 0;
+  {
+    const int prec = c->opt.precision == HZ_MIXED ? 1 : 0;
+    const SolveTree T = plan_solve_tree(P.local, local_merge_width(prec), local_merge_sparse(P.local));
+    s.solve_levels = T.nlev;
+    s.merged_chains = 0;
+    for (const auto& ch : T.chains) s.merged_chains += ch.size() > 1;
+    s.merged_bytes = T.merged_elems * vs;
+  }
   if (!it && !P.coarse.voff.empty()) {
-    const SolveTree T = plan_solve_tree(P.coarse, 0, hz::kMaxSolveK);
+    const SolveTree T = plan_solve_tree(P.coarse, hz::kMaxSolveK);
     s.coarse_solve_levels = T.nlev;
     for (const auto& ch : T.chains) s.coarse_merged_chains += ch.size() > 1;
     s.coarse_merged_bytes = T.merged_elems * 16;
@@ -2301,17 +2319,19 @@ extern "C" hz_status hz_plan(const hz_mesh_desc* md, const hz_options* op, hz_st
   {
     const int prec = op->precision == HZ_MIXED ? 1 : 0;
     const int rows = op->bwd_chunk > 0 ? op->bwd_chunk : (prec == 1 ? 512 : 256);
-    const SweepPlan sp = plan_sweeps(view_of(P.local), prec, rows, op->sweep_tasks);
+    const SolveTree T = plan_solve_tree(P.local, local_merge_width(prec), local_merge_sparse(P.local));
+    const SweepPlan sp = plan_sweeps(T.view(), prec, rows, op->sweep_tasks);     // the sweeps' tree
+    const SweepPlan spf = plan_sweeps(view_of(P.local), prec, rows, op->sweep_tasks);   // the factor's
     hz_stats& st = tmp.stats;
     st.fwd_levels_wide = sp.fwd_wide;
     st.fwd_levels_narrow = sp.fwd_narrow;
     st.bwd_levels_wide = sp.bwd_wide;
     st.bwd_levels_narrow = sp.bwd_narrow;
     st.bwd_split_blocks = sp.bwd_split;
-    st.tc_tiles = sp.tc_tiles;
-    st.tc_multi_fronts = sp.tc_multi;
-    st.tc_max_kstages = sp.tc_kstages;
-    st.max_snode_width = sp.max_k;
+    st.tc_tiles = spf.tc_tiles;
+    st.tc_multi_fronts = spf.tc_multi;
+    st.tc_max_kstages = spf.tc_kstages;
+    st.max_snode_width = spf.max_k;
   }
   tmp.stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   // device bytes a context would hold after hz_factor (excluding transient fronts)
@@ -2360,7 +2380,8 @@ static hz_status populate(hz_ctx* c, hz::HostProblem& P, int order, const hz_opt
     }
   }
   SETUP_TRY(upload_factor(c, P.local, op->precision == HZ_MIXED ? 1 : 0, c->n, c->loc, c->loc_max,
-                          op->precision == HZ_MIXED ? 512 : 256, c->S, op->sweep_tasks, op->bwd_chunk));
+                          op->precision == HZ_MIXED ? 512 : 256, c->S, op->sweep_tasks, op->bwd_chunk,
+                          local_merge_width(op->precision == HZ_MIXED ? 1 : 0), local_merge_sparse(P.local)));
   {
     const hz::FactorDev& F = c->loc;
     hz_stats& st = c->stats;
@@ -2908,10 +2929,12 @@ void plan_bytes(const hz::HostProblem& P, const hz_options& op, int64_t& persist
   int64_t b = 0;
   b += P.A.pat.nnz() * (4 + 8 + 16 + 16 + 16) + (n + 1) * 8;                  // A pattern, K, M', B', A
   b += P.local.panel_elems * vs + (3 * P.local.voff.back() + P.local.u_elems) * vs;
+  b += plan_solve_tree(P.local, local_merge_width(op.precision == HZ_MIXED ? 1 : 0), local_merge_sparse(P.local))
+           .merged_elems * vs;                                                // merged solve panels
   b += int64_t(P.local.rowlist.size()) * 4 + int64_t(P.local.cidx.size()) * 8 + int64_t(P.local.epos.size()) * 40;
   b += P.coarse.panel_elems * 16;
   if (!P.coarse.voff.empty() && P.clocal.voff.empty())
-    b += plan_solve_tree(P.coarse, 0, hz::kMaxSolveK).merged_elems * 16;          // merged solve panels
+    b += plan_solve_tree(P.coarse, hz::kMaxSolveK).merged_elems * 16;          // merged solve panels
   if (!P.coarse.voff.empty())
     b += (3 * P.coarse.voff.back() + P.coarse.u_elems) * 16 + int64_t(P.coarse.epos.size()) * 40;
   if (!P.clocal.voff.empty()) {

@@ -10,6 +10,7 @@ namespace hz {
 // One supernode of a batched multifrontal factorisation (56 bytes).
 // widest merged solve supernode of the complex128 sweeps (see FactorDev::ssn)
 constexpr int kMaxSolveK = 448;
+constexpr int kMaxSolveK64 = 512;   // the same for the complex64 sweeps
 
 struct SnDev {
   int32_t k, m, first, parent;   // pivots, front order, first vector index, parent (-1 root)

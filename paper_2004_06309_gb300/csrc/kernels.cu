@@ -907,7 +907,7 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
                                              float2* zout, float2* u) {
   constexpr int NP = 256 / CG;                       // row pairs per task
   constexpr int ROWS = 2 * NP;
-  __shared__ float2 b1[kMaxK];
+  __shared__ float2 b1[kMaxSolveK64];
   __shared__ float2 part[CG][ROWS];
   const SnDev S = sn[t.x];
   const int k = S.k, m = S.m, tid = threadIdx.x;
@@ -960,6 +960,23 @@ __device__ __forceinline__ void fwd_c64_item(const int2 t, const SnDev* sn, cons
             if (j < j0) c0 = cmad(make_float2(pv[q].x, pv[q].y), bj, c0);
           }
         }
+      }
+      // merged solve supernodes wider than kMaxK: the remaining columns, same chains
+      int j = cg + CG * MQ;
+      for (; j + CG < j1; j += 2 * CG) {
+        const float4 p = P4[int64_t(j) * ld4];
+        const float4 q = P4[int64_t(j + CG) * ld4];
+        const float2 bj = b1[j], bq = b1[j + CG];
+        a1 = cmad(make_float2(p.z, p.w), bj, a1);
+        c1 = cmad(make_float2(q.z, q.w), bq, c1);
+        if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
+        if (j + CG < j0) c0 = cmad(make_float2(q.x, q.y), bq, c0);
+      }
+      if (j < j1) {
+        const float4 p = P4[int64_t(j) * ld4];
+        const float2 bj = b1[j];
+        a1 = cmad(make_float2(p.z, p.w), bj, a1);
+        if (j < j0) a0 = cmad(make_float2(p.x, p.y), bj, a0);
       }
     }
   } else {
@@ -1297,7 +1314,8 @@ void launch_solve(const FactorDev& F, cudaStream_t st) {
 // dependent levels.
 // ---------------------------------------------------------------------------
 // tmp (ks x w, column-major) = M[w .. w + ks, 0 .. w)
-__global__ void k_merge_save(const double2* M, int ldm, int w, int ks, double2* tmp) {
+template <typename V>
+__global__ void k_merge_save(const V* M, int ldm, int w, int ks, V* tmp) {
   const int64_t n = int64_t(ks) * w;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
     const int q = int(e % ks), c = int(e / ks);
@@ -1307,27 +1325,29 @@ __global__ void k_merge_save(const double2* M, int ldm, int w, int ks, double2* 
 
 // M[w + i, c] = (i >= ks ? M[w + i, c] : 0) - sum_q C(i, q) tmp[q, c] for i < ms, c < w, with
 // C = [T_s (unit diagonal, upper part 0); G_s] the appended panel.  64 x 32 output tiles,
-// 16-deep slices of q staged in shared memory; each thread owns 4 rows x 2 columns.
-__global__ void __launch_bounds__(256) k_merge_update(double2* M, int ldm, int w, const double2* Ps, int lds,
-                                                      int ks, int ms, const double2* tmp) {
-  __shared__ double2 Cs[16][64];
-  __shared__ double2 As[16][32];
+// 16-deep slices of q staged in shared memory; each thread owns 4 rows x 2 columns.  The
+// sums run in the panels' precision (the complex64 factor is itself computed in FP32).
+template <typename V>
+__global__ void __launch_bounds__(256) k_merge_update(V* M, int ldm, int w, const V* Ps, int lds,
+                                                      int ks, int ms, const V* tmp) {
+  __shared__ V Cs[16][64];
+  __shared__ V As[16][32];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int i0 = blockIdx.x * 64, c0 = blockIdx.y * 32;
-  double2 acc[4][2];
+  V acc[4][2];
 #pragma unroll
   for (int a = 0; a < 4; a++)
 #pragma unroll
-    for (int b = 0; b < 2; b++) acc[a][b] = make_double2(0.0, 0.0);
+    for (int b = 0; b < 2; b++) acc[a][b] = czero<V>();
   for (int q0 = 0; q0 < ks; q0 += 16) {
 #pragma unroll
     for (int t = 0; t < 4; t++) {
       const int e = tid + 256 * t, il = e & 63, ql = e >> 6;
       const int i = i0 + il, q = q0 + ql;
-      double2 v = make_double2(0.0, 0.0);
+      V v = czero<V>();
       if (i < ms && q < ks) {
         if (i >= ks || i > q) v = Ps[i + int64_t(lds) * q];
-        else if (i == q) v = make_double2(1.0, 0.0);
+        else if (i == q) v = from2<V>(make_double2(1.0, 0.0));
       }
       Cs[ql][il] = v;
     }
@@ -1335,15 +1355,15 @@ __global__ void __launch_bounds__(256) k_merge_update(double2* M, int ldm, int w
     for (int t = 0; t < 2; t++) {
       const int e = tid + 256 * t, ql = e & 15, cl = e >> 4;
       const int q = q0 + ql, c = c0 + cl;
-      As[ql][cl] = (q < ks && c < w) ? tmp[q + int64_t(ks) * c] : make_double2(0.0, 0.0);
+      As[ql][cl] = (q < ks && c < w) ? tmp[q + int64_t(ks) * c] : czero<V>();
     }
     __syncthreads();
 #pragma unroll
     for (int ql = 0; ql < 16; ql++) {
-      double2 b0 = As[ql][2 * tx], b1 = As[ql][2 * tx + 1];
+      const V b0 = As[ql][2 * tx], b1 = As[ql][2 * tx + 1];
 #pragma unroll
       for (int a = 0; a < 4; a++) {
-        const double2 cv = Cs[ql][4 * ty + a];
+        const V cv = Cs[ql][4 * ty + a];
         acc[a][0] = cmad(cv, b0, acc[a][0]);
         acc[a][1] = cmad(cv, b1, acc[a][1]);
       }
@@ -1358,15 +1378,15 @@ __global__ void __launch_bounds__(256) k_merge_update(double2* M, int ldm, int w
     for (int b = 0; b < 2; b++) {
       const int c = c0 + 2 * tx + b;
       if (c >= w) continue;
-      double2* o = M + (w + i) + int64_t(ldm) * c;
-      const double2 base = i >= ks ? *o : make_double2(0.0, 0.0);
-      *o = make_double2(base.x - acc[a][b].x, base.y - acc[a][b].y);
+      V* o = M + (w + i) + int64_t(ldm) * c;
+      *o = csub(i >= ks ? *o : czero<V>(), acc[a][b]);
     }
   }
 }
 
 // M[w + i, w + q] = Ps[i, q] for i < ms, q < ks
-__global__ void k_merge_put(double2* M, int ldm, int w, const double2* Ps, int lds, int ks, int ms) {
+template <typename V>
+__global__ void k_merge_put(V* M, int ldm, int w, const V* Ps, int lds, int ks, int ms) {
   const int64_t n = int64_t(ks) * ms;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
     const int i = int(e % ms), q = int(e / ms);
@@ -1374,13 +1394,13 @@ __global__ void k_merge_put(double2* M, int ldm, int w, const double2* Ps, int l
   }
 }
 
-void launch_merge_panels(const FactorDev& F, cudaStream_t st) {
-  if (F.merges.empty() || F.precision != 0) return;
-  double2* P = (double2*)F.panels;
-  double2* tmp = (double2*)F.merge_tmp;
+template <typename V>
+static void merge_panels_t(const FactorDev& F, cudaStream_t st) {
+  V* P = (V*)F.panels;
+  V* tmp = (V*)F.merge_tmp;
   for (const FactorDev::MergeStep& m : F.merges) {
-    double2* M = P + m.moff;
-    const double2* Ps = P + m.soff;
+    V* M = P + m.moff;
+    const V* Ps = P + m.soff;
     if (m.w > 0) {
       HZ_COUNT();
       k_merge_save<<<grid_for(int64_t(m.ks) * m.w, 256), 256, 0, st>>>(M, m.ldm, m.w, m.ks, tmp);
@@ -1391,6 +1411,12 @@ void launch_merge_panels(const FactorDev& F, cudaStream_t st) {
     HZ_COUNT();
     k_merge_put<<<grid_for(int64_t(m.ks) * m.ms, 256), 256, 0, st>>>(M, m.ldm, m.w, Ps, m.lds, m.ks, m.ms);
   }
+}
+
+void launch_merge_panels(const FactorDev& F, cudaStream_t st) {
+  if (F.merges.empty()) return;
+  if (F.precision == 0) merge_panels_t<double2>(F, st);
+  else merge_panels_t<float2>(F, st);
 }
 
 void launch_prolong(const FactorDev& F, const double2* y, double2* z, cudaStream_t st) {

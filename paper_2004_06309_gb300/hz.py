@@ -77,6 +77,7 @@ class Stats(C.Structure):
         ("sweep_chunk", C.c_int32), ("sweep_scale", C.c_double),
         ("coarse_solve_levels", C.c_int32), ("coarse_merged_chains", C.c_int32),
         ("coarse_merged_bytes", C.c_int64),
+        ("solve_levels", C.c_int32), ("merged_chains", C.c_int32), ("merged_bytes", C.c_int64),
     ]
 
     def as_dict(self):

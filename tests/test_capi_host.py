@@ -90,8 +90,8 @@ def test_sweep_schedules_cover_every_kernel_variant(hzmod):
         plans = {sw: hzmod.plan(p, precision=prec, sweep_tasks=sw) for sw in (0, 1, 2)}
         for st in plans.values():
             assert st["max_snode_width"] == width
-            assert st["fwd_levels_wide"] + st["fwd_levels_narrow"] == st["nlevels"]
-            assert st["bwd_levels_wide"] + st["bwd_levels_narrow"] == st["nlevels"]
+            assert st["fwd_levels_wide"] + st["fwd_levels_narrow"] == st["solve_levels"]
+            assert st["bwd_levels_wide"] + st["bwd_levels_narrow"] == st["solve_levels"]
             assert st["bwd_split_blocks"] > 0
         assert plans[1]["fwd_levels_narrow"] == 0 and plans[1]["bwd_levels_narrow"] == 0
         assert plans[2]["fwd_levels_wide"] == 0 and plans[2]["bwd_levels_wide"] == 0
@@ -150,11 +150,11 @@ def test_dense_eig_real_pairs_diagonal_and_bad_input(hzmod):
     assert e.value.status == hzmod.HZ_ERR_BREAKDOWN
 
 
-def test_coarse_solve_tree_merges_the_separator_chains(hzmod):
+def test_solve_trees_merge_the_separator_chains(hzmod):
     """The direct coarse factor's sweeps run on a solve tree with the supernode chains at the
-    top separators merged: fewer levels than the factor tree, merged widths within 448, the
-    merged panels counted in the planned device bytes; the iterative coarse solve has no
-    direct factor and merges nothing."""
+    top separators merged: fewer levels than the factor tree, merged widths within 448; the
+    subdomain factors' sweeps likewise on their sparse top levels; the iterative coarse
+    solve has no direct factor and merges nothing there."""
     import bench
     p = bench.make_problem(bench.WORKLOADS["overthrust-small"])
     st = hzmod.plan(p, precision=hzmod.HZ_MIXED)
@@ -162,6 +162,9 @@ def test_coarse_solve_tree_merges_the_separator_chains(hzmod):
     assert 0 < st["coarse_solve_levels"] < st["nlevels_coarse"], st
     # a merged chain's panel holds at most 448 columns of n_coarse rows
     assert 0 < st["coarse_merged_bytes"] <= st["coarse_merged_chains"] * 448 * st["n_coarse"] * 16
+    # the subdomain factors: chains merge on the sparse top levels only
+    assert st["merged_chains"] > 0 and 0 < st["solve_levels"] < st["nlevels"], st
+    assert 0 < st["merged_bytes"] < st["nnz_factor"] * 8
     it = hzmod.plan(p, precision=hzmod.HZ_MIXED, coarse_solver=hzmod.HZ_COARSE_ORAS)
     assert it["coarse_merged_chains"] == 0 and it["coarse_merged_bytes"] == 0
     assert it["coarse_solve_levels"] == it["nlevels_coarse"]

@@ -89,7 +89,7 @@ def test_apply_M_every_variant(hzmod, case, prec, sweep, chunk):
     assert st["max_snode_width"] == (128 if prec == "mixed" else 112), st
     if sweep == 1:
         assert st["fwd_levels_narrow"] == 0 and st["bwd_levels_narrow"] == 0
-        assert st["fwd_levels_wide"] == st["nlevels"] and st["bwd_levels_wide"] == st["nlevels"]
+        assert st["fwd_levels_wide"] == st["solve_levels"] and st["bwd_levels_wide"] == st["solve_levels"]
         assert st["bwd_split_blocks"] > 0          # supernodes taller than one chunk
     elif sweep == 2:
         assert st["fwd_levels_wide"] == 0 and st["bwd_levels_wide"] == 0
