@@ -1303,7 +1303,7 @@ void launch_solve(const FactorDev& F, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// merged solve supernodes (complex128 factors): a chain s_1 -> s_2 -> ... in which each
+// merged solve supernodes (complex128 and complex64 factors): a chain s_1 -> s_2 -> ... in which each
 // supernode is the only child of the next and its rows below its pivots are exactly the
 // next one's rows.  A supernode's panel holds T = L11^{-1} (strict lower part; D^{-1} on the
 // diagonal) over G = L21 L11^{-1}.  Appending s (T_s, G_s) to the merged M (T_M, G_M, width

@@ -101,6 +101,10 @@ def test_apply_M_every_variant(hzmod, case, prec, sweep, chunk):
     if prec == "mixed":
         assert st["tc_multi_fronts"] > 0 and st["tc_max_kstages"] > 1, st
         assert st["tc_tiles"] > st["tc_multi_fronts"]
+    # the sweeps ran on merged solve trees: separator chains merged on the subdomains'
+    # sparse top levels and in the direct coarse factor
+    assert st["merged_chains"] > 0 and st["solve_levels"] < st["nlevels"], st
+    assert st["coarse_merged_chains"] > 0 and st["coarse_solve_levels"] < st["nlevels_coarse"], st
     err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
     tol = 1e-10 if prec == "fp64" else kappa * U32
     print(f"apply_M {prec} sweep={sweep} chunk={chunk}: rel L2 {err:.3e} (bound {tol:.3e}, "
