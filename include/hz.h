@@ -235,7 +235,9 @@ typedef struct {
   int64_t coarse_merged_bytes;   /* device bytes of their panels                         */
   /* the same for the subdomain factors, whose chains merge (up to 512 wide in complex64,
      448 in complex128) on the sparse top levels of the batched trees, where each level
-     holds at most two supernodes per subdomain                                        */
+     holds at most two supernodes per subdomain.  Setting the environment variable
+     HZ_NO_SOLVE_MERGE (read once per process) turns both merges off: the sweeps then run
+     on the factor trees, for comparison; results agree to rounding.                    */
   int32_t solve_levels;          /* levels of the subdomains' solve tree (nlevels: factor) */
   int32_t merged_chains;
   int64_t merged_bytes;

@@ -168,3 +168,39 @@ def test_solve_trees_merge_the_separator_chains(hzmod):
     it = hzmod.plan(p, precision=hzmod.HZ_MIXED, coarse_solver=hzmod.HZ_COARSE_ORAS)
     assert it["coarse_merged_chains"] == 0 and it["coarse_merged_bytes"] == 0
     assert it["coarse_solve_levels"] == it["nlevels_coarse"]
+
+
+def test_solve_tree_merge_off_plans_the_factor_trees(hzmod):
+    """With HZ_NO_SOLVE_MERGE set (read once per process, hence a child process) the
+    sweeps are planned on the factor trees: as many solve levels as factor levels, no
+    merged panels, and planned device bytes lower by the merged panels' bytes plus the 5 %
+    headroom the plan adds to everything it counts."""
+    import json
+    import subprocess
+    import sys
+    code = ("import json, bench\n"
+            "from paper_2004_06309_gb300 import hz\n"
+            "p = bench.make_problem(bench.WORKLOADS['overthrust-small'])\n"
+            "out = {}\n"
+            "for prec in (hz.HZ_MIXED, hz.HZ_FP64):\n"
+            "    out[prec] = hz.plan(p, precision=prec)\n"
+            "print(json.dumps(out))\n")
+    runs = {}
+    for off in (False, True):
+        env = dict(os.environ)
+        env.pop("HZ_NO_SOLVE_MERGE", None)
+        if off:
+            env["HZ_NO_SOLVE_MERGE"] = "1"
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs[off] = json.loads(r.stdout.strip().splitlines()[-1])
+    for prec in runs[False]:
+        on, off = runs[False][prec], runs[True][prec]
+        assert off["solve_levels"] == off["nlevels"] and off["coarse_solve_levels"] == off["nlevels_coarse"]
+        assert off["merged_chains"] == 0 and off["merged_bytes"] == 0
+        assert off["coarse_merged_chains"] == 0 and off["coarse_merged_bytes"] == 0
+        assert on["merged_bytes"] > 0 and on["coarse_merged_bytes"] > 0
+        assert on["nnz_factor"] == off["nnz_factor"] and on["nlevels"] == off["nlevels"]
+        merged = on["merged_bytes"] + on["coarse_merged_bytes"]
+        assert abs(on["device_bytes"] - off["device_bytes"] - 1.05 * merged) <= 2, (on, off)
