@@ -103,6 +103,31 @@ def make_problem(spec):
                                     part_jitter=spec.get("part_jitter", 0.0))
 
 
+
+def workload_config(args, spec, world, n=None):
+    """The bench line's ``config``: the workload as it is defined, so that the GPU arm and the
+    reference arm print the same object.  ``n`` (the dof count the library reports) defaults to
+    the count the workload's mesh has."""
+    if spec["kind"] == "tiny":
+        p = make_problem(spec)                       # P1: one dof per vertex
+        n0, nsub, overlap, levels, restart, freq = len(p.mesh.xyz), p.nsub, p.overlap, p.levels, p.restart, p.freq
+    else:
+        nx, ny, nz = synth_cells(spec)
+        n0 = (4 * nx + 1) * (4 * ny + 1) * (4 * nz + 1)
+        nsub, overlap, levels, restart, freq = spec["nsub"], spec["overlap"], 2, spec["restart"], spec["freq"]
+    nrhs = spec["nrhs"] if args.nrhs == 1 and spec.get("nrhs") else args.nrhs
+    block = spec["block"] if args.block == 0 and spec.get("block") else args.block
+    return {"workload": args.workload, "n_dofs": int(n if n is not None else n0), "nsub": nsub, "overlap": overlap,
+            "levels": 2 if levels == 2 else 1, "restart": restart, "tol": 1e-6,
+            "rhs_per_step": nrhs, "block_size": block, "freq_hz": freq,
+            "part_jitter": spec.get("part_jitter", 0.0),
+            "coarse_solver": spec.get("coarse", args.coarse), "recycle": args.recycle,
+            "coarse_tol": args.coarse_tol or spec.get("coarse_tol", 0.0),
+            "factor_group": spec.get("factor_group", 0), "tune_sweeps": args.tune_sweeps,
+            "l2": "inputs larger than L2 (factors >> 129 MB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -633,7 +658,7 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "RHS/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "complex128",
-                "data": "synthetic", "config": {"workload": args.workload},
+                "data": "synthetic", "config": workload_config(args, WORKLOADS[args.workload], world),
                 "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": base["cores"], "kind": "oracle",
                                  "sample": base["sample"]},
                 "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -829,15 +854,7 @@ def main():
         "dtype": "complex64 subdomain factors/solves + complex128 Krylov, SpMV, coarse" if main_p == "mixed"
         else "complex128",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_dofs": n, "nsub": prob.nsub, "overlap": prob.overlap,
-                   "levels": 2 if prob.levels == 2 else 1, "restart": prob.restart, "tol": 1e-6,
-                   "rhs_per_step": args.nrhs, "block_size": args.block, "freq_hz": prob.freq,
-                   "part_jitter": spec.get("part_jitter", 0.0),
-                   "coarse_solver": coarse, "recycle": args.recycle,
-                   "coarse_tol": args.coarse_tol or spec.get("coarse_tol", 0.0),
-                   "factor_group": spec.get("factor_group", 0), "tune_sweeps": args.tune_sweeps,
-                   "l2": "inputs larger than L2 (factors >> 129 MB)",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(args, spec, world, n),
         "iterations": R["iterations"][-1], "rel_residual": R["rel"],
         "latency_ms": lat(R),
         "factor_seconds": R["t_factor"],
